@@ -1,0 +1,321 @@
+"""Benchmark: Expected Force (EF_2) of every node, clusters/s on one GB300.
+
+Workload (default): the power-law configuration model with n = 4,000,000,
+P(d) ~ d^-2.3 on [3, 20000], seed 20230609 -- the ~44M-entry power-law graph
+(20.7M undirected edges, 41.3M CSR entries, 1.28e10 clusters).  Other
+workloads: --workload ba1m (Barabasi-Albert n=1e6, m=5) or er2000.
+
+One step = one ef_compute_ex call over the whole graph (validation, prep,
+wedge pass, triangle pass, finalize), FP32-compensated path, inputs resident
+in HBM.  The metric is clusters/s = W / step time with W = sum_v C(D_v, 2),
+the number of clusters Algorithm 1 enumerates.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead (the
+vertex-centric formulation, OpenMP over the host cores) on a bounded random
+sample of the same graph.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    "plcm4m": (3, "power-law configuration model n=4000000 gamma=2.3 degrees in [3,20000] seed=20230609"),
+    "ba1m": (2, "Barabasi-Albert n=1000000 m=5 seed=20230608"),
+    "er2000": (1, "Erdos-Renyi G(n=2000, p=0.004) seed=20230607"),
+}
+MUFU_PER_SM_CLK = 16     # lg2 results per SM per clock (MUFU pipe)
+NUM_SMS = 152
+SM_MAX_MHZ = 2070.0
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=list(WORKLOADS), default="plcm4m")
+    p.add_argument("--precision", choices=["fp32c", "fp64"], default="fp32c")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def graph_stats(g):
+    d = g.degrees.astype(np.int64)
+    W = int((d * (d - 1) // 2).sum())
+    big = d[d > 32]
+    return dict(n=g.n, nnz=g.nnz, W=W, big_evals=int((big * (big - 1)).sum()),
+                small_evals=int((d[d <= 32] * (d[d <= 32] - 1)).sum()), maxdeg=int(d.max()) if g.n else 0)
+
+
+def cpu_baseline(g, seconds: float, seed: int = 0):
+    """The oracle (vertex-centric, OpenMP on all host cores) on a random node
+    sample sized for about `seconds` of CPU work.  Returns clusters/s, where a
+    sample's cluster count is the sum of its nodes' credited clusters / 4
+    (every cluster carries 4 credits), so the rate is comparable with W/t."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    cores = oracle.num_threads()
+    k = 2000
+    t_used = 0.0
+    credits = 0
+    nodes_done = 0
+    while True:
+        nodes = rng.choice(g.n, size=min(k, g.n), replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        r = oracle.vertex(g, nodes, threads=cores)
+        dt = time.perf_counter() - t0
+        t_used += dt
+        credits += int(r["N"].sum())
+        nodes_done += len(nodes)
+        if t_used >= seconds or len(nodes) == g.n:
+            break
+        k = int(min(g.n, max(2000, k * max(1.5, min(8.0, (seconds - t_used) / max(dt, 1e-3))))))
+    rate = credits / 4 / t_used
+    return {"value": rate, "unit": "clusters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nodes_done} uniformly random nodes (vertex-centric oracle, OpenMP dynamic,2), "
+                      f"{credits / 4:.3g} clusters = credited/4, {t_used:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    idx, desc = WORKLOADS[args.workload]
+    g = synth.workload(idx)
+    st = graph_stats(g)
+    rates = []
+    for _ in range(args.warmup):
+        cpu_baseline(g, min(2.0, args.cpu_seconds / 4), seed=99)
+    t_total = 0.0
+    for i in range(args.steps):
+        r = cpu_baseline(g, args.cpu_seconds / max(args.steps, 1) * 2, seed=i)
+        rates.append(r["value"])
+        t_total += st["W"] / r["value"]
+    v = float(statistics.median(rates))
+    line = {"impl": "reference", "metric": "clusters/s", "value": v, "unit": "clusters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": st["W"] / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "nodes": st["n"], "nnz": st["nnz"],
+                                            "clusters": st["W"]},
+            "cpu_baseline": dict(r, value=v),
+            "e2e": {"value": v, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2306_00606_gb300 as ef
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    idx, desc = WORKLOADS[args.workload]
+    g = synth.workload(idx)
+    st = graph_stats(g)
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    ci = torch.from_numpy(g.col_idx).to(dev)
+    n = g.n
+    stream = torch.cuda.current_stream(dev)
+    ctx = ef.Context(local, stream)
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def step(profile=False):
+        ef.ef_compute_ex(ctx.handle, rp, ci, precision=args.precision, ef=out, profile=profile)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    ctx.stats(reset=True)
+
+    # ---- device-resident timing (inputs in HBM; > L2, no flush) ----
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(profile=True)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    passes = ctx.stats(reset=True)
+    ms_step = ms / args.steps
+    value = st["W"] * args.steps * world / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers (H2D + compute + D2H) ----
+    h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+    h_ci = torch.from_numpy(g.col_idx).pin_memory()
+    h_out = torch.empty(n, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        ef.ef_compute_ex(ctx.handle, h_rp, h_ci, precision=args.precision, ef=h_out, host_io=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ef.ef_compute_ex(ctx.handle, h_rp, h_ci, precision=args.precision, ef=h_out, host_io=True)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = st["W"] * args.steps * world / e2e_s
+    h2d = 4 * (n + 1) + 4 * g.nnz
+    d2h = 8 * n
+
+    # ---- roofline of the dominant pass ----
+    per = {k: passes[k] / max(passes["calls"], 1) for k in
+           ("prep_ms", "wedge_small_ms", "wedge_big_ms", "triangle_ms", "finalize_ms", "total_ms")}
+    clocks = clk.summary()
+    dom = max(("prep_ms", "wedge_small_ms", "wedge_big_ms", "triangle_ms", "finalize_ms"), key=lambda k: per[k])
+    peak_evals = NUM_SMS * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    if dom in ("wedge_big_ms", "wedge_small_ms"):
+        evals = st["big_evals"] if dom == "wedge_big_ms" else st["small_evals"]
+        achieved = evals / (per[dom] / 1e3)
+        roofline = {"kernel": dom[:-3], "bound": "alu", "achieved": achieved / 1e12, "peak": peak_evals / 1e12,
+                    "unit": "T(d log2 d evals)/s", "frac": achieved / peak_evals, "traffic": None,
+                    "peak_source": "152 SMs x 16 MUFU lg2/clk x 2070 MHz (recipe unit counts and max clock)"}
+    else:
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+            hbm = float(peaks["hbm_gbs"])
+            src = "measured"
+        except (OSError, KeyError, ValueError):
+            hbm, src = 6800.0, "fallback"
+        bytes_alg = 4 * (n + 1) + 4 * g.nnz + 8 * n
+        achieved = bytes_alg / (per[dom] / 1e3) / 1e9
+        roofline = {"kernel": dom[:-3], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": None, "peak_source": src}
+
+    line = {
+        "metric": "clusters/s", "value": value, "unit": "clusters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32c" else "f64", "data": "synthetic",
+        "config": {"workload": desc, "nodes": n, "nnz": g.nnz, "edges": g.nnz // 2, "clusters": st["W"],
+                   "max_degree": st["maxdeg"], "precision": args.precision,
+                   "l2": f"inputs larger than L2 (CSR {(4 * (n + 1) + 4 * g.nnz) / 2**20:.0f} MiB), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "ef_wall_ms_per_graph": ms_step,
+        "passes_ms": per,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": "clusters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(passes["kernels"]),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

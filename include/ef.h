@@ -1,0 +1,139 @@
+/*
+ * ef.h -- C ABI of libef.so: the Expected Force (EF_2) of every node of an
+ * undirected simple graph, computed by hand-written sm_103a CUDA kernels.
+ *
+ * Method (paper "Scaling Expected Force", Sections 3.3 and 4): a 2-hop
+ * transmission cluster is a tree with two edges; its out-degree d is the
+ * number of edges leaving it.  Algorithm 1 enumerates every cluster once as
+ * a triple (i, v, j) of a middle node v and two of its neighbours i < j,
+ * with d = D_v + D_i + D_j - 4, minus 2 more when i and j are adjacent, and
+ * credits d once to i, once to j and twice to v.  EF(v) is the entropy of
+ * the normalised degrees of the clusters credited to v (Eq. 1), which equals
+ *     EF(v) = ln S_v - T_v / S_v,  S_v = sum of credited d,
+ *                                  T_v = sum of credited d ln d.
+ * A node whose credited degrees sum to 0 (no clusters, or only clusters of
+ * degree 0) is degenerate: EF = 0 and its flag is 1.
+ *
+ * Graph format (all entry points): symmetric CSR, int32 indices.
+ *   row_ptr[n+1], row_ptr[0] = 0, row_ptr[n] = m, non-decreasing;
+ *   col_idx[m]: each undirected edge stored in both rows (m = nnz = 2|E|),
+ *   every row strictly ascending, no self-loops, entries in [0, n).
+ *   m must be < 2^31.
+ *
+ * Memory: the caller owns every input and output buffer.  Pointers are
+ * device pointers unless ef_options.host_io = 1.  A context owns its device
+ * scratch, grows it on demand and frees it in ef_ctx_destroy.  Work is
+ * issued on the context's stream; ef_compute_ex returns after the stream has
+ * finished unless ef_options.async = 1 (see there).
+ *
+ * Errors: every entry point returns an int status (no exceptions cross the
+ * ABI).  ef_last_error(ctx) gives a one-line message for the last failure.
+ */
+#ifndef EF_H
+#define EF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum ef_status {
+    EF_OK = 0,
+    EF_ERR_ARG = 1,         /* null pointer, negative size, m >= 2^31, bad option */
+    EF_ERR_GRAPH = 2,       /* not a symmetric simple sorted CSR (checked on device) */
+    EF_ERR_OOM = 3,         /* device or pinned allocation failed */
+    EF_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    EF_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    EF_ERR_MODEL = 6,       /* surrogate model malformed or mismatched */
+    EF_ERR_UNSUPPORTED = 7  /* option combination not provided */
+};
+
+enum ef_precision {
+    EF_PREC_FP64 = 0,  /* d ln d from an FP64 table, FP64 sums everywhere */
+    EF_PREC_FP32C = 1  /* d ln d in FP32 with compensated (Kahan) FP32 sums
+                          per thread; FP64 for every cross-thread, per-node
+                          and final reduction and for ln S - T/S */
+};
+
+typedef struct ef_ctx ef_ctx;
+
+typedef struct {
+    const int32_t *row_ptr;   /* n+1 entries */
+    const int32_t *col_idx;   /* m entries */
+} ef_csr;
+
+typedef struct {
+    int32_t precision;     /* enum ef_precision; default EF_PREC_FP64 */
+    int32_t trust_input;   /* 1: skip CSR validation (and its host sync) */
+    int32_t host_io;       /* 1: graph and outputs are host pointers; the
+                              library copies them in and out */
+    int32_t async;         /* 1 (device I/O and trust_input only): return
+                              without waiting; results valid after ef_sync */
+    int32_t profile;       /* 1: time each pass with CUDA events on the
+                              context stream (read with ef_get_stats) */
+    int32_t wedge_mode;    /* 0: automatic; 1: force the direct pairwise
+                              wedge kernel for every middle node (reference
+                              kernel for benchmarking); 2: force the
+                              degree-class kernel for every middle node of
+                              degree > 32 */
+    int32_t reserved[2];
+} ef_options;
+
+/* Optional per-node outputs (any may be NULL); length n each. */
+typedef struct {
+    double  *ef;          /* EF(v) */
+    int64_t *n_clusters;  /* N_v: number of credited clusters (weights 2/1/1) */
+    int64_t *s;           /* S_v: sum of credited cluster degrees (exact) */
+    double  *t;           /* T_v: sum of credited d ln d */
+    int64_t *triangles;   /* t_v: triangles through v */
+    uint8_t *flag;        /* 1: degenerate (S_v = 0), EF = 0 */
+} ef_outputs;
+
+/* Per-pass timings in milliseconds, summed over profiled calls. */
+typedef struct {
+    int64_t calls;
+    double prep_ms;        /* validation, degrees, neighbour sums, orientation, reverse slots */
+    double wedge_small_ms; /* middle nodes of degree <= 32 */
+    double wedge_big_ms;   /* middle nodes of degree > 32 */
+    double triangle_ms;    /* triangle listing and corrections */
+    double finalize_ms;    /* per-node sums, S, N, EF */
+    double total_ms;
+    int64_t kernels;       /* kernels launched by profiled calls */
+} ef_stats;
+
+/* Create a context on CUDA device `device` issuing work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  0 on success. */
+int ef_ctx_create(int device, void *stream, ef_ctx **out);
+/* Free the context and its scratch.  Safe on NULL. */
+int ef_ctx_destroy(ef_ctx *ctx);
+/* Message of the last failure on this context ("" if none); ctx may be
+ * NULL for failures of ef_compute and ef_ctx_create. */
+const char *ef_last_error(const ef_ctx *ctx);
+/* Wait for all work issued on the context's stream. */
+int ef_sync(ef_ctx *ctx);
+/* Read (and with reset != 0, clear) the accumulated pass timings. */
+int ef_get_stats(ef_ctx *ctx, ef_stats *out, int reset);
+
+/*
+ * EF of every node (Algorithm 1, Eq. 1).  Device pointers; FP64 path;
+ * input validated; synchronous on the current device's legacy default
+ * stream, with a library-owned context per device.
+ *   g: CSR (device), n: nodes, m: nnz, out_ef: double[n] (device).
+ * Returns EF_OK or an ef_status code.
+ */
+int ef_compute(const ef_csr *g, int32_t n, int64_t m, double *out_ef);
+
+/*
+ * Full-control form of ef_compute: options (NULL = defaults) and optional
+ * per-node outputs N, S, T, t, flag besides EF.
+ */
+int ef_compute_ex(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
+                  const ef_options *opt, ef_outputs *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EF_H */

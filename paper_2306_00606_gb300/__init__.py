@@ -1,0 +1,192 @@
+"""Expected Force (EF_2) on GB300: Python binding of libef.so.
+
+The binding only marshals arguments: every step of the computation runs in
+the library's sm_103a CUDA kernels behind the C ABI of ``include/ef.h``.
+PyTorch provides device memory and streams.  There is no CPU path: if
+``libef.so`` has not been built, or no CUDA device is present, every call
+raises ``EfError``.
+
+Functions carry the C names (``ef_ctx_create``, ``ef_compute``,
+``ef_compute_ex``, ...); ``Context`` is a small convenience wrapper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libef.so")
+
+EF_OK, EF_ERR_ARG, EF_ERR_GRAPH, EF_ERR_OOM, EF_ERR_CUDA, EF_ERR_TIMEOUT, EF_ERR_MODEL, EF_ERR_UNSUPPORTED = range(8)
+EF_PREC_FP64, EF_PREC_FP32C = 0, 1
+PRECISIONS = {"fp64": EF_PREC_FP64, "fp32c": EF_PREC_FP32C}
+
+# Every symbol include/ef.h declares (checked by the CPU test of the ABI).
+EXPORTED = ("ef_ctx_create", "ef_ctx_destroy", "ef_last_error", "ef_sync", "ef_get_stats",
+            "ef_compute", "ef_compute_ex")
+
+
+class EfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libef error {code}: {msg}")
+        self.code = code
+
+
+class ef_csr(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
+
+
+class ef_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("trust_input", ctypes.c_int32), ("host_io", ctypes.c_int32),
+                ("async_", ctypes.c_int32), ("profile", ctypes.c_int32), ("wedge_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+class ef_outputs(ctypes.Structure):
+    _fields_ = [("ef", ctypes.c_void_p), ("n_clusters", ctypes.c_void_p), ("s", ctypes.c_void_p),
+                ("t", ctypes.c_void_p), ("triangles", ctypes.c_void_p), ("flag", ctypes.c_void_p)]
+
+
+class ef_stats(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int64), ("prep_ms", ctypes.c_double), ("wedge_small_ms", ctypes.c_double),
+                ("wedge_big_ms", ctypes.c_double), ("triangle_ms", ctypes.c_double),
+                ("finalize_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("kernels", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libef.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise EfError(EF_ERR_CUDA, f"{path} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.ef_ctx_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.ef_ctx_destroy.argtypes = [vp]
+    lib.ef_last_error.argtypes = [vp]
+    lib.ef_last_error.restype = ctypes.c_char_p
+    lib.ef_sync.argtypes = [vp]
+    lib.ef_get_stats.argtypes = [vp, ctypes.POINTER(ef_stats), ctypes.c_int]
+    lib.ef_compute.argtypes = [ctypes.POINTER(ef_csr), i32, i64, vp]
+    lib.ef_compute_ex.argtypes = [vp, ctypes.POINTER(ef_csr), i32, i64, ctypes.POINTER(ef_options),
+                                  ctypes.POINTER(ef_outputs)]
+    for name in EXPORTED:
+        if name != "ef_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, ctx=None):
+    if rc != EF_OK:
+        msg = load_library().ef_last_error(ctx)
+        raise EfError(rc, (msg or b"").decode(errors="replace"))
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+# ------------------------------------------------------------- C-named calls
+
+def ef_ctx_create(device: int = 0, stream: int | None = None) -> int:
+    """Create a context on `device` issuing on `stream` (a cudaStream_t handle, None = default)."""
+    h = ctypes.c_void_p()
+    _check(load_library().ef_ctx_create(device, stream or None, ctypes.byref(h)))
+    return h.value
+
+
+def ef_ctx_destroy(ctx: int) -> None:
+    _check(load_library().ef_ctx_destroy(ctx), ctx)
+
+
+def ef_last_error(ctx: int | None = None) -> str:
+    return (load_library().ef_last_error(ctx) or b"").decode(errors="replace")
+
+
+def ef_sync(ctx: int) -> None:
+    _check(load_library().ef_sync(ctx), ctx)
+
+
+def ef_get_stats(ctx: int, reset: bool = False) -> dict:
+    st = ef_stats()
+    _check(load_library().ef_get_stats(ctx, ctypes.byref(st), int(reset)), ctx)
+    return st.as_dict()
+
+
+def ef_compute(row_ptr, col_idx, out_ef) -> None:
+    """EF of every node; CUDA tensors (int32 CSR, float64 output), FP64 path, synchronous."""
+    n = int(row_ptr.shape[0]) - 1
+    g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
+    _check(load_library().ef_compute(ctypes.byref(g), n, int(col_idx.shape[0]), _ptr(out_ef)))
+
+
+def ef_compute_ex(ctx: int, row_ptr, col_idx, *, precision: str = "fp64", ef=None, n_clusters=None, s=None,
+                  t=None, triangles=None, flag=None, trust_input: bool = False, host_io: bool = False,
+                  async_: bool = False, profile: bool = False, wedge_mode: int = 0) -> None:
+    """Full-control EF: writes whichever output buffers are given (device, or host with host_io)."""
+    n = int(row_ptr.shape[0]) - 1
+    g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
+    o = ef_options(PRECISIONS[precision], int(trust_input), int(host_io), int(async_), int(profile),
+                   int(wedge_mode))
+    out = ef_outputs(_ptr(ef), _ptr(n_clusters), _ptr(s), _ptr(t), _ptr(triangles), _ptr(flag))
+    _check(load_library().ef_compute_ex(ctx, ctypes.byref(g), n, int(col_idx.shape[0]), ctypes.byref(o),
+                                        ctypes.byref(out)), ctx)
+
+
+# ---------------------------------------------------------------- convenience
+
+class Context:
+    """A libef context bound to one CUDA device and the torch stream current at creation."""
+
+    def __init__(self, device: int | None = None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise EfError(EF_ERR_CUDA, "no CUDA device")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.handle = ef_ctx_create(self.device, self.stream.cuda_stream)
+
+    def close(self):
+        if self.handle:
+            ef_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def compute(self, row_ptr, col_idx, precision: str = "fp64", outputs=("ef",), **kw) -> dict:
+        """Allocate the requested outputs on the device and run ef_compute_ex."""
+        import torch
+        n = int(row_ptr.shape[0]) - 1
+        dev = torch.device("cuda", self.device)
+        dt = dict(ef=torch.float64, n_clusters=torch.int64, s=torch.int64, t=torch.float64,
+                  triangles=torch.int64, flag=torch.uint8)
+        res = {k: torch.empty(n, dtype=dt[k], device=dev) for k in outputs}
+        ef_compute_ex(self.handle, row_ptr, col_idx, precision=precision, **res, **kw)
+        return res
+
+    def stats(self, reset: bool = False) -> dict:
+        return ef_get_stats(self.handle, reset)

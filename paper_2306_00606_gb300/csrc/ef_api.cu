@@ -1,0 +1,386 @@
+// C ABI of libef (declared in include/ef.h): contexts, scratch management and
+// the orchestration of the passes for one graph.
+//
+// Pass order on the context stream (one graph):
+//   prep A   degrees + row_ptr checks, per-row checks + sigma1/sigma2 +
+//            out-degrees, work bins
+//   prep B   oriented CSR, reverse slots, omega, big-item offsets
+//   [host]   one 4-byte-class readback of the error word and max degree
+//            (skipped with trust_input)
+//   f table  f(d) = d ln d, d < 3 maxdeg + 1
+//   wedge    small middle nodes (sub-warp), big middle nodes (CTA items)
+//   triangle warp owners, CTA owners
+//   finalize per-node sums, N, S, T, EF, flag
+#include "ef_internal.cuh"
+
+#include <mutex>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+struct ef_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    char err[512] = {0};
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    double *ftab = nullptr;
+    int64_t ftab_cap = 0;
+    int32_t *h_counters = nullptr;   // pinned, 64 ints
+    void *io = nullptr;              // device copies for host_io
+    size_t io_bytes = 0;
+    cudaEvent_t ev[8] = {};
+    bool events = false;
+    ef_stats stats = {};
+};
+
+namespace {
+
+thread_local char g_err[512];
+
+// Kernels one ef_compute_ex call launches: prep A 3, prep B 2 scans of 3 +
+// reverse fill + item counts, f table 1, small wedges 4, big wedges 2,
+// triangles 2, finalize 1.
+constexpr int64_t KERNELS_PER_CALL = 3 + 8 + 1 + 4 + 2 + 2 + 1;
+
+void set_err(ef_ctx *c, const char *fmt, ...) {
+    char *dst = c ? c->err : g_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+}
+
+#define CU(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            set_err(ctx, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                    __LINE__);                                                              \
+            return e_ == cudaErrorMemoryAllocation ? EF_ERR_OOM : EF_ERR_CUDA;              \
+        }                                                                                   \
+    } while (0)
+
+inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carve the per-call scratch; returns the bytes needed (and fills s when base != null).
+size_t carve(char *base, int32_t n, int64_t m, ef::Scratch &s) {
+    using namespace ef;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        void *p = base ? base + off : nullptr;
+        off += al(bytes);
+        return p;
+    };
+    const size_t N = (size_t)n, M = (size_t)m;
+    s.D = (int32_t *)take(4 * N);
+    s.sig1 = (int64_t *)take(8 * N);
+    s.sig2 = (int64_t *)take(8 * N);
+    s.omega = (int64_t *)take(8 * N);
+    s.outdeg = (int32_t *)take(4 * N);
+    s.out_ptr = (int32_t *)take(4 * (N + 1));
+    s.out_col = (int32_t *)take(4 * (M + 1));
+    s.out_D = (int32_t *)take(4 * (M + 1));
+    s.out_rslot = (int32_t *)take(4 * (M + 1));
+    s.rev = (int32_t *)take(4 * (M + 1));
+    s.slotR = take(8 * (M + 1));
+    s.slotC = (double *)take(8 * (M + 1));
+    s.slotT = (int32_t *)take(4 * (M + 1));
+    s.Ccenter = (double *)take(8 * N);
+    s.tri_own = (double *)take(8 * N);
+    s.t_own = (int64_t *)take(8 * N);
+    s.bins = (int32_t *)take(4 * N * NUM_BINS);
+    s.counters = (int32_t *)take(4 * 64);
+    s.big_chunks = (int32_t *)take(4 * (N + 1));
+    s.big_partial = (double *)take(8 * (M / BIG_ROWS + N + 2));
+    s.scan_tmp = (int32_t *)take(4 * (N / 4096 + 4));
+    s.tri_gl = nullptr;
+    s.tri_gl_cap = 0;
+    return off;
+}
+
+int ensure_scratch(ef_ctx *ctx, size_t bytes) {
+    if (ctx->scratch_bytes >= bytes) return EF_OK;
+    if (ctx->scratch) {
+        CU(cudaStreamSynchronize(ctx->stream));
+        CU(cudaFree(ctx->scratch));
+        ctx->scratch = nullptr;
+        ctx->scratch_bytes = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    CU(cudaMalloc(&ctx->scratch, want));
+    ctx->scratch_bytes = want;
+    return EF_OK;
+}
+
+int ensure_ftab(ef_ctx *ctx, int64_t cap) {
+    if (ctx->ftab_cap >= cap) return EF_OK;
+    if (ctx->ftab) {
+        CU(cudaStreamSynchronize(ctx->stream));
+        CU(cudaFree(ctx->ftab));
+        ctx->ftab = nullptr;
+        ctx->ftab_cap = 0;
+    }
+    CU(cudaMalloc(&ctx->ftab, (size_t)cap * sizeof(double)));
+    ctx->ftab_cap = cap;
+    return EF_OK;
+}
+
+int ensure_io(ef_ctx *ctx, size_t bytes) {
+    if (ctx->io_bytes >= bytes) return EF_OK;
+    if (ctx->io) {
+        CU(cudaStreamSynchronize(ctx->stream));
+        CU(cudaFree(ctx->io));
+        ctx->io = nullptr;
+        ctx->io_bytes = 0;
+    }
+    CU(cudaMalloc(&ctx->io, bytes));
+    ctx->io_bytes = bytes;
+    return EF_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+const char *err_bits(int bits, char *buf, size_t len) {
+    buf[0] = 0;
+    if (bits & ef::ERRB_ROWPTR) strncat(buf, " row_ptr", len - strlen(buf) - 1);
+    if (bits & ef::ERRB_RANGE) strncat(buf, " column-out-of-range", len - strlen(buf) - 1);
+    if (bits & ef::ERRB_SELFLOOP) strncat(buf, " self-loop", len - strlen(buf) - 1);
+    if (bits & ef::ERRB_UNSORTED) strncat(buf, " row-not-strictly-ascending", len - strlen(buf) - 1);
+    if (bits & ef::ERRB_ASYM) strncat(buf, " asymmetric", len - strlen(buf) - 1);
+    return buf;
+}
+
+int compute_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const ef_options &o,
+                   const ef_outputs &out) {
+    using namespace ef;
+    cudaStream_t st = ctx->stream;
+    if (o.wedge_mode != 0 && o.wedge_mode != 1) {
+        set_err(ctx, "wedge_mode %d is not available", o.wedge_mode);
+        return EF_ERR_UNSUPPORTED;
+    }
+    Scratch s;
+    size_t need = carve(nullptr, n, m, s);
+    int rc = ensure_scratch(ctx, need);
+    if (rc) return rc;
+    carve((char *)ctx->scratch, n, m, s);
+    const bool prof = o.profile != 0;
+    if (prof) CU(cudaEventRecord(ctx->ev[0], st));
+
+    CU(cudaMemsetAsync(s.counters, 0, 64 * sizeof(int32_t), st));
+    if (launch_prep_a(rp, ci, n, m, s, st)) { set_err(ctx, "prep A launch failed"); return EF_ERR_CUDA; }
+    if (launch_prep_b(rp, ci, n, m, s, st)) { set_err(ctx, "prep B launch failed"); return EF_ERR_CUDA; }
+
+    int64_t fcap;
+    if (!o.trust_input) {
+        CU(cudaMemcpyAsync(ctx->h_counters, s.counters, 64 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        int bits = ctx->h_counters[CNT_ERR];
+        if (bits) {
+            char buf[160];
+            set_err(ctx, "input is not a symmetric simple sorted CSR:%s", err_bits(bits, buf, sizeof buf));
+            return EF_ERR_GRAPH;
+        }
+        fcap = 3 * (int64_t)ctx->h_counters[CNT_MAXDEG] + 1;
+    } else {
+        int64_t bound = (int64_t)n - 1 < m ? (int64_t)n - 1 : m;
+        fcap = 3 * (bound > 0 ? bound : 0) + 1;
+    }
+    rc = ensure_ftab(ctx, fcap);
+    if (rc) return rc;
+    s.ftab = ctx->ftab;
+    if (launch_ftab(s.ftab, s.counters + CNT_MAXDEG, fcap, st)) { set_err(ctx, "f table launch failed"); return EF_ERR_CUDA; }
+    CU(cudaMemsetAsync(s.slotC, 0, (size_t)m * sizeof(double), st));
+    CU(cudaMemsetAsync(s.slotT, 0, (size_t)m * sizeof(int32_t), st));
+    CU(cudaMemsetAsync(s.tri_own, 0, (size_t)n * sizeof(double), st));
+    CU(cudaMemsetAsync(s.t_own, 0, (size_t)n * sizeof(int64_t), st));
+    if (prof) CU(cudaEventRecord(ctx->ev[1], st));
+
+    if (launch_wedge_small(rp, ci, s, o.precision, n, st)) { set_err(ctx, "wedge small launch failed"); return EF_ERR_CUDA; }
+    if (prof) CU(cudaEventRecord(ctx->ev[2], st));
+    if (launch_wedge_big(rp, ci, s, o.precision, n, m, ctx->num_sms, st)) { set_err(ctx, "wedge big launch failed"); return EF_ERR_CUDA; }
+    if (prof) CU(cudaEventRecord(ctx->ev[3], st));
+    if (launch_triangles(s, n, ctx->num_sms, st)) { set_err(ctx, "triangle launch failed"); return EF_ERR_CUDA; }
+    if (prof) CU(cudaEventRecord(ctx->ev[4], st));
+    if (launch_finalize(rp, ci, s, o.precision, n, out, st)) { set_err(ctx, "finalize launch failed"); return EF_ERR_CUDA; }
+    if (prof) CU(cudaEventRecord(ctx->ev[5], st));
+    return EF_OK;
+}
+
+int check_args(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_options &o, const ef_outputs *out) {
+    if (!g || !out) { set_err(ctx, "null graph or outputs"); return EF_ERR_ARG; }
+    if (n < 0 || m < 0 || m >= ((int64_t)1 << 31)) { set_err(ctx, "bad sizes n=%d m=%lld", n, (long long)m); return EF_ERR_ARG; }
+    if (n > 0 && (!g->row_ptr || (m > 0 && !g->col_idx))) { set_err(ctx, "null CSR array"); return EF_ERR_ARG; }
+    if (o.precision != EF_PREC_FP64 && o.precision != EF_PREC_FP32C) { set_err(ctx, "bad precision %d", o.precision); return EF_ERR_ARG; }
+    if (o.async && (o.host_io || !o.trust_input)) { set_err(ctx, "async needs device I/O and trust_input"); return EF_ERR_ARG; }
+    return EF_OK;
+}
+
+void accumulate_stats(ef_ctx *ctx) {
+    float t[5];
+    for (int i = 0; i < 5; ++i)
+        if (cudaEventElapsedTime(&t[i], ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) t[i] = 0.f;
+    ctx->stats.calls += 1;
+    ctx->stats.prep_ms += t[0];
+    ctx->stats.wedge_small_ms += t[1];
+    ctx->stats.wedge_big_ms += t[2];
+    ctx->stats.triangle_ms += t[3];
+    ctx->stats.finalize_ms += t[4];
+    ctx->stats.total_ms += t[0] + t[1] + t[2] + t[3] + t[4];
+    ctx->stats.kernels += KERNELS_PER_CALL;
+}
+
+std::mutex g_default_mu;
+ef_ctx *g_default[64];
+
+}  // namespace
+
+extern "C" {
+
+int ef_ctx_create(int device, void *stream, ef_ctx **out) {
+    ef_ctx *ctx = nullptr;
+    if (!out) { set_err(nullptr, "null out pointer"); return EF_ERR_ARG; }
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        set_err(nullptr, "no CUDA device %d (count %d)", device, ndev);
+        return EF_ERR_CUDA;
+    }
+    ctx = new (std::nothrow) ef_ctx();
+    if (!ctx) { set_err(nullptr, "host allocation failed"); return EF_ERR_OOM; }
+    DeviceGuard dg(device);
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)stream;
+    int rc = EF_OK;
+    do {
+        cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+        if (e != cudaSuccess) { set_err(nullptr, "device query failed: %s", cudaGetErrorString(e)); rc = EF_ERR_CUDA; break; }
+        e = cudaMallocHost(&ctx->h_counters, 64 * sizeof(int32_t));
+        if (e != cudaSuccess) { set_err(nullptr, "pinned allocation failed: %s", cudaGetErrorString(e)); rc = EF_ERR_OOM; break; }
+        for (int i = 0; i < 8; ++i) {
+            e = cudaEventCreate(&ctx->ev[i]);
+            if (e != cudaSuccess) { set_err(nullptr, "event creation failed: %s", cudaGetErrorString(e)); rc = EF_ERR_CUDA; break; }
+        }
+        ctx->events = rc == EF_OK;
+    } while (0);
+    if (rc != EF_OK) {
+        ef_ctx_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return EF_OK;
+}
+
+int ef_ctx_destroy(ef_ctx *ctx) {
+    if (!ctx) return EF_OK;
+    DeviceGuard dg(ctx->device);
+    if (ctx->stream || ctx->scratch) cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->scratch);
+    cudaFree(ctx->ftab);
+    cudaFree(ctx->io);
+    if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    for (int i = 0; i < 8; ++i)
+        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    delete ctx;
+    return EF_OK;
+}
+
+const char *ef_last_error(const ef_ctx *ctx) { return ctx ? ctx->err : g_err; }
+
+int ef_sync(ef_ctx *ctx) {
+    if (!ctx) return EF_ERR_ARG;
+    DeviceGuard dg(ctx->device);
+    CU(cudaStreamSynchronize(ctx->stream));
+    return EF_OK;
+}
+
+int ef_get_stats(ef_ctx *ctx, ef_stats *out, int reset) {
+    if (!ctx || !out) return EF_ERR_ARG;
+    *out = ctx->stats;
+    if (reset) ctx->stats = ef_stats{};
+    return EF_OK;
+}
+
+int ef_compute_ex(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_options *opt, ef_outputs *out) {
+    if (!ctx) { set_err(nullptr, "null context"); return EF_ERR_ARG; }
+    ef_options o = {};
+    if (opt) o = *opt;
+    int rc = check_args(ctx, g, n, m, o, out);
+    if (rc) return rc;
+    ctx->err[0] = 0;
+    if (n == 0) return EF_OK;
+    DeviceGuard dg(ctx->device);
+    if (!o.host_io) {
+        rc = compute_device(ctx, g->row_ptr, g->col_idx, n, m, o, *out);
+    } else {
+        // device staging: row_ptr, col_idx, then every requested output
+        const size_t N = (size_t)n;
+        size_t off = 0;
+        auto slot = [&](size_t bytes) { size_t o_ = off; off += al(bytes); return o_; };
+        size_t o_rp = slot(4 * (N + 1)), o_ci = slot(4 * (size_t)(m + 1));
+        size_t o_ef = slot(8 * N), o_n = slot(8 * N), o_s = slot(8 * N), o_t = slot(8 * N), o_tr = slot(8 * N),
+               o_fl = slot(N);
+        rc = ensure_io(ctx, off);
+        if (rc) return rc;
+        char *b = (char *)ctx->io;
+        CU(cudaMemcpyAsync(b + o_rp, g->row_ptr, 4 * (N + 1), cudaMemcpyHostToDevice, ctx->stream));
+        if (m > 0) CU(cudaMemcpyAsync(b + o_ci, g->col_idx, 4 * (size_t)m, cudaMemcpyHostToDevice, ctx->stream));
+        ef_outputs dout = {};
+        dout.ef = out->ef ? (double *)(b + o_ef) : nullptr;
+        dout.n_clusters = out->n_clusters ? (int64_t *)(b + o_n) : nullptr;
+        dout.s = out->s ? (int64_t *)(b + o_s) : nullptr;
+        dout.t = out->t ? (double *)(b + o_t) : nullptr;
+        dout.triangles = out->triangles ? (int64_t *)(b + o_tr) : nullptr;
+        dout.flag = out->flag ? (uint8_t *)(b + o_fl) : nullptr;
+        rc = compute_device(ctx, (const int32_t *)(b + o_rp), (const int32_t *)(b + o_ci), n, m, o, dout);
+        if (rc) return rc;
+        if (out->ef) CU(cudaMemcpyAsync(out->ef, dout.ef, 8 * N, cudaMemcpyDeviceToHost, ctx->stream));
+        if (out->n_clusters) CU(cudaMemcpyAsync(out->n_clusters, dout.n_clusters, 8 * N, cudaMemcpyDeviceToHost, ctx->stream));
+        if (out->s) CU(cudaMemcpyAsync(out->s, dout.s, 8 * N, cudaMemcpyDeviceToHost, ctx->stream));
+        if (out->t) CU(cudaMemcpyAsync(out->t, dout.t, 8 * N, cudaMemcpyDeviceToHost, ctx->stream));
+        if (out->triangles) CU(cudaMemcpyAsync(out->triangles, dout.triangles, 8 * N, cudaMemcpyDeviceToHost, ctx->stream));
+        if (out->flag) CU(cudaMemcpyAsync(out->flag, dout.flag, N, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    if (rc) return rc;
+    if (!o.async) {
+        CU(cudaStreamSynchronize(ctx->stream));
+        if (o.profile) accumulate_stats(ctx);
+    }
+    CU(cudaGetLastError());
+    return EF_OK;
+}
+
+int ef_compute(const ef_csr *g, int32_t n, int64_t m, double *out_ef) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        set_err(nullptr, "no current CUDA device");
+        return EF_ERR_CUDA;
+    }
+    ef_ctx *ctx;
+    {
+        std::lock_guard<std::mutex> lk(g_default_mu);
+        if (!g_default[dev]) {
+            int rc = ef_ctx_create(dev, nullptr, &g_default[dev]);
+            if (rc) return rc;
+        }
+        ctx = g_default[dev];
+    }
+    ef_outputs out = {};
+    out.ef = out_ef;
+    int rc = ef_compute_ex(ctx, g, n, m, nullptr, &out);
+    if (rc) snprintf(g_err, sizeof g_err, "%s", ctx->err);
+    return rc;
+}
+
+}  // extern "C"

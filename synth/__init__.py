@@ -161,7 +161,14 @@ def from_edges(n: int, edges) -> Graph:
 # ---------------------------------------------------------------- families
 
 def complete(n: int) -> Graph:
-    return from_edges(n, [(i, j) for i in range(n) for j in range(i + 1, n)])
+    """K_n, built directly as CSR (row v = all other nodes, ascending)."""
+    if n <= 1:
+        return Graph(np.zeros(n + 1, np.int32), np.zeros(0, np.int32), f"K{n}")
+    cols = np.tile(np.arange(n, dtype=np.int32), n).reshape(n, n)
+    mask = ~np.eye(n, dtype=bool)
+    col_idx = cols[mask].astype(np.int32)
+    row_ptr = (np.arange(n + 1, dtype=np.int64) * (n - 1)).astype(np.int32)
+    return Graph(row_ptr, col_idx, f"K{n}")
 
 
 def star(k: int) -> Graph:
@@ -178,7 +185,13 @@ def cycle(n: int) -> Graph:
 
 
 def complete_bipartite(r: int, s: int) -> Graph:
-    return from_edges(r + s, [(i, r + j) for i in range(r) for j in range(s)])
+    """K_{r,s}: nodes 0..r-1 on one side, r..r+s-1 on the other; built directly as CSR."""
+    left = np.tile(np.arange(r, r + s, dtype=np.int32), r)
+    right = np.tile(np.arange(0, r, dtype=np.int32), s)
+    col_idx = np.concatenate([left, right]).astype(np.int32)
+    deg = np.concatenate([np.full(r, s, np.int64), np.full(s, r, np.int64)])
+    row_ptr = np.concatenate([[0], np.cumsum(deg)]).astype(np.int32)
+    return Graph(row_ptr, col_idx, f"K{r},{s}")
 
 
 def hypercube(k: int) -> Graph:

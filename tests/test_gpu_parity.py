@@ -1,0 +1,267 @@
+"""GPU parity: libef (through the C ABI) against the CPU oracle.
+
+Bar: cluster counts N_v, degree sums S_v, triangle counts t_v and degenerate
+flags bit-exact; EF within 1e-9 relative on the FP64 path and 2e-5 absolute on
+the FP32C path; T_v within 1e-10 relative (FP64) / 2e-6 relative (FP32C).
+Sizes span several tiles and work items and ragged tails; the full-size
+workloads are checked on sampled nodes (vertex-centric oracle) and on
+properties that hold at any size.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+EF_RTOL64 = 1e-9
+EF_ATOL32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2306_00606_gb300 as ef
+    c = ef.Context(0)
+    yield c
+    c.close()
+
+
+def run(ctx, g, precision, **kw):
+    import torch
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    out = ctx.compute(rp, ci, precision=precision,
+                      outputs=("ef", "n_clusters", "s", "t", "triangles", "flag"), **kw)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def assert_parity(got, ref, precision, nodes=None):
+    sel = (lambda a: a) if nodes is None else (lambda a: a[nodes])
+    np.testing.assert_array_equal(sel(got["n_clusters"]), ref["N"])
+    np.testing.assert_array_equal(sel(got["s"]), ref["S"])
+    np.testing.assert_array_equal(sel(got["flag"]), ref["flag"])
+    if "tri" in ref:
+        np.testing.assert_array_equal(sel(got["triangles"]), ref["tri"])
+    ef, ref_ef = sel(got["ef"]), ref["EF"]
+    if precision == "fp64":
+        np.testing.assert_allclose(ef, ref_ef, rtol=EF_RTOL64, atol=1e-12)
+        np.testing.assert_allclose(sel(got["t"]), ref["T"], rtol=1e-10, atol=1e-9)
+    else:
+        np.testing.assert_allclose(ef, ref_ef, rtol=0, atol=EF_ATOL32)
+        np.testing.assert_allclose(sel(got["t"]), ref["T"], rtol=2e-6, atol=1e-3)
+
+
+def alg1_ref(g):
+    r = oracle.alg1(g)
+    r["tri"] = oracle.triangles(g)
+    return r
+
+
+SPECIAL = {
+    "K3": lambda: synth.complete(3), "K4": lambda: synth.complete(4), "K9": lambda: synth.complete(9),
+    "K40": lambda: synth.complete(40), "K150": lambda: synth.complete(150),
+    "star2": lambda: synth.star(2), "star33": lambda: synth.star(33), "star5000": lambda: synth.star(5000),
+    "P5": lambda: synth.path(5), "C7": lambda: synth.cycle(7), "petersen": synth.petersen,
+    "Q10": lambda: synth.hypercube(10), "K40_40": lambda: synth.complete_bipartite(40, 40),
+    "K2+isolated": lambda: synth.from_edges(5, [(1, 3)]),
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+@pytest.mark.parametrize("name", list(SPECIAL))
+def test_special_graphs(ctx, name, precision):
+    g = SPECIAL[name]()
+    assert_parity(run(ctx, g, precision), alg1_ref(g), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_er_workload_1(ctx, precision):
+    """Erdos-Renyi G(2000, 0.004), the small workload, against literal Algorithm 1."""
+    g = synth.workload(1)
+    assert_parity(run(ctx, g, precision), alg1_ref(g), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_mixed_union(ctx, precision):
+    g = synth.disjoint_union([synth.erdos_renyi(700, 0.02, 3), synth.barabasi_albert(3000, 3, 4),
+                              synth.watts_strogatz(900, 8, 0.1, 5), synth.complete(3), synth.path(3),
+                              synth.star(70), synth.rmat(9, 8, 6), synth.from_edges(3, [])])
+    assert_parity(run(ctx, g, precision), alg1_ref(g), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_ba_many_work_items(ctx, precision):
+    """BA n=20000, m=5: hubs with several hundred neighbours -> several CTA work items each."""
+    g = synth.barabasi_albert(20000, 5, 11)
+    assert g.degrees.max() > 2 * 256
+    assert_parity(run(ctx, g, precision), alg1_ref(g), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_dense_triangles(ctx, precision):
+    """Dense random graph: many triangles, triangle owners above the warp capacity."""
+    g = synth.erdos_renyi(500, 0.5, 12)
+    ref = alg1_ref(g)
+    assert ref["tri"].max() > 1000
+    assert_parity(run(ctx, g, precision), ref, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_powerlaw_hubs_beyond_one_tile(ctx, precision):
+    """Power-law configuration model plus a hub joined to 5000 of its nodes: a middle node of
+    degree > 4096 (several shared-memory tiles) among power-law neighbours."""
+    g0 = synth.powerlaw_cm(20000, 2.3, 3, 1000, 13)
+    src = np.repeat(np.arange(g0.n), np.diff(g0.row_ptr))
+    e = np.stack([src, g0.col_idx], 1)
+    e = e[e[:, 0] < e[:, 1]]
+    spokes = np.random.default_rng(13).choice(g0.n, 5000, replace=False)
+    hub = np.stack([np.full(5000, g0.n), spokes], 1)
+    g = synth.from_edges(g0.n + 1, np.concatenate([e, hub]))
+    assert g.degrees.max() > 4096
+    ref = oracle.vertex(g)
+    ref["tri"] = ref["t"]
+    assert_parity(run(ctx, g, precision), ref, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_bipartite_closed_form_multi_tile(ctx, precision):
+    """K_{6200,6200}: triangle-free 6200-regular, so every cluster has d = 3r-4 and
+    EF = ln(2r(r-1)); degrees exceed one wedge tile and owners exceed one triangle tile."""
+    r = 6200
+    g = synth.complete_bipartite(r, r)
+    got = run(ctx, g, precision)
+    N = 2 * r * (r - 1)
+    assert np.all(got["n_clusters"] == N) and np.all(got["s"] == N * (3 * r - 4))
+    assert np.all(got["triangles"] == 0) and np.all(got["flag"] == 0)
+    tol = dict(rtol=EF_RTOL64, atol=0) if precision == "fp64" else dict(rtol=0, atol=EF_ATOL32)
+    np.testing.assert_allclose(got["ef"], math.log(N), **tol)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_complete_closed_form_large(ctx, precision):
+    """K_600: every cluster is a triangle of degree 3(n-3), EF = ln(2(n-1)(n-2))."""
+    n = 600
+    got = run(ctx, synth.complete(n), precision)
+    N = 2 * (n - 1) * (n - 2)
+    assert np.all(got["n_clusters"] == N) and np.all(got["s"] == N * 3 * (n - 3))
+    assert np.all(got["triangles"] == (n - 1) * (n - 2) // 2)
+    tol = dict(rtol=EF_RTOL64, atol=0) if precision == "fp64" else dict(rtol=0, atol=EF_ATOL32)
+    np.testing.assert_allclose(got["ef"], math.log(N), **tol)
+
+
+def _closed_counts(g):
+    d = g.degrees
+    src = np.repeat(np.arange(g.n), d)
+    sig1 = np.bincount(src, weights=d[g.col_idx], minlength=g.n).astype(np.int64)
+    return d * (d - 2) + sig1
+
+
+def _sample(g, k_random, k_hub, rng, hub_rank_lo=20):
+    d = g.degrees
+    order = np.argsort(-d, kind="stable")
+    hubs = order[hub_rank_lo:hub_rank_lo + 400][:: max(1, 400 // max(k_hub, 1))][:k_hub]
+    rnd = rng.choice(g.n, size=k_random, replace=False)
+    return np.unique(np.concatenate([hubs, rnd, [order[-1], 0, g.n - 1]])).astype(np.int32)
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+@pytest.mark.parametrize("idx", [2, 3])
+def test_full_size_workloads_sampled(ctx, idx, precision):
+    """BA n=1e6 m=5 and the power-law model n=4e6 at full size: every node's N_v
+    against its closed form, sum N = 4W, and sampled nodes (hubs included)
+    against the vertex-centric oracle."""
+    g = synth.workload(idx)
+    got = run(ctx, g, precision)
+    np.testing.assert_array_equal(got["n_clusters"], _closed_counts(g))
+    assert int(got["n_clusters"].sum()) == 4 * g.wedges()
+    assert int(got["triangles"].sum()) % 3 == 0
+    nodes = _sample(g, 48, 6, np.random.default_rng(idx))
+    ref = oracle.vertex(g, nodes)
+    ref["tri"] = ref["t"]
+    assert_parity(got, ref, precision, nodes=nodes)
+
+
+def test_fp32c_tracks_fp64(ctx):
+    g = synth.powerlaw_cm(200000, 2.3, 3, 3000, 21)
+    a = run(ctx, g, "fp64")
+    b = run(ctx, g, "fp32c")
+    np.testing.assert_array_equal(a["s"], b["s"])
+    np.testing.assert_allclose(b["ef"], a["ef"], rtol=0, atol=EF_ATOL32)
+
+
+def test_deterministic_fp64(ctx):
+    g = synth.workload(1)
+    a, b = run(ctx, g, "fp64"), run(ctx, g, "fp64")
+    assert np.array_equal(a["ef"], b["ef"])
+
+
+@pytest.mark.parametrize("bad", ["asym", "unsorted", "dup", "loop", "range", "rowptr"])
+def test_invalid_graphs_rejected(ctx, bad):
+    import torch
+    import paper_2306_00606_gb300 as ef
+    g = synth.erdos_renyi(300, 0.05, 2)
+    rp, ci = g.row_ptr.copy(), g.col_idx.copy()
+    v = int(np.argmax(np.diff(rp) >= 3))
+    a = rp[v]
+    if bad == "asym":
+        # replace one neighbour u of v by a non-neighbour x that keeps the row sorted:
+        # v now lists x (x does not list v) and u lists v (v does not list u)
+        row = set(ci[rp[v]:rp[v + 1]].tolist())
+        hi = ci[a + 1]
+        x = next(x for x in range(hi) if x != v and x not in row)
+        ci[a] = x
+        ci[rp[v]:rp[v + 1]] = np.sort(ci[rp[v]:rp[v + 1]])
+    elif bad == "unsorted":
+        ci[a], ci[a + 1] = ci[a + 1], ci[a]
+    elif bad == "dup":
+        ci[a + 1] = ci[a]
+    elif bad == "loop":
+        ci[a] = v
+        ci[rp[v]:rp[v + 1]] = np.sort(ci[rp[v]:rp[v + 1]])
+    elif bad == "range":
+        ci[rp[v + 1] - 1] = g.n + 5
+    elif bad == "rowptr":
+        rp[v + 1] = rp[v] - 1
+    with pytest.raises(ef.EfError) as ei:
+        ctx.compute(torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda(), outputs=("ef",))
+    assert ei.value.code == ef.EF_ERR_GRAPH
+
+
+def test_empty_graph(ctx):
+    import torch
+    out = ctx.compute(torch.zeros(1, dtype=torch.int32, device="cuda"),
+                      torch.zeros(0, dtype=torch.int32, device="cuda"), outputs=("ef",))
+    assert out["ef"].numel() == 0
+
+
+def test_host_io_matches_device(ctx):
+    import paper_2306_00606_gb300 as ef
+    g = synth.barabasi_albert(5000, 4, 3)
+    dev = run(ctx, g, "fp64")
+    host = {k: np.zeros(g.n, dt) for k, dt in (("ef", np.float64), ("s", np.int64), ("n_clusters", np.int64))}
+    ef.ef_compute_ex(ctx.handle, g.row_ptr, g.col_idx, precision="fp64", host_io=True, **host)
+    assert np.array_equal(host["ef"], dev["ef"]) and np.array_equal(host["s"], dev["s"])
+
+
+def test_plain_ef_compute_entry(ctx):
+    import torch
+    import paper_2306_00606_gb300 as ef
+    g = synth.workload(1)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    ef.ef_compute(rp, ci, out)
+    np.testing.assert_allclose(out.cpu().numpy(), oracle.alg1(g)["EF"], rtol=EF_RTOL64, atol=1e-12)
+
+
+def test_profile_stats(ctx):
+    g = synth.barabasi_albert(50000, 5, 1)
+    ctx.stats(reset=True)
+    run(ctx, g, "fp32c", profile=True)
+    st = ctx.stats(reset=True)
+    assert st["calls"] == 1 and st["total_ms"] > 0 and st["wedge_big_ms"] > 0
