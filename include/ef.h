@@ -132,6 +132,27 @@ int ef_compute(const ef_csr *g, int32_t n, int64_t m, double *out_ef);
 int ef_compute_ex(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
                   const ef_options *opt, ef_outputs *out);
 
+/*
+ * ef_compute_static: EF of every node with no memory allocation at all.
+ * The paper has no counterpart; this is for callers that cannot allocate
+ * device memory when they need EF (code inside a memory pool that owns the
+ * device, hosts that forbid cudaMalloc/cudaFree because they synchronise the
+ * device, real-time loops that must not touch an allocator).
+ *   g: CSR (device pointers), n, m as above; precision: enum ef_precision;
+ *   out_ef: double[n] (device); stream: a cudaStream_t (NULL = legacy
+ *   default stream) on the current device.  Synchronous: returns after the
+ *   stream has finished this call's work.  Input is validated.
+ * Scratch lives in a fixed 32 MiB device array inside the library, held by
+ * every GPU that loads it until the process exits.  Graphs whose scratch
+ * would exceed it (about 100 n + 36 m + 24 min(n, m) bytes) are rejected with
+ * EF_ERR_ARG and a message naming the limit; nothing runs on the GPU then.
+ * The first call on a device looks up the array's address (make it before
+ * any stream capture).  All calls share the array: calls that overlap on the
+ * GPU race and must be serialised by the caller.  Errors: ef_last_error(NULL).
+ */
+int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t precision,
+                      double *out_ef, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,7 @@ PRECISIONS = {"fp64": EF_PREC_FP64, "fp32c": EF_PREC_FP32C}
 
 # Every symbol include/ef.h declares (checked by the CPU test of the ABI).
 EXPORTED = ("ef_ctx_create", "ef_ctx_destroy", "ef_last_error", "ef_sync", "ef_get_stats",
-            "ef_compute", "ef_compute_ex")
+            "ef_compute", "ef_compute_ex", "ef_compute_static")
 
 
 class EfError(RuntimeError):
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ef_compute.argtypes = [ctypes.POINTER(ef_csr), i32, i64, vp]
     lib.ef_compute_ex.argtypes = [vp, ctypes.POINTER(ef_csr), i32, i64, ctypes.POINTER(ef_options),
                                   ctypes.POINTER(ef_outputs)]
+    lib.ef_compute_static.argtypes = [ctypes.POINTER(ef_csr), i32, i64, i32, vp, vp]
     for name in EXPORTED:
         if name != "ef_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -145,6 +146,14 @@ def ef_compute_ex(ctx: int, row_ptr, col_idx, *, precision: str = "fp64", ef=Non
     out = ef_outputs(_ptr(ef), _ptr(n_clusters), _ptr(s), _ptr(t), _ptr(triangles), _ptr(flag))
     _check(load_library().ef_compute_ex(ctx, ctypes.byref(g), n, int(col_idx.shape[0]), ctypes.byref(o),
                                         ctypes.byref(out)), ctx)
+
+
+def ef_compute_static(row_ptr, col_idx, out_ef, precision: str = "fp64", stream: int | None = None) -> None:
+    """EF of every node with no allocation (fixed 32 MiB library scratch); CUDA tensors, synchronous."""
+    n = int(row_ptr.shape[0]) - 1
+    g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
+    _check(load_library().ef_compute_static(ctypes.byref(g), n, int(col_idx.shape[0]), PRECISIONS[precision],
+                                            _ptr(out_ef), stream or None))
 
 
 # ---------------------------------------------------------------- convenience

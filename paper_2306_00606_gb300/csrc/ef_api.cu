@@ -246,6 +246,11 @@ ef_ctx *g_default[64];
 
 }  // namespace
 
+namespace ef {
+// Message for ef_last_error(NULL), for entry points that run without a context.
+void set_global_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace ef
+
 extern "C" {
 
 int ef_ctx_create(int device, void *stream, ef_ctx **out) {

@@ -1,0 +1,156 @@
+// ef_compute_static: EF of every node without allocating any memory.
+//
+// Some callers cannot allocate device memory at the point where they need EF:
+// code running inside a memory pool that owns the whole device, plug-ins whose
+// host forbids cudaMalloc/cudaFree (which synchronise the device and can
+// break its own allocator's accounting), and real-time loops that must not
+// touch the allocator at all.  For them this entry point runs the same passes
+// as ef_compute_ex, but on a fixed scratch area that is part of the library
+// image: a file-scope __device__ array of EF_STATIC_SCRATCH_BYTES (32 MiB),
+// which every GPU that loads libef holds until the process exits.
+//
+// Set-up: the first call on a device looks up the array's device address with
+// cudaGetSymbolAddress (with that device current) and caches it; make that
+// first call before any stream capture.  Afterwards a call only launches
+// kernels, memsets and one small device-to-host copy of the validation word
+// into a stack variable.  It calls no cudaMalloc, cudaFree, cudaMallocHost or
+// any other allocating routine.
+//
+// All calls share the one array and it keeps the previous call's contents;
+// everything that must start at zero is cleared by each call.  Two calls
+// whose work overlaps on the GPU (different streams, or different host
+// threads) race on the array and give wrong results: serialise them.
+#include "ef_internal.cuh"
+
+#include <mutex>
+#include <stdio.h>
+
+namespace ef {
+void set_global_error(const char *msg);
+}
+
+namespace {
+
+constexpr size_t EF_STATIC_SCRATCH_BYTES = (size_t)32 << 20;
+
+__device__ __align__(256) unsigned char g_static_scratch[EF_STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mu;
+void *g_static_addr[64];
+
+inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Same layout as the context scratch, plus the f(d) table at the end.
+size_t carve_static(char *base, int32_t n, int64_t m, int64_t fcap, ef::Scratch &s) {
+    using namespace ef;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        void *p = base ? base + off : nullptr;
+        off += al256(bytes);
+        return p;
+    };
+    const size_t N = (size_t)n, M = (size_t)m;
+    s.D = (int32_t *)take(4 * N);
+    s.sig1 = (int64_t *)take(8 * N);
+    s.sig2 = (int64_t *)take(8 * N);
+    s.omega = (int64_t *)take(8 * N);
+    s.outdeg = (int32_t *)take(4 * N);
+    s.out_ptr = (int32_t *)take(4 * (N + 1));
+    s.out_col = (int32_t *)take(4 * (M + 1));
+    s.out_D = (int32_t *)take(4 * (M + 1));
+    s.out_rslot = (int32_t *)take(4 * (M + 1));
+    s.rev = (int32_t *)take(4 * (M + 1));
+    s.slotR = take(8 * (M + 1));
+    s.slotC = (double *)take(8 * (M + 1));
+    s.slotT = (int32_t *)take(4 * (M + 1));
+    s.Ccenter = (double *)take(8 * N);
+    s.tri_own = (double *)take(8 * N);
+    s.t_own = (int64_t *)take(8 * N);
+    s.bins = (int32_t *)take(4 * N * NUM_BINS);
+    s.counters = (int32_t *)take(4 * 64);
+    s.big_chunks = (int32_t *)take(4 * (N + 1));
+    s.big_partial = (double *)take(8 * (M / BIG_ROWS + N + 2));
+    s.scan_tmp = (int32_t *)take(4 * (N / 4096 + 4));
+    s.ftab = (double *)take(8 * (size_t)fcap);
+    s.tri_gl = nullptr;
+    s.tri_gl_cap = 0;
+    return off;
+}
+
+int fail(int code, const char *msg) {
+    ef::set_global_error(msg);
+    return code;
+}
+
+}  // namespace
+
+extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t precision, double *out_ef,
+                                 void *stream) {
+    using namespace ef;
+    if (!g || !out_ef) return fail(EF_ERR_ARG, "ef_compute_static: null graph or output");
+    if (n < 0 || m < 0 || m >= ((int64_t)1 << 31)) return fail(EF_ERR_ARG, "ef_compute_static: bad sizes");
+    if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32C)
+        return fail(EF_ERR_ARG, "ef_compute_static: bad precision");
+    if (n == 0) return EF_OK;
+    if (!g->row_ptr || (m > 0 && !g->col_idx)) return fail(EF_ERR_ARG, "ef_compute_static: null CSR array");
+
+    // the f table is sized for the largest degree the graph can have
+    const int64_t bound = (int64_t)n - 1 < m ? (int64_t)n - 1 : m;
+    const int64_t fcap = 3 * (bound > 0 ? bound : 0) + 1;
+    Scratch s;
+    const size_t need = carve_static(nullptr, n, m, fcap, s);
+    if (need > EF_STATIC_SCRATCH_BYTES) {
+        char msg[200];
+        snprintf(msg, sizeof msg,
+                 "ef_compute_static: graph needs %zu bytes of scratch, above the fixed %zu-byte maximum "
+                 "(about 100 n + 36 m + 24 min(n, m) bytes); use ef_compute_ex",
+                 need, EF_STATIC_SCRATCH_BYTES);
+        return fail(EF_ERR_ARG, msg);
+    }
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return fail(EF_ERR_CUDA, "ef_compute_static: no current CUDA device");
+    void *base;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_addr[dev]) {
+            cudaError_t e = cudaGetSymbolAddress(&g_static_addr[dev], g_static_scratch);
+            if (e != cudaSuccess) {
+                g_static_addr[dev] = nullptr;
+                return fail(EF_ERR_CUDA, "ef_compute_static: cudaGetSymbolAddress failed");
+            }
+        }
+        base = g_static_addr[dev];
+    }
+    carve_static((char *)base, n, m, fcap, s);
+    int num_sms = 0;
+    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fail(EF_ERR_CUDA, "ef_compute_static: device query failed");
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t *rp = g->row_ptr, *ci = g->col_idx;
+    if (cudaMemsetAsync(s.counters, 0, 64 * sizeof(int32_t), st) != cudaSuccess)
+        return fail(EF_ERR_CUDA, "ef_compute_static: memset failed");
+    if (launch_prep_a(rp, ci, n, m, s, st) || launch_prep_b(rp, ci, n, m, s, st))
+        return fail(EF_ERR_CUDA, "ef_compute_static: prep launch failed");
+    int32_t h_cnt[64];
+    if (cudaMemcpyAsync(h_cnt, s.counters, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(EF_ERR_CUDA, "ef_compute_static: validation readback failed");
+    if (h_cnt[CNT_ERR]) return fail(EF_ERR_GRAPH, "ef_compute_static: input is not a symmetric simple sorted CSR");
+    ef_outputs out = {};
+    out.ef = out_ef;
+    if (launch_ftab(s.ftab, s.counters + CNT_MAXDEG, fcap, st) ||
+        cudaMemsetAsync(s.slotC, 0, (size_t)m * sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(s.slotT, 0, (size_t)m * sizeof(int32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(s.tri_own, 0, (size_t)n * sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(s.t_own, 0, (size_t)n * sizeof(int64_t), st) != cudaSuccess ||
+        launch_wedge_small(rp, ci, s, precision, n, st) ||
+        launch_wedge_big(rp, ci, s, precision, n, m, num_sms, st) || launch_triangles(s, n, num_sms, st) ||
+        launch_finalize(rp, ci, s, precision, n, out, st))
+        return fail(EF_ERR_CUDA, "ef_compute_static: launch failed");
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return fail(EF_ERR_CUDA, "ef_compute_static: kernel execution failed");
+    return EF_OK;
+}

@@ -1,0 +1,56 @@
+"""ef_compute_static: the entry point for callers that cannot allocate.
+
+Callers running inside a memory pool that owns the whole GPU, hosts that
+forbid cudaMalloc/cudaFree, or loops that must not touch an allocator, get EF
+from a fixed scratch array inside the library.  These tests call it through
+the C ABI and check it against ef_compute_ex on two calls in a row (the array
+keeps the previous call's contents, so the second call shows that everything
+that must start at zero is cleared), and that an oversized graph is refused
+before any GPU work.  This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _static(lib, ef_mod, rp, ci, out, precision):
+    g = ef_mod.ef_csr(rp.data_ptr(), ci.data_ptr())
+    return lib.ef_compute_static(ctypes.byref(g), rp.shape[0] - 1, ci.shape[0], precision, out.data_ptr(), None)
+
+
+def test_static_entry_matches_ef_compute_ex_twice():
+    import torch
+    import paper_2306_00606_gb300 as ef
+    lib = ef.load_library()
+    graphs = [synth.barabasi_albert(20000, 5, 31), synth.erdos_renyi(3000, 0.01, 32)]
+    with ef.Context(0) as ctx:
+        for g in graphs:
+            rp = torch.from_numpy(g.row_ptr).cuda()
+            ci = torch.from_numpy(g.col_idx).cuda()
+            for prec_name, prec, tol in (("fp64", 0, dict(rtol=1e-9, atol=1e-12)),
+                                         ("fp32c", 1, dict(rtol=0, atol=2e-5))):
+                ref = ctx.compute(rp, ci, precision=prec_name)["ef"].cpu().numpy()
+                for _ in range(2):
+                    out = torch.full((g.n,), -1.0, dtype=torch.float64, device="cuda")
+                    torch.cuda.synchronize()
+                    rc = _static(lib, ef, rp, ci, out, prec)
+                    assert rc == ef.EF_OK, ef.ef_last_error(None)
+                    np.testing.assert_allclose(out.cpu().numpy(), ref, **tol)
+
+
+def test_static_entry_rejects_oversized_graph():
+    import torch
+    import paper_2306_00606_gb300 as ef
+    lib = ef.load_library()
+    n, m = 2_000_000, 2_000_000
+    rp = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    ci = torch.zeros(m, dtype=torch.int32, device="cuda")
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    rc = _static(lib, ef, rp, ci, out, 0)
+    assert rc == ef.EF_ERR_ARG
+    assert "maximum" in ef.ef_last_error(None)
