@@ -39,10 +39,10 @@ namespace {
 
 thread_local char g_err[512];
 
-// Kernels one ef_compute_ex call launches: prep A 3, prep B 2 scans of 3 +
-// reverse fill + item counts, f table 1, small wedges 4, big wedges 2,
-// triangles 2, finalize 1.
-constexpr int64_t KERNELS_PER_CALL = 3 + 8 + 1 + 4 + 2 + 2 + 1;
+// Kernels one ef_compute_ex call launches (default wedge mode): prep A 3,
+// prep B 2 scans of 3 + reverse pairs 2 + orientation 2 + item counts,
+// f table 1, small wedges 4, class wedges 2, triangles 1, finalize 2.
+constexpr int64_t KERNELS_PER_CALL = 3 + 11 + 1 + 4 + 2 + 1 + 2;
 
 void set_err(ef_ctx *c, const char *fmt, ...) {
     char *dst = c ? c->err : g_err;
@@ -63,42 +63,6 @@ void set_err(ef_ctx *c, const char *fmt, ...) {
     } while (0)
 
 inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
-
-// Carve the per-call scratch; returns the bytes needed (and fills s when base != null).
-size_t carve(char *base, int32_t n, int64_t m, ef::Scratch &s) {
-    using namespace ef;
-    size_t off = 0;
-    auto take = [&](size_t bytes) -> void * {
-        void *p = base ? base + off : nullptr;
-        off += al(bytes);
-        return p;
-    };
-    const size_t N = (size_t)n, M = (size_t)m;
-    s.D = (int32_t *)take(4 * N);
-    s.sig1 = (int64_t *)take(8 * N);
-    s.sig2 = (int64_t *)take(8 * N);
-    s.omega = (int64_t *)take(8 * N);
-    s.outdeg = (int32_t *)take(4 * N);
-    s.out_ptr = (int32_t *)take(4 * (N + 1));
-    s.out_col = (int32_t *)take(4 * (M + 1));
-    s.out_D = (int32_t *)take(4 * (M + 1));
-    s.out_rslot = (int32_t *)take(4 * (M + 1));
-    s.rev = (int32_t *)take(4 * (M + 1));
-    s.slotR = take(8 * (M + 1));
-    s.slotC = (double *)take(8 * (M + 1));
-    s.slotT = (int32_t *)take(4 * (M + 1));
-    s.Ccenter = (double *)take(8 * N);
-    s.tri_own = (double *)take(8 * N);
-    s.t_own = (int64_t *)take(8 * N);
-    s.bins = (int32_t *)take(4 * N * NUM_BINS);
-    s.counters = (int32_t *)take(4 * 64);
-    s.big_chunks = (int32_t *)take(4 * (N + 1));
-    s.big_partial = (double *)take(8 * (M / BIG_ROWS + N + 2));
-    s.scan_tmp = (int32_t *)take(4 * (N / 4096 + 4));
-    s.tri_gl = nullptr;
-    s.tri_gl_cap = 0;
-    return off;
-}
 
 int ensure_scratch(ef_ctx *ctx, size_t bytes) {
     if (ctx->scratch_bytes >= bytes) return EF_OK;
@@ -166,25 +130,25 @@ int compute_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n,
                    const ef_outputs &out) {
     using namespace ef;
     cudaStream_t st = ctx->stream;
-    if (o.wedge_mode != 0 && o.wedge_mode != 1) {
+    if (o.wedge_mode < 0 || o.wedge_mode > 1) {
         set_err(ctx, "wedge_mode %d is not available", o.wedge_mode);
         return EF_ERR_UNSUPPORTED;
     }
     Scratch s;
-    size_t need = carve(nullptr, n, m, s);
+    size_t need = carve_scratch(nullptr, n, m, s);
     int rc = ensure_scratch(ctx, need);
     if (rc) return rc;
-    carve((char *)ctx->scratch, n, m, s);
+    carve_scratch((char *)ctx->scratch, n, m, s);
     const bool prof = o.profile != 0;
     if (prof) CU(cudaEventRecord(ctx->ev[0], st));
 
-    CU(cudaMemsetAsync(s.counters, 0, 64 * sizeof(int32_t), st));
+    CU(cudaMemsetAsync(s.counters, 0, NUM_COUNTERS * sizeof(int32_t), st));
     if (launch_prep_a(rp, ci, n, m, s, st)) { set_err(ctx, "prep A launch failed"); return EF_ERR_CUDA; }
     if (launch_prep_b(rp, ci, n, m, s, st)) { set_err(ctx, "prep B launch failed"); return EF_ERR_CUDA; }
 
     int64_t fcap;
     if (!o.trust_input) {
-        CU(cudaMemcpyAsync(ctx->h_counters, s.counters, 64 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(ctx->h_counters, s.counters, NUM_COUNTERS * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         int bits = ctx->h_counters[CNT_ERR];
         if (bits) {
@@ -201,19 +165,18 @@ int compute_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n,
     if (rc) return rc;
     s.ftab = ctx->ftab;
     if (launch_ftab(s.ftab, s.counters + CNT_MAXDEG, fcap, st)) { set_err(ctx, "f table launch failed"); return EF_ERR_CUDA; }
-    CU(cudaMemsetAsync(s.slotC, 0, (size_t)m * sizeof(double), st));
-    CU(cudaMemsetAsync(s.slotT, 0, (size_t)m * sizeof(int32_t), st));
-    CU(cudaMemsetAsync(s.tri_own, 0, (size_t)n * sizeof(double), st));
     CU(cudaMemsetAsync(s.t_own, 0, (size_t)n * sizeof(int64_t), st));
     if (prof) CU(cudaEventRecord(ctx->ev[1], st));
 
     if (launch_wedge_small(rp, ci, s, o.precision, n, st)) { set_err(ctx, "wedge small launch failed"); return EF_ERR_CUDA; }
     if (prof) CU(cudaEventRecord(ctx->ev[2], st));
-    if (launch_wedge_big(rp, ci, s, o.precision, n, m, ctx->num_sms, st)) { set_err(ctx, "wedge big launch failed"); return EF_ERR_CUDA; }
+    if (launch_wedge_big(rp, ci, s, o.precision, o.wedge_mode, n, m, ctx->num_sms, st)) { set_err(ctx, "wedge big launch failed"); return EF_ERR_CUDA; }
+    // the count slots served as the hubs' class indices during the wedge pass
+    CU(cudaMemsetAsync(s.slotT, 0, (size_t)m * sizeof(int32_t), st));
     if (prof) CU(cudaEventRecord(ctx->ev[3], st));
-    if (launch_triangles(s, n, ctx->num_sms, st)) { set_err(ctx, "triangle launch failed"); return EF_ERR_CUDA; }
+    if (launch_triangles(s, o.precision, n, m, ctx->num_sms, st)) { set_err(ctx, "triangle launch failed"); return EF_ERR_CUDA; }
     if (prof) CU(cudaEventRecord(ctx->ev[4], st));
-    if (launch_finalize(rp, ci, s, o.precision, n, out, st)) { set_err(ctx, "finalize launch failed"); return EF_ERR_CUDA; }
+    if (launch_finalize(rp, ci, s, o.precision, n, out, ctx->num_sms, st)) { set_err(ctx, "finalize launch failed"); return EF_ERR_CUDA; }
     if (prof) CU(cudaEventRecord(ctx->ev[5], st));
     return EF_OK;
 }
@@ -247,6 +210,40 @@ ef_ctx *g_default[64];
 }  // namespace
 
 namespace ef {
+
+size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        void *p = base ? base + off : nullptr;
+        off += al(bytes);
+        return p;
+    };
+    const size_t N = (size_t)n, M = (size_t)m;
+    s.D = (int32_t *)take(4 * N);
+    s.sig1 = (int64_t *)take(8 * N);
+    s.sig2 = (int64_t *)take(8 * N);
+    s.outdeg = (int32_t *)take(4 * N);
+    s.out_ptr = (int32_t *)take(4 * (N + 1));
+    s.out_col = (int32_t *)take(4 * (M + 1));
+    s.out_D = (int32_t *)take(4 * (M + 1));
+    s.out_rslot = (int32_t *)take(4 * (M + 1));
+    s.out_src = (int32_t *)take(4 * (M + 1));
+    s.rev = (int32_t *)take(4 * (M + 1));
+    s.slotR = take(8 * (M + 1));
+    s.slotT = (int32_t *)take(4 * (M + 1));
+    s.Ccenter = (double *)take(8 * N);
+    s.t_own = (int64_t *)take(8 * N);
+    s.bins = (int32_t *)take(4 * N * NUM_BINS);
+    s.counters = (int32_t *)take(4 * NUM_COUNTERS);
+    s.big_chunks = (int32_t *)take(4 * (N + 1));
+    s.big_partial = (double *)take(8 * (M / BIG_ROWS + N + 2));
+    s.scan_tmp = (int32_t *)take(4 * (N / 4096 + 4));
+    s.hub_cls = take(8 * (M + N + 2));
+    s.hub_q = take(8 * (M + N + 2));
+    s.ftab = nullptr;
+    return off;
+}
+
 // Message for ef_last_error(NULL), for entry points that run without a context.
 void set_global_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
 }  // namespace ef

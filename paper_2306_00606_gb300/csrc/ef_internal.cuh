@@ -14,6 +14,12 @@
 // middle, 1 + 1 as an end), all of degree sum - 6 instead of sum - 4, where
 // sum = D_a + D_b + D_c.  So each node of the triangle gets
 // 4 * (f(sum-6) - f(sum-4)) added to T and -8 added to S.
+//
+// Per-edge credits travel through "slots": the slot at position e of row v
+// (e in [row_ptr[v], row_ptr[v+1]), column u) holds what v receives from u:
+// the open-degree credit R_u(v) of u as a middle node, plus the triangle
+// corrections u found as a triangle owner.  Each slot has exactly one writer
+// per pass, so no slot needs an atomic in the warp-level kernels.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -34,56 +40,60 @@ enum : int {
     ERRB_ASYM = 16,     // x in N(u) but u not in N(x)
 };
 
-// Work bins.  Middle nodes are binned by degree for the wedge pass; triangle
-// owners (nodes with >= 2 out-neighbours in degree order) by out-degree.
+// Work bins (each a list of node ids of capacity n).
 enum : int {
-    BIN_S4 = 0,   // 1 <= D <= 4   (8 middle nodes per warp)
-    BIN_S8,       // 5..8          (4 per warp)
-    BIN_S16,      // 9..16         (2 per warp)
-    BIN_S32,      // 17..32        (1 per warp)
-    BIN_BIG,      // D > 32        (CTA work items)
-    BIN_TW,       // 2 <= out-degree <= TRI_WARP_CAP (warp per owner)
-    BIN_TC,       // out-degree > TRI_WARP_CAP (CTA per owner)
+    BIN_S4 = 0,    // 1 <= D <= 4   middle nodes, 8 per warp
+    BIN_S8,        // 5..8          4 per warp
+    BIN_S16,       // 9..16         2 per warp
+    BIN_S32,       // 17..32        1 per warp
+    BIN_BIG,       // D > 32        (finalize warp list; direct wedge kernel)
+    BIN_MID,       // 32 < D <= MID_MAX   degree-class wedge kernel, one warp each
+    BIN_HUB0,      // D > MID_MAX, bucket floor(log2 D) - 9, capped at NUM_HUB_BUCKETS-1
+    BIN_HUB_LAST = BIN_HUB0 + 6,
     NUM_BINS
 };
+constexpr int NUM_HUB_BUCKETS = BIN_HUB_LAST - BIN_HUB0 + 1;
 
 constexpr int SMALL_MAX = 32;
-constexpr int TRI_WARP_CAP = 128;
-constexpr int BIG_ROWS = 256;          // rows (neighbours) per big work item = threads per CTA
-constexpr int BIG_TILE = 4096;         // neighbour degrees staged in shared memory per tile
-constexpr int TRI_CTA_THREADS = 512;
-constexpr int TRI_CTA_SMEM_CAP = 6000; // out-neighbours per shared-memory tile of the CTA kernel (48000 B)
+constexpr int MID_MAX = 512;
+constexpr int MID_HIST = 256;          // dense degree histogram of the warp-level class kernel
+constexpr int HUB_HIST = 2048;         // dense degree histogram of the CTA-level class kernel
+constexpr int HUB_THREADS = 512;
+constexpr int HUB_SMEM_K = 4096;       // classes held in shared memory by the CTA kernel
+constexpr int BIG_ROWS = 256;          // rows per work item of the direct big-node kernel
+constexpr int BIG_TILE = 4096;         // neighbour degrees staged per tile by the direct kernel
+constexpr int ROW_CTA = 512;           // threads of the per-hub-row kernels
 
 // Scratch carved from one device allocation per call (sizes depend on n, m).
 struct Scratch {
     int32_t *D;          // n      degrees
     int64_t *sig1;       // n      sum of neighbour degrees
     int64_t *sig2;       // n      sum of squared neighbour degrees
-    int64_t *omega;      // n      sum of neighbours' sig1
-    int32_t *outdeg;     // n      out-degree in degree order
+    int32_t *outdeg;     // n      out-degree in (degree, id) order
     int32_t *out_ptr;    // n+1    oriented CSR offsets
-    int32_t *out_col;    // m/2+1  oriented neighbour ids (ascending id within a row)
-    int32_t *out_D;      // m/2+1  their degrees
-    int32_t *out_rslot;  // m/2+1  slot of the reverse entry (position of the owner in the neighbour's row)
-    int32_t *rev;        // m      rev[e] = position of u in N(x) for e = (u -> x)
-    void    *slotR;      // m      open-degree credit to the row owner from the column node as middle (float or double)
-    double  *slotC;      // m      triangle correction to the row owner found by the column node as owner
-    int32_t *slotT;      // m      triangle count credited the same way
-    double  *Ccenter;    // n      middle-node credit sum (2 * sum over pairs of f(d0))
-    double  *tri_own;    // n      triangle corrections found as owner (sum of f(s-6)-f(s-4))
+    int32_t *out_col;    // m+1    oriented neighbour ids (ascending id within a row)
+    int32_t *out_D;      // m+1    their degrees
+    int32_t *out_rslot;  // m+1    slot of the owner in the neighbour's row
+    int32_t *out_src;    // m+1    owner of each oriented edge
+    int32_t *rev;        // m+1    rev[e] = position of u in N(x) for e = (u -> x)
+    void    *slotR;      // m+1    credit to the row owner from the column node (float or double)
+    int32_t *slotT;      // m+1    triangles credited the same way
+    double  *Ccenter;    // n      middle-node credit + own triangle corrections
     int64_t *t_own;      // n      triangles found as owner
     int32_t *bins;       // NUM_BINS * n   work lists
-    int32_t *counters;   // 64 ints: [0..NUM_BINS) bin counts, [16] error word, [17] max degree,
-                         //          [18] big item counter, [19] triangle CTA counter, [20] timeout flag
-    int32_t *big_chunks; // n+1    work items per big middle node, then its exclusive scan
-    double  *big_partial;// m/BIG_ROWS + n + 1  per-item middle-node partial sums
+    int32_t *counters;   // 64 ints: [0..NUM_BINS) bin counts, CNT_* below
+    int32_t *big_chunks; // n+1    work items per big middle node (direct kernel), then their scan
+    double  *big_partial;// m/BIG_ROWS + n + 2  per-item middle-node partial sums (direct kernel)
     int32_t *scan_tmp;   // scan block sums
     double  *ftab;       // 3*maxdeg+1 (capacity): f(d) = d ln d in FP64
-    int32_t *tri_gl;     // global overflow arrays for huge triangle owners
-    int64_t tri_gl_cap;  // entries per CTA
+    void    *hub_cls;    // m+n+2  class (degree, count) pairs of hubs with > HUB_SMEM_K classes
+    void    *hub_q;      // m+n+2  their per-class credits
 };
 
-enum : int { CNT_ERR = 16, CNT_MAXDEG = 17, CNT_BIGITEM = 18, CNT_TRICTA = 19 };
+enum : int { CNT_ERR = 32, CNT_MAXDEG = 33, CNT_BIGITEM = 34, CNT_HUB = 36, CNT_NOUT = 37, NUM_COUNTERS = 64 };
+
+// Bytes of scratch for a graph (f table excluded), and its layout when base != nullptr.
+size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s);
 
 // ----------------------------------------------------------------- helpers
 __device__ __forceinline__ bool rank_less(int32_t Dx, int32_t x, int32_t Dy, int32_t y) {
@@ -106,6 +116,21 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int len, int32_
         if (a[mid] < key) lo = mid + 1; else hi = mid;
     }
     return lo;
+}
+
+// Total number of hub rows (degree > MID_MAX) in the hub buckets.
+__device__ __forceinline__ int hub_total(const int32_t *cnt) {
+    int t = 0;
+#pragma unroll
+    for (int b = 0; b < NUM_HUB_BUCKETS; ++b) t += cnt[BIN_HUB0 + b];
+    return t;
+}
+
+// The item-th hub row, largest degree bucket first (item < hub_total).
+__device__ __forceinline__ int hub_row(const int32_t *bins, int32_t n, const int32_t *cnt, int item) {
+    int b = NUM_HUB_BUCKETS - 1;
+    while (item >= cnt[BIN_HUB0 + b]) item -= cnt[BIN_HUB0 + b--];
+    return bins[(size_t)(BIN_HUB0 + b) * n + item];
 }
 
 // Kahan-compensated FP32 accumulation (compensation kept in c).
@@ -131,10 +156,10 @@ int launch_scan(const int32_t *in, int32_t *out, int32_t n, int32_t *tmp, cudaSt
 int launch_ftab(double *ftab, const int32_t *maxdeg_dev, int64_t cap, cudaStream_t st);
 int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
                        cudaStream_t st);
-int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
-                     int64_t m, int num_sms, cudaStream_t st);
-int launch_triangles(const Scratch &s, int32_t n, int num_sms, cudaStream_t st);
+int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int wedge_mode,
+                     int32_t n, int64_t m, int num_sms, cudaStream_t st);
+int launch_triangles(const Scratch &s, int precision, int32_t n, int64_t m, int num_sms, cudaStream_t st);
 int launch_finalize(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
-                    const ef_outputs &out, cudaStream_t st);
-size_t tri_cta_grid(int num_sms);
+                    const ef_outputs &out, int num_sms, cudaStream_t st);
+int hub_grid(int num_sms);
 }  // namespace ef

@@ -1,40 +1,114 @@
-// Preparation passes of libef: CSR validation, degrees, neighbour-degree sums,
-// work binning, degree orientation for triangle listing, reverse slots, the
-// f(d) = d ln d table, and a device-wide exclusive scan.
+// Preparation passes of libef: CSR validation, degrees and work bins,
+// neighbour-degree sums, reverse slots, degree orientation for triangle
+// listing, the f(d) = d ln d table, and a device-wide exclusive scan.
 //
 // Algorithm 1's Phase 2 needs |Adj(x)| of every cluster member; the degree
 // array D is the only per-node quantity the wedge pass reads besides the CSR.
+//
+// Row passes use three granularities so that no row's latency chain becomes
+// the tail of the pass: a thread per row of degree <= 32 (serial loop), a
+// warp per row of degree 33..MID_MAX, and a CTA per hub row (degree >
+// MID_MAX, listed by the degree kernel, largest first).
 #include "ef_internal.cuh"
 
 namespace ef {
 
-// ------------------------------------------------------------------ degrees
+// ------------------------------------------------------- block reductions
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *s_buf) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) s_buf[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        T t = lane < (int)(blockDim.x >> 5) ? s_buf[lane] : (T)0;
+        t = warp_sum(t);
+        if (lane == 0) s_buf[0] = t;
+    }
+    __syncthreads();
+    T r = s_buf[0];
+    __syncthreads();
+    return r;
+}
+
+// Block-wide exclusive scan of one int per thread (all threads must call).
+__device__ __forceinline__ int block_exclusive_scan(int x, int *total = nullptr) {
+    __shared__ int s_w[33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        int t = lane < nw ? s_w[lane] : 0;
+        int ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL, ti, o);
+            if (lane >= o) ti += y;
+        }
+        s_w[lane] = ti - t;   // exclusive offset of each warp
+        if (lane == 31) s_w[32] = ti;
+    }
+    __syncthreads();
+    int off = s_w[w];
+    if (total) *total = s_w[32];
+    __syncthreads();
+    return off + inc - x;
+}
+
+// --------------------------------------------------------- degrees + bins
+// Thread per node: D, max degree, row_ptr checks, and the wedge bins (they
+// depend on D only): small sub-warp bins, or "big" plus the mid list or a
+// hub bucket.  Block-level counting in shared memory, one global atomic per
+// bin per block.
 __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, int32_t *__restrict__ D,
-                          int32_t *__restrict__ cnt) {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    int mx = 0, err = 0;
+                          int32_t *__restrict__ bins, int32_t *__restrict__ cnt) {
+    __shared__ int s_cnt[NUM_BINS], s_base[NUM_BINS];
+    __shared__ int s_mx[32], s_err[32];
+    if (threadIdx.x < NUM_BINS) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    int mx = 0, err = 0, b0 = -1, b1 = -1, p0 = 0, p1 = 0;
     if (v < n) {
-        int a = rp[v], b = rp[v + 1];
-        if (a < 0 || b < a || (int64_t)b > m) {
-            err |= ERRB_ROWPTR;
-            D[v] = 0;
-        } else {
-            D[v] = b - a;
-            mx = b - a;
+        const int a = rp[v], b = rp[v + 1];
+        int d = 0;
+        if (a < 0 || b < a || (int64_t)b > m) err |= ERRB_ROWPTR;
+        else d = b - a;
+        D[v] = d;
+        mx = d;
+        if (d >= 1 && d <= SMALL_MAX) {
+            b0 = d <= 4 ? BIN_S4 : d <= 8 ? BIN_S8 : d <= 16 ? BIN_S16 : BIN_S32;
+        } else if (d > SMALL_MAX) {
+            b0 = BIN_BIG;
+            if (d <= MID_MAX) {
+                b1 = BIN_MID;
+            } else {
+                const int lg = 31 - __clz(d);   // floor(log2 d) >= 9
+                b1 = BIN_HUB0 + min(lg - 9, NUM_HUB_BUCKETS - 1);
+            }
         }
     }
     if (v == 0 && (rp[0] != 0 || (int64_t)rp[n] != m)) err |= ERRB_ROWPTR;
+    if (b0 >= 0) p0 = atomicAdd(&s_cnt[b0], 1);
+    if (b1 >= 0) p1 = atomicAdd(&s_cnt[b1], 1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mx = max(mx, __shfl_xor_sync(FULL, mx, o));
         err |= __shfl_xor_sync(FULL, err, o);
     }
-    __shared__ int s_mx[32], s_err[32];
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) { s_mx[w] = mx; s_err[w] = err; }
     __syncthreads();
+    if (threadIdx.x < NUM_BINS)
+        s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(cnt + threadIdx.x, s_cnt[threadIdx.x]) : 0;
     if (w == 0) {
-        int nw = blockDim.x >> 5;
+        const int nw = blockDim.x >> 5;
         mx = l < nw ? s_mx[l] : 0;
         err = l < nw ? s_err[l] : 0;
 #pragma unroll
@@ -47,133 +121,260 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
             if (err) atomicOr(cnt + CNT_ERR, err);
         }
     }
+    __syncthreads();
+    if (b0 >= 0) bins[(size_t)b0 * n + s_base[b0] + p0] = v;
+    if (b1 >= 0) bins[(size_t)b1 * n + s_base[b1] + p1] = v;
 }
 
 // ------------------------------------------- per-row checks and neighbour sums
-// One warp per row: range, self-loop and strict-order checks; sigma1, sigma2
-// and the out-degree of v in the (degree, id) order.
+// Range, self-loop and strict-order checks; sigma1 = sum of neighbour degrees,
+// sigma2 = sum of their squares, and the out-degree in (degree, id) order.
+struct RowStats {
+    int64_t s1 = 0, s2 = 0;
+    int od = 0, err = 0;
+    __device__ __forceinline__ void slot(const int32_t *__restrict__ ci, const int32_t *__restrict__ D, int32_t n,
+                                         int v, int Dv, int a, int e) {
+        const int x = ci[e];
+        if (x < 0 || x >= n) { err |= ERRB_RANGE; return; }
+        if (x == v) err |= ERRB_SELFLOOP;
+        if (e > a && ci[e - 1] >= x) err |= ERRB_UNSORTED;
+        const int Dx = D[x];
+        s1 += Dx;
+        s2 += (int64_t)Dx * Dx;
+        od += rank_less(Dv, v, Dx, x) ? 1 : 0;
+    }
+};
+
 __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
                             const int32_t *__restrict__ D, int64_t *__restrict__ sig1, int64_t *__restrict__ sig2,
                             int32_t *__restrict__ outdeg, int32_t *__restrict__ cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += nwarps) {
-        int a = rp[v], b = rp[v + 1];
-        bool ok = a >= 0 && a <= b && (int64_t)b <= m;
-        int Dv = ok ? b - a : 0;
-        int64_t s1 = 0, s2 = 0;
-        int od = 0, err = 0;
-        if (ok) {
-            for (int e = a + lane; e < b; e += 32) {
-                int x = ci[e];
-                if (x < 0 || x >= n) { err |= ERRB_RANGE; continue; }
-                if (x == (int)v) err |= ERRB_SELFLOOP;
-                if (e > a && ci[e - 1] >= x) err |= ERRB_UNSORTED;
-                int Dx = D[x];
-                s1 += Dx;
-                s2 += (int64_t)Dx * Dx;
-                od += rank_less(Dv, (int)v, Dx, x) ? 1 : 0;
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+         base += nwarps * 32) {
+        const int v = (int)(base + lane);
+        const bool in = base + lane < n;
+        const int a = in ? rp[v] : 0, b = in ? rp[v + 1] : 0;
+        const bool ok = in && a >= 0 && a <= b && (int64_t)b <= m;
+        const int Dv = ok ? b - a : 0;
+        if (in && Dv <= SMALL_MAX) {
+            RowStats r;
+            if (ok)
+                for (int e = a; e < b; ++e) r.slot(ci, D, n, v, Dv, a, e);
+            sig1[v] = r.s1;
+            sig2[v] = r.s2;
+            outdeg[v] = r.od;
+            if (r.err) atomicOr(cnt + CNT_ERR, r.err);
+        }
+        unsigned mid = __ballot_sync(FULL, Dv > SMALL_MAX && Dv <= MID_MAX);
+        while (mid) {
+            const int j = __ffs(mid) - 1;
+            mid &= mid - 1;
+            const int u = (int)(base + j);
+            const int ua = __shfl_sync(FULL, a, j), ub = __shfl_sync(FULL, b, j);
+            RowStats r;
+            for (int e = ua + lane; e < ub; e += 32) r.slot(ci, D, n, u, ub - ua, ua, e);
+            const int64_t s1 = warp_sum(r.s1), s2 = warp_sum(r.s2);
+            const int od = warp_sum(r.od);
+            const int err = __reduce_or_sync(FULL, r.err);
+            if (lane == 0) {
+                sig1[u] = s1;
+                sig2[u] = s2;
+                outdeg[u] = od;
+                if (err) atomicOr(cnt + CNT_ERR, err);
             }
         }
-        s1 = warp_sum(s1);
-        s2 = warp_sum(s2);
-        od = warp_sum(od);
-        err = __reduce_or_sync(FULL, err);
-        if (lane == 0) {
-            sig1[v] = s1;
-            sig2[v] = s2;
-            outdeg[v] = od;
-            if (err) atomicOr(cnt + CNT_ERR, err);
+    }
+}
+
+__global__ void __launch_bounds__(ROW_CTA) k_row_stats_hub(const int32_t *__restrict__ rp,
+                                                           const int32_t *__restrict__ ci, int32_t n,
+                                                           const int32_t *__restrict__ D,
+                                                           const int32_t *__restrict__ bins,
+                                                           int64_t *__restrict__ sig1, int64_t *__restrict__ sig2,
+                                                           int32_t *__restrict__ outdeg, int32_t *__restrict__ cnt) {
+    __shared__ int64_t s_buf[32];
+    const int total = hub_total(cnt);
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int u = hub_row(bins, n, cnt, it);
+        const int a = rp[u], b = rp[u + 1];
+        RowStats r;
+        for (int e = a + threadIdx.x; e < b; e += ROW_CTA) r.slot(ci, D, n, u, b - a, a, e);
+        const int64_t s1 = block_sum<int64_t>(r.s1, s_buf);
+        const int64_t s2 = block_sum<int64_t>(r.s2, s_buf);
+        const int64_t od = block_sum<int64_t>(r.od, s_buf);
+        const int err = __reduce_or_sync(FULL, r.err);
+        if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
+        if (threadIdx.x == 0) {
+            sig1[u] = s1;
+            sig2[u] = s2;
+            outdeg[u] = (int32_t)od;
         }
     }
 }
 
-// ------------------------------------------------------------------- binning
-__global__ void k_bin(const int32_t *__restrict__ D, const int32_t *__restrict__ outdeg, int32_t n,
-                      int32_t *__restrict__ bins, int32_t *__restrict__ cnt) {
-    __shared__ int s_cnt[NUM_BINS], s_base[NUM_BINS];
-    if (threadIdx.x < NUM_BINS) s_cnt[threadIdx.x] = 0;
-    __syncthreads();
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    int wb = -1, tb = -1, pw = 0, pt = 0;
-    if (v < n) {
-        int d = D[v];
-        if (d >= 1) wb = d <= 4 ? BIN_S4 : d <= 8 ? BIN_S8 : d <= 16 ? BIN_S16 : d <= SMALL_MAX ? BIN_S32 : BIN_BIG;
-        int o = outdeg[v];
-        if (o >= 2) tb = o <= TRI_WARP_CAP ? BIN_TW : BIN_TC;
+// ------------------------------------------------------------ reverse slots
+// Every undirected edge {v, x} is resolved once, from the row of its higher-
+// ranked end v: the lower-ranked end's row is the shorter one, so v is
+// binary-searched in N(x) and both directions are set, rev[e] = p and
+// rev[p] = e.  rev starts at -1; a slot left at -1, or a failed search,
+// means the input is not symmetric.  Rows and columns that failed validation
+// are skipped (memory safety only: the call returns EF_ERR_GRAPH before any
+// later pass runs).
+__device__ __forceinline__ int rev_slot(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
+                                        int64_t m, const int32_t *__restrict__ D, int32_t *__restrict__ rev, int v,
+                                        int Dv, int e) {
+    const int x = ci[e];
+    if (x < 0 || x >= n) return 0;
+    const int Dx = D[x];
+    if (!rank_less(Dx, x, Dv, v)) return 0;
+    const int xa = rp[x], xb = rp[x + 1];
+    if (!(xa >= 0 && xa <= xb && (int64_t)xb <= m)) return ERRB_ASYM;
+    const int pos = xa + lower_bound_i32(ci + xa, xb - xa, v);
+    if (pos < xb && ci[pos] == v) {
+        rev[e] = pos;
+        rev[pos] = e;
+        return 0;
     }
-    if (wb >= 0) pw = atomicAdd(&s_cnt[wb], 1);
-    if (tb >= 0) pt = atomicAdd(&s_cnt[tb], 1);
-    __syncthreads();
-    if (threadIdx.x < NUM_BINS) s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(cnt + threadIdx.x, s_cnt[threadIdx.x]) : 0;
-    __syncthreads();
-    if (wb >= 0) bins[(size_t)wb * n + s_base[wb] + pw] = v;
-    if (tb >= 0) bins[(size_t)tb * n + s_base[tb] + pt] = v;
+    return ERRB_ASYM;
 }
 
-// ------------------------------------------- reverse slots and orientation
-// One warp per row u.  For each slot e = (u -> x): rev[e] = position of u in
-// N(x) (binary search; missing -> asymmetric input); omega[u] = sum of
-// sigma1 over N(u); and the out-neighbours x of u in (degree, id) order are
-// appended to the oriented CSR in ascending id order, with D_x and rev[e].
-__global__ void k_rev_fill(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
-                           const int32_t *__restrict__ D, const int64_t *__restrict__ sig1,
-                           const int32_t *__restrict__ out_ptr, int32_t *__restrict__ rev,
-                           int32_t *__restrict__ out_col, int32_t *__restrict__ out_D,
-                           int32_t *__restrict__ out_rslot, int64_t *__restrict__ omega,
-                           int32_t *__restrict__ cnt) {
+__global__ void k_rev_pairs(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
+                            const int32_t *__restrict__ D, int32_t *__restrict__ rev, int32_t *__restrict__ cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t vv = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); vv < n; vv += nwarps) {
-        const int v = (int)vv;
-        const int a = rp[v], b = rp[v + 1];
-        // rows and columns that failed validation are skipped (memory safety
-        // only: the call returns EF_ERR_GRAPH before any later pass runs)
-        const bool ok = a >= 0 && a <= b && (int64_t)b <= m;
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+         base += nwarps * 32) {
+        const int v = (int)(base + lane);
+        const bool in = base + lane < n;
+        const int a = in ? rp[v] : 0, b = in ? rp[v + 1] : 0;
+        const bool ok = in && a >= 0 && a <= b && (int64_t)b <= m;
         const int Dv = ok ? b - a : 0;
-        int base = out_ptr[v];
-        int64_t om = 0;
         int err = 0;
-        for (int e0 = a; ok && e0 < b; e0 += 32) {
-            int e = e0 + lane;
-            bool act = e < b;
-            int x = act ? ci[e] : 0;
-            bool xin = act && x >= 0 && x < n;
-            int Dx = xin ? D[x] : 0;
-            int p = e;
-            if (act) {
-                int xa = xin ? rp[x] : 0, xb = xin ? rp[x + 1] : 0;
-                if (xin && xa >= 0 && xa <= xb && (int64_t)xb <= m) {
-                    int pos = xa + lower_bound_i32(ci + xa, xb - xa, v);
-                    if (pos < xb && ci[pos] == v) p = pos;
-                    else err |= ERRB_ASYM;
-                    om += sig1[x];
-                } else {
-                    err |= ERRB_ASYM;
-                }
-                rev[e] = p;
-            }
-            bool isout = xin && rank_less(Dv, v, Dx, x);
-            unsigned bal = __ballot_sync(FULL, isout);
-            if (isout) {
-                int k = base + __popc(bal & ((1u << lane) - 1u));
-                out_col[k] = x;
-                out_D[k] = Dx;
-                out_rslot[k] = p;
-            }
-            base += __popc(bal);
+        if (ok && Dv <= SMALL_MAX)
+            for (int e = a; e < b; ++e) err |= rev_slot(rp, ci, n, m, D, rev, v, Dv, e);
+        unsigned mid = __ballot_sync(FULL, Dv > SMALL_MAX && Dv <= MID_MAX);
+        while (mid) {
+            const int j = __ffs(mid) - 1;
+            mid &= mid - 1;
+            const int u = (int)(base + j);
+            const int ua = __shfl_sync(FULL, a, j), ub = __shfl_sync(FULL, b, j);
+            for (int e = ua + lane; e < ub; e += 32) err |= rev_slot(rp, ci, n, m, D, rev, u, ub - ua, e);
         }
-        om = warp_sum(om);
         err = __reduce_or_sync(FULL, err);
-        if (lane == 0) {
-            omega[v] = om;
-            if (err) atomicOr(cnt + CNT_ERR, err);
-        }
+        if (lane == 0 && err) atomicOr(cnt + CNT_ERR, err);
     }
 }
 
-// Work items of the big middle nodes: ceil(D / BIG_ROWS) each; entries past
-// the bin count are 0 so a scan over n gives the item offsets.
+__global__ void __launch_bounds__(ROW_CTA) k_rev_pairs_hub(const int32_t *__restrict__ rp,
+                                                           const int32_t *__restrict__ ci, int32_t n, int64_t m,
+                                                           const int32_t *__restrict__ D,
+                                                           const int32_t *__restrict__ bins,
+                                                           int32_t *__restrict__ rev, int32_t *__restrict__ cnt) {
+    const int total = hub_total(cnt);
+    int err = 0;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int u = hub_row(bins, n, cnt, it);
+        const int a = rp[u], b = rp[u + 1];
+        for (int e = a + threadIdx.x; e < b; e += ROW_CTA) err |= rev_slot(rp, ci, n, m, D, rev, u, b - a, e);
+    }
+    err = __reduce_or_sync(FULL, err);
+    if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
+}
+
+// ------------------------------------------------------------- orientation
+// Checks that every slot was paired and appends the out-neighbours x of u
+// (in (degree, id) order) to the oriented CSR in ascending id order, with
+// D_x, the slot of u in x's row (rev[e]) and the owner u.
+struct Orient {
+    const int32_t *ci, *D, *rev;
+    int32_t *out_col, *out_D, *out_rslot, *out_src;
+    int32_t n;
+    __device__ __forceinline__ bool probe(int u, int Du, int e, int &x, int &Dx, int &r, int &err) const {
+        x = ci[e];
+        const bool xin = x >= 0 && x < n;
+        Dx = xin ? D[x] : 0;
+        r = rev[e];
+        if (r < 0) {
+            err |= ERRB_ASYM;
+            r = e;
+        }
+        return xin && rank_less(Du, u, Dx, x);
+    }
+    __device__ __forceinline__ void put(int k, int u, int x, int Dx, int r) const {
+        out_col[k] = x;
+        out_D[k] = Dx;
+        out_rslot[k] = r;
+        out_src[k] = u;
+    }
+};
+
+__global__ void k_orient(const int32_t *__restrict__ rp, int32_t n, int64_t m, Orient o,
+                         const int32_t *__restrict__ out_ptr, int32_t *__restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+         base += nwarps * 32) {
+        const int v = (int)(base + lane);
+        const bool in = base + lane < n;
+        const int a = in ? rp[v] : 0, b = in ? rp[v + 1] : 0;
+        const bool ok = in && a >= 0 && a <= b && (int64_t)b <= m;
+        const int Dv = ok ? b - a : 0;
+        int err = 0;
+        if (ok && Dv <= SMALL_MAX) {
+            int k = out_ptr[v];
+            for (int e = a; e < b; ++e) {
+                int x, Dx, r;
+                if (o.probe(v, Dv, e, x, Dx, r, err)) o.put(k++, v, x, Dx, r);
+            }
+        }
+        unsigned mid = __ballot_sync(FULL, Dv > SMALL_MAX && Dv <= MID_MAX);
+        while (mid) {
+            const int j = __ffs(mid) - 1;
+            mid &= mid - 1;
+            const int u = (int)(base + j);
+            const int ua = __shfl_sync(FULL, a, j), ub = __shfl_sync(FULL, b, j);
+            int k0 = out_ptr[u];
+            for (int e0 = ua; e0 < ub; e0 += 32) {
+                const int e = e0 + lane;
+                int x = 0, Dx = 0, r = 0;
+                const bool isout = e < ub && o.probe(u, ub - ua, e, x, Dx, r, err);
+                const unsigned bal = __ballot_sync(FULL, isout);
+                if (isout) o.put(k0 + __popc(bal & ((1u << lane) - 1u)), u, x, Dx, r);
+                k0 += __popc(bal);
+            }
+        }
+        err = __reduce_or_sync(FULL, err);
+        if (lane == 0 && err) atomicOr(cnt + CNT_ERR, err);
+    }
+}
+
+__global__ void __launch_bounds__(ROW_CTA) k_orient_hub(const int32_t *__restrict__ rp, int32_t n, Orient o,
+                                                        const int32_t *__restrict__ bins,
+                                                        const int32_t *__restrict__ out_ptr,
+                                                        int32_t *__restrict__ cnt) {
+    const int total = hub_total(cnt);
+    int err = 0;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int u = hub_row(bins, n, cnt, it);
+        const int a = rp[u], b = rp[u + 1];
+        int k0 = out_ptr[u];
+        for (int e0 = a; e0 < b; e0 += ROW_CTA) {
+            const int e = e0 + threadIdx.x;
+            int x = 0, Dx = 0, r = 0;
+            const bool isout = e < b && o.probe(u, b - a, e, x, Dx, r, err);
+            int tot;
+            const int off = block_exclusive_scan(isout ? 1 : 0, &tot);
+            if (isout) o.put(k0 + off, u, x, Dx, r);
+            k0 += tot;
+        }
+    }
+    err = __reduce_or_sync(FULL, err);
+    if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
+}
+
+// Work items of the big middle nodes for the direct kernel: ceil(D / BIG_ROWS)
+// each; entries past the bin count are 0 so a scan over n gives the offsets.
 __global__ void k_big_chunks(const int32_t *__restrict__ D, const int32_t *__restrict__ big_list,
                              const int32_t *__restrict__ cnt, int32_t n, int32_t *__restrict__ chunks) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -195,36 +396,8 @@ constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_PER = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER;
 
-// Block-wide exclusive scan of one int per thread (all threads must call).
-__device__ __forceinline__ int block_exclusive_scan(int x) {
-    __shared__ int s_w[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_w[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        int nw = blockDim.x >> 5;
-        int t = lane < nw ? s_w[lane] : 0;
-        int ti = t;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(FULL, ti, o);
-            if (lane >= o) ti += y;
-        }
-        s_w[lane] = ti - t;   // exclusive offset of each warp
-    }
-    __syncthreads();
-    int off = s_w[w];
-    __syncthreads();
-    return off + inc - x;
-}
-
 __global__ void k_scan_reduce(const int32_t *__restrict__ in, int32_t n, int32_t *__restrict__ bsum) {
+    __shared__ int s_buf[32];
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     int s = 0;
 #pragma unroll
@@ -232,15 +405,8 @@ __global__ void k_scan_reduce(const int32_t *__restrict__ in, int32_t n, int32_t
         int64_t idx = base + (int64_t)threadIdx.x * SCAN_PER + i;
         if (idx < n) s += in[idx];
     }
-    s = warp_sum(s);
-    __shared__ int s_w[32];
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        int t = threadIdx.x < (blockDim.x >> 5) ? s_w[threadIdx.x] : 0;
-        t = warp_sum(t);
-        if (threadIdx.x == 0) bsum[blockIdx.x] = t;
-    }
+    s = block_sum<int>(s, s_buf);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = s;
 }
 
 // Single block: exclusive scan of the nb block sums in place.
@@ -303,20 +469,24 @@ static inline unsigned grid_for(int64_t work, int per_block, int64_t cap) {
     return (unsigned)g;
 }
 
-// Validation, degrees, neighbour sums, out-degrees and bins.
+// Degrees + wedge bins, per-row checks and neighbour sums.
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
-    k_degrees<<<grid_for(n, 256, 1 << 30), 256, 0, st>>>(rp, n, m, s.D, s.counters);
-    k_row_stats<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, s.sig1, s.sig2, s.outdeg, s.counters);
-    k_bin<<<grid_for(n, 1024, 1 << 30), 1024, 0, st>>>(s.D, s.outdeg, n, s.bins, s.counters);
+    k_degrees<<<grid_for(n, 1024, 1 << 30), 1024, 0, st>>>(rp, n, m, s.D, s.bins, s.counters);
+    k_row_stats<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, s.sig1, s.sig2, s.outdeg, s.counters);
+    k_row_stats_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, ci, n, s.D, s.bins, s.sig1, s.sig2, s.outdeg, s.counters);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Oriented CSR, reverse slots, omega, big-item offsets.
+// Reverse slots, oriented CSR, big-item offsets (direct kernel).
 int launch_prep_b(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
+    if (cudaMemsetAsync(s.rev, 0xff, (size_t)m * sizeof(int32_t), st) != cudaSuccess) return -1;
     if (launch_scan(s.outdeg, s.out_ptr, n, s.scan_tmp, st)) return -1;
-    k_rev_fill<<<grid_for(n, 8, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, s.sig1, s.out_ptr, s.rev, s.out_col, s.out_D,
-                                                         s.out_rslot, s.omega, s.counters);
-    // outdeg is free after the scan: reuse it for the big-item counts
+    k_rev_pairs<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, s.rev, s.counters);
+    k_rev_pairs_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, ci, n, m, s.D, s.bins, s.rev, s.counters);
+    Orient o{ci, s.D, s.rev, s.out_col, s.out_D, s.out_rslot, s.out_src, n};
+    k_orient<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, n, m, o, s.out_ptr, s.counters);
+    k_orient_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters);
+    // outdeg is free after the scan: reuse it for the direct kernel's item counts
     k_big_chunks<<<grid_for(n, 256, 1 << 30), 256, 0, st>>>(s.D, s.bins + (size_t)BIN_BIG * n, s.counters, n, s.outdeg);
     if (launch_scan(s.outdeg, s.big_chunks, n, s.scan_tmp, st)) return -1;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -40,43 +40,6 @@ void *g_static_addr[64];
 
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Same layout as the context scratch, plus the f(d) table at the end.
-size_t carve_static(char *base, int32_t n, int64_t m, int64_t fcap, ef::Scratch &s) {
-    using namespace ef;
-    size_t off = 0;
-    auto take = [&](size_t bytes) -> void * {
-        void *p = base ? base + off : nullptr;
-        off += al256(bytes);
-        return p;
-    };
-    const size_t N = (size_t)n, M = (size_t)m;
-    s.D = (int32_t *)take(4 * N);
-    s.sig1 = (int64_t *)take(8 * N);
-    s.sig2 = (int64_t *)take(8 * N);
-    s.omega = (int64_t *)take(8 * N);
-    s.outdeg = (int32_t *)take(4 * N);
-    s.out_ptr = (int32_t *)take(4 * (N + 1));
-    s.out_col = (int32_t *)take(4 * (M + 1));
-    s.out_D = (int32_t *)take(4 * (M + 1));
-    s.out_rslot = (int32_t *)take(4 * (M + 1));
-    s.rev = (int32_t *)take(4 * (M + 1));
-    s.slotR = take(8 * (M + 1));
-    s.slotC = (double *)take(8 * (M + 1));
-    s.slotT = (int32_t *)take(4 * (M + 1));
-    s.Ccenter = (double *)take(8 * N);
-    s.tri_own = (double *)take(8 * N);
-    s.t_own = (int64_t *)take(8 * N);
-    s.bins = (int32_t *)take(4 * N * NUM_BINS);
-    s.counters = (int32_t *)take(4 * 64);
-    s.big_chunks = (int32_t *)take(4 * (N + 1));
-    s.big_partial = (double *)take(8 * (M / BIG_ROWS + N + 2));
-    s.scan_tmp = (int32_t *)take(4 * (N / 4096 + 4));
-    s.ftab = (double *)take(8 * (size_t)fcap);
-    s.tri_gl = nullptr;
-    s.tri_gl_cap = 0;
-    return off;
-}
-
 int fail(int code, const char *msg) {
     ef::set_global_error(msg);
     return code;
@@ -98,12 +61,12 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     const int64_t bound = (int64_t)n - 1 < m ? (int64_t)n - 1 : m;
     const int64_t fcap = 3 * (bound > 0 ? bound : 0) + 1;
     Scratch s;
-    const size_t need = carve_static(nullptr, n, m, fcap, s);
+    const size_t need = carve_scratch(nullptr, n, m, s) + al256(8 * (size_t)fcap);
     if (need > EF_STATIC_SCRATCH_BYTES) {
         char msg[200];
         snprintf(msg, sizeof msg,
                  "ef_compute_static: graph needs %zu bytes of scratch, above the fixed %zu-byte maximum "
-                 "(about 100 n + 36 m + 24 min(n, m) bytes); use ef_compute_ex",
+                 "(about 128 n + 52 m + 24 min(n, m) bytes); use ef_compute_ex",
                  need, EF_STATIC_SCRATCH_BYTES);
         return fail(EF_ERR_ARG, msg);
     }
@@ -123,18 +86,18 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
         }
         base = g_static_addr[dev];
     }
-    carve_static((char *)base, n, m, fcap, s);
+    s.ftab = (double *)((char *)base + carve_scratch((char *)base, n, m, s));
     int num_sms = 0;
     if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: device query failed");
 
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t *rp = g->row_ptr, *ci = g->col_idx;
-    if (cudaMemsetAsync(s.counters, 0, 64 * sizeof(int32_t), st) != cudaSuccess)
+    if (cudaMemsetAsync(s.counters, 0, NUM_COUNTERS * sizeof(int32_t), st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: memset failed");
     if (launch_prep_a(rp, ci, n, m, s, st) || launch_prep_b(rp, ci, n, m, s, st))
         return fail(EF_ERR_CUDA, "ef_compute_static: prep launch failed");
-    int32_t h_cnt[64];
+    int32_t h_cnt[NUM_COUNTERS];
     if (cudaMemcpyAsync(h_cnt, s.counters, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: validation readback failed");
@@ -142,13 +105,12 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     ef_outputs out = {};
     out.ef = out_ef;
     if (launch_ftab(s.ftab, s.counters + CNT_MAXDEG, fcap, st) ||
-        cudaMemsetAsync(s.slotC, 0, (size_t)m * sizeof(double), st) != cudaSuccess ||
-        cudaMemsetAsync(s.slotT, 0, (size_t)m * sizeof(int32_t), st) != cudaSuccess ||
-        cudaMemsetAsync(s.tri_own, 0, (size_t)n * sizeof(double), st) != cudaSuccess ||
         cudaMemsetAsync(s.t_own, 0, (size_t)n * sizeof(int64_t), st) != cudaSuccess ||
         launch_wedge_small(rp, ci, s, precision, n, st) ||
-        launch_wedge_big(rp, ci, s, precision, n, m, num_sms, st) || launch_triangles(s, n, num_sms, st) ||
-        launch_finalize(rp, ci, s, precision, n, out, st))
+        launch_wedge_big(rp, ci, s, precision, 0, n, m, num_sms, st) ||
+        cudaMemsetAsync(s.slotT, 0, (size_t)m * sizeof(int32_t), st) != cudaSuccess ||
+        launch_triangles(s, precision, n, m, num_sms, st) ||
+        launch_finalize(rp, ci, s, precision, n, out, num_sms, st))
         return fail(EF_ERR_CUDA, "ef_compute_static: launch failed");
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: kernel execution failed");

@@ -160,6 +160,292 @@ __global__ void k_big_reduce(const int32_t *__restrict__ list, const int32_t *__
     }
 }
 
+// ------------------------------------------------- degree-class wedge kernels
+// For a middle node u, R_u(x) depends on its end x only through D_x:
+//     R_u(x) = Q_u(D_x) - f(D_u - 4 + 2 D_x),
+//     Q_u(a) = sum_b c_u(b) f(D_u - 4 + a + b),
+// where c_u(b) is the number of neighbours of u of degree b, and the middle
+// node's credit is sum_a c_u(a) R_u(a).  So u costs K_u^2 evaluations of f
+// (K_u = distinct neighbour degrees) instead of D_u^2.  The classes are
+// found with a dense histogram over small degrees plus one class per
+// neighbour of large degree (duplicates among those stay separate classes:
+// still exact, only a little redundant work).
+
+// Per-class arithmetic: FP32C keeps (degree, count) as floats and sums
+// count * d log2 d with Kahan compensation; FP64 keeps them as ints and sums
+// count * f(d) from the FP64 table.
+template <bool F64>
+struct ClassEval;
+
+template <>
+struct ClassEval<false> {
+    using Cls = float2;
+    using R = float;
+    static __device__ __forceinline__ Cls make(int b, int c) { return make_float2((float)b, (float)c); }
+    static __device__ __forceinline__ float bval(Cls x) { return x.x; }
+    static __device__ __forceinline__ float cval(Cls x) { return x.y; }
+    // returns R = (sum_j c_j f(base + b_i + b_j) - f(base + 2 b_i)) in natural-log units
+    static __device__ __forceinline__ float row(const Cls *cls, int K, int base, Cls ci, const double *) {
+        const float fb = (float)base + ci.x;
+        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+        int j = 0;
+        for (; j + 2 <= K; j += 2) {
+            const float4 q = *reinterpret_cast<const float4 *>(cls + j);
+            kahan_add(s0, c0, q.y * dlog2d(fb + q.x));
+            kahan_add(s1, c1, q.w * dlog2d(fb + q.z));
+        }
+        if (j < K) kahan_add(s0, c0, cls[j].y * dlog2d(fb + cls[j].x));
+        const double sum = ((double)s0 - (double)c0) + ((double)s1 - (double)c1);
+        return (float)((sum - (double)dlog2d(fb + ci.x)) * LN2);
+    }
+};
+
+template <>
+struct ClassEval<true> {
+    using Cls = int2;
+    using R = double;
+    static __device__ __forceinline__ Cls make(int b, int c) { return make_int2(b, c); }
+    static __device__ __forceinline__ int bval(Cls x) { return x.x; }
+    static __device__ __forceinline__ int cval(Cls x) { return x.y; }
+    static __device__ __forceinline__ double row(const Cls *cls, int K, int base, Cls ci, const double *ftab) {
+        const int fb = base + ci.x;
+        double s0 = 0.0, s1 = 0.0;
+        int j = 0;
+        for (; j + 2 <= K; j += 2) {
+            const int4 q = *reinterpret_cast<const int4 *>(cls + j);
+            s0 = fma((double)q.y, __ldg(ftab + (fb + q.x)), s0);
+            s1 = fma((double)q.w, __ldg(ftab + (fb + q.z)), s1);
+        }
+        if (j < K) s0 = fma((double)cls[j].y, __ldg(ftab + (fb + cls[j].x)), s0);
+        return (s0 + s1) - __ldg(ftab + (fb + ci.x));
+    }
+};
+
+constexpr int MID_WARPS = 4;
+
+// One warp per middle node of degree 33..MID_MAX.
+template <bool F64>
+__global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
+    const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
+    const int32_t *__restrict__ rev, const int32_t *__restrict__ list, const int32_t *__restrict__ cnt,
+    const double *__restrict__ ftab, void *__restrict__ slot_, double *__restrict__ Ccenter) {
+    using E = ClassEval<F64>;
+    using Cls = typename E::Cls;
+    using R = typename E::R;
+    R *slot = reinterpret_cast<R *>(slot_);
+    __shared__ int32_t s_hist[MID_WARPS][MID_HIST];
+    __shared__ int32_t s_cidx[MID_WARPS][MID_MAX];
+    __shared__ __align__(16) Cls s_cls[MID_WARPS][MID_MAX];
+    __shared__ R s_q[MID_WARPS][MID_MAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t *hist = s_hist[w], *cidx = s_cidx[w];
+    Cls *cls = s_cls[w];
+    R *cq = s_q[w];
+    const unsigned lt = (1u << lane) - 1u;
+    const int count = cnt[BIN_MID];
+    const int64_t nwarps = (int64_t)gridDim.x * MID_WARPS;
+    for (int64_t it = (int64_t)blockIdx.x * MID_WARPS + w; it < count; it += nwarps) {
+        const int u = list[it];
+        const int start = rp[u];
+        const int Du = rp[u + 1] - start;
+        const int base = Du - 4;
+        for (int i = lane; i < MID_HIST; i += 32) hist[i] = 0;
+        __syncwarp();
+        for (int k = lane; k < Du; k += 32) {
+            const int a = D[ci[start + k]];
+            cidx[k] = a;
+            if (a < MID_HIST) atomicAdd(hist + a, 1);
+        }
+        __syncwarp();
+        int K = 0;
+        for (int i0 = 0; i0 < MID_HIST; i0 += 32) {
+            const int i = i0 + lane;
+            const int c = hist[i];
+            const unsigned bal = __ballot_sync(FULL, c > 0);
+            if (c > 0) {
+                const int idx = K + __popc(bal & lt);
+                cls[idx] = E::make(i, c);
+                hist[i] = idx;
+            }
+            K += __popc(bal);
+        }
+        __syncwarp();
+        for (int k0 = 0; k0 < Du; k0 += 32) {
+            const int k = k0 + lane;
+            const bool act = k < Du;
+            const int a = act ? cidx[k] : 0;
+            const bool sp = act && a >= MID_HIST;
+            const unsigned bal = __ballot_sync(FULL, sp);
+            if (sp) {
+                const int idx = K + __popc(bal & lt);
+                cls[idx] = E::make(a, 1);
+                cidx[k] = idx;
+            } else if (act) {
+                cidx[k] = hist[a];
+            }
+            K += __popc(bal);
+        }
+        __syncwarp();
+        double center = 0.0;
+        for (int i = lane; i < K; i += 32) {
+            const Cls c_i = cls[i];
+            const R r = E::row(cls, K, base, c_i, ftab);
+            cq[i] = r;
+            center += (double)E::cval(c_i) * (double)r;
+        }
+        __syncwarp();
+        for (int k = lane; k < Du; k += 32) slot[rev[start + k]] = cq[cidx[k]];
+        center = warp_sum(center);
+        if (lane == 0) Ccenter[u] = center;
+        __syncwarp();
+    }
+}
+
+// Block-wide exclusive scan of one int per thread (HUB_THREADS threads).
+__device__ __forceinline__ int hub_scan(int x, int *s_w, int &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int t = lane < HUB_THREADS / 32 ? s_w[lane] : 0;
+        int ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, ti, o);
+            if (lane >= o) ti += y;
+        }
+        s_w[lane] = ti - t;
+        if (lane == 31) s_w[32] = ti;
+    }
+    __syncthreads();
+    const int r = s_w[w] + inc - x;
+    total = s_w[32];
+    __syncthreads();
+    return r;
+}
+
+// One CTA per hub (degree > MID_MAX), hubs taken largest degree bucket first
+// from an atomic counter.  Per-slot global arrays hold the class index of
+// every neighbour (cidx_g, at the hub's own row positions) and, for hubs with
+// more than HUB_SMEM_K classes, the classes themselves (cls_g, q_g).
+template <bool F64>
+__global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
+    const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
+    const int32_t *__restrict__ rev, const int32_t *__restrict__ bins, int32_t n, int32_t *__restrict__ cnt,
+    const double *__restrict__ ftab, void *__restrict__ slot_, double *__restrict__ Ccenter,
+    int32_t *__restrict__ cidx_g, void *__restrict__ cls_g_, void *__restrict__ q_g_) {
+    using E = ClassEval<F64>;
+    using Cls = typename E::Cls;
+    using R = typename E::R;
+    R *slot = reinterpret_cast<R *>(slot_);
+    Cls *cls_g = reinterpret_cast<Cls *>(cls_g_);
+    R *q_g = reinterpret_cast<R *>(q_g_);
+    extern __shared__ __align__(16) unsigned char hub_smem[];
+    int32_t *hist = reinterpret_cast<int32_t *>(hub_smem);
+    Cls *cls_s = reinterpret_cast<Cls *>(hub_smem + HUB_HIST * sizeof(int32_t));
+    R *q_s = reinterpret_cast<R *>(hub_smem + HUB_HIST * sizeof(int32_t) + HUB_SMEM_K * sizeof(Cls));
+    __shared__ int s_w[33];
+    __shared__ int s_item, s_nsp;
+    __shared__ double s_red[HUB_THREADS / 32];
+    const int tid = threadIdx.x;
+    int total = 0;
+    for (int b = NUM_HUB_BUCKETS - 1; b >= 0; --b) total += cnt[BIN_HUB0 + b];
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(cnt + CNT_HUB, 1);
+        __syncthreads();
+        int item = s_item;
+        if (item >= total) break;
+        int b = NUM_HUB_BUCKETS - 1;
+        while (item >= cnt[BIN_HUB0 + b]) item -= cnt[BIN_HUB0 + b--];
+        const int u = bins[(size_t)(BIN_HUB0 + b) * n + item];
+        const int start = rp[u];
+        const int Du = rp[u + 1] - start;
+        const int base = Du - 4;
+        int32_t *cidx = cidx_g + start;
+        for (int i = tid; i < HUB_HIST; i += HUB_THREADS) hist[i] = 0;
+        if (tid == 0) s_nsp = 0;
+        __syncthreads();
+        int nsp = 0;
+        for (int k = tid; k < Du; k += HUB_THREADS) {
+            const int a = D[ci[start + k]];
+            cidx[k] = a;
+            if (a < HUB_HIST) atomicAdd(hist + a, 1);
+            else ++nsp;
+        }
+        nsp = __reduce_add_sync(FULL, nsp);
+        if ((tid & 31) == 0 && nsp) atomicAdd(&s_nsp, nsp);
+        __syncthreads();
+        // dense classes: thread t owns bins [4t, 4t+4)
+        int hc[HUB_HIST / HUB_THREADS];
+        int mine = 0;
+#pragma unroll
+        for (int j = 0; j < HUB_HIST / HUB_THREADS; ++j) {
+            hc[j] = hist[tid * (HUB_HIST / HUB_THREADS) + j];
+            mine += hc[j] > 0;
+        }
+        int Kd;
+        int off = hub_scan(mine, s_w, Kd);
+        const int K = Kd + s_nsp;
+        // global fallback: rows own disjoint ranges [start + u, start + u + Du], and an
+        // even first index keeps the pairwise 16-byte class loads aligned
+        const int64_t gpos = ((int64_t)start + u + 1) & ~(int64_t)1;
+        Cls *cls = K <= HUB_SMEM_K ? cls_s : cls_g + gpos;
+        R *cq = K <= HUB_SMEM_K ? q_s : q_g + gpos;
+#pragma unroll
+        for (int j = 0; j < HUB_HIST / HUB_THREADS; ++j) {
+            const int bin = tid * (HUB_HIST / HUB_THREADS) + j;
+            if (hc[j] > 0) {
+                cls[off] = E::make(bin, hc[j]);
+                hist[bin] = off++;
+            }
+        }
+        __syncthreads();
+        // sparse classes, in neighbour order
+        int kbase = Kd;
+        for (int k0 = 0; k0 < Du; k0 += HUB_THREADS) {
+            const int k = k0 + tid;
+            const bool act = k < Du;
+            const int a = act ? cidx[k] : 0;
+            const bool sp = act && a >= HUB_HIST;
+            int tot;
+            const int pos = hub_scan(sp ? 1 : 0, s_w, tot);
+            if (sp) {
+                cls[kbase + pos] = E::make(a, 1);
+                cidx[k] = kbase + pos;
+            } else if (act) {
+                cidx[k] = hist[a];
+            }
+            kbase += tot;
+        }
+        __syncthreads();
+        double center = 0.0;
+        for (int i = tid; i < K; i += HUB_THREADS) {
+            const Cls c_i = cls[i];
+            const R r = E::row(cls, K, base, c_i, ftab);
+            cq[i] = r;
+            center += (double)E::cval(c_i) * (double)r;
+        }
+        __syncthreads();
+        for (int k = tid; k < Du; k += HUB_THREADS) slot[rev[start + k]] = cq[cidx[k]];
+        center = warp_sum(center);
+        if ((tid & 31) == 0) s_red[tid >> 5] = center;
+        __syncthreads();
+        if (tid < 32) {
+            double v = tid < HUB_THREADS / 32 ? s_red[tid] : 0.0;
+            v = warp_sum(v);
+            if (tid == 0) Ccenter[u] = v;
+        }
+    }
+}
+
+int hub_grid(int num_sms) { return num_sms * 2; }
+
 template <bool F64>
 static void small_all(const int32_t *rp, const int32_t *ci, const Scratch &s, int32_t n, cudaStream_t st,
                       unsigned grid) {
@@ -183,18 +469,41 @@ int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, i
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
-                     int64_t m, int num_sms, cudaStream_t st) {
+template <bool F64>
+static int big_classes(const int32_t *rp, const int32_t *ci, const Scratch &s, int32_t n, int num_sms,
+                       cudaStream_t st) {
+    using E = ClassEval<F64>;
+    const int32_t *mid = s.bins + (size_t)BIN_MID * n;
+    k_wedge_mid<F64><<<(unsigned)(num_sms * 8), MID_WARPS * 32, 0, st>>>(rp, ci, s.D, s.rev, mid, s.counters, s.ftab,
+                                                                         s.slotR, s.Ccenter);
+    const size_t smem = HUB_HIST * sizeof(int32_t) + HUB_SMEM_K * (sizeof(typename E::Cls) + sizeof(typename E::R));
+    if (cudaFuncSetAttribute(k_wedge_hub<F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return -1;
+    k_wedge_hub<F64><<<(unsigned)hub_grid(num_sms), HUB_THREADS, smem, st>>>(
+        rp, ci, s.D, s.rev, s.bins, n, s.counters, s.ftab, s.slotR, s.Ccenter, s.slotT, s.hub_cls, s.hub_q);
+    return 0;
+}
+
+int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int wedge_mode,
+                     int32_t n, int64_t m, int num_sms, cudaStream_t st) {
     (void)m;
     const int32_t *big = s.bins + (size_t)BIN_BIG * n;
-    unsigned grid = (unsigned)(num_sms * 4);
-    if (precision == EF_PREC_FP64)
-        k_wedge_big_direct<true><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, s.rev, big, s.counters, s.big_chunks, s.ftab,
-                                                            s.slotR, s.big_partial);
-    else
-        k_wedge_big_direct<false><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, s.rev, big, s.counters, s.big_chunks,
-                                                             s.ftab, s.slotR, s.big_partial);
-    k_big_reduce<<<(unsigned)(num_sms * 2), 256, 0, st>>>(big, s.counters, s.big_chunks, s.big_partial, s.Ccenter);
+    if (wedge_mode == 1) {
+        unsigned grid = (unsigned)(num_sms * 4);
+        if (precision == EF_PREC_FP64)
+            k_wedge_big_direct<true><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, s.rev, big, s.counters, s.big_chunks,
+                                                                s.ftab, s.slotR, s.big_partial);
+        else
+            k_wedge_big_direct<false><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, s.rev, big, s.counters, s.big_chunks,
+                                                                 s.ftab, s.slotR, s.big_partial);
+        k_big_reduce<<<(unsigned)(num_sms * 2), 256, 0, st>>>(big, s.counters, s.big_chunks, s.big_partial,
+                                                              s.Ccenter);
+    } else {
+        int rc = precision == EF_PREC_FP64 ? big_classes<true>(rp, ci, s, n, num_sms, st)
+                                           : big_classes<false>(rp, ci, s, n, num_sms, st);
+        if (rc) return rc;
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -128,10 +128,12 @@ def test_powerlaw_hubs_beyond_one_tile(ctx, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32c"])
-def test_bipartite_closed_form_multi_tile(ctx, precision):
-    """K_{6200,6200}: triangle-free 6200-regular, so every cluster has d = 3r-4 and
-    EF = ln(2r(r-1)); degrees exceed one wedge tile and owners exceed one triangle tile."""
-    r = 6200
+@pytest.mark.parametrize("r", [300, 3000, 6200])
+def test_bipartite_closed_form(ctx, precision, r):
+    """K_{r,r}: triangle-free r-regular, so every cluster has d = 3r-4 and EF = ln(2r(r-1)).
+    r = 300: warp-level class kernel with every neighbour above its histogram range;
+    r = 3000: CTA class kernel, classes in shared memory; r = 6200: classes spill to
+    global memory, triangle owners span two shared-memory tiles."""
     g = synth.complete_bipartite(r, r)
     got = run(ctx, g, precision)
     N = 2 * r * (r - 1)
@@ -183,6 +185,20 @@ def test_full_size_workloads_sampled(ctx, idx, precision):
     ref = oracle.vertex(g, nodes)
     ref["tri"] = ref["t"]
     assert_parity(got, ref, precision, nodes=nodes)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_direct_and_class_wedge_kernels_agree(ctx, precision):
+    """The direct pairwise kernel and the degree-class kernels compute the same credits."""
+    g = synth.powerlaw_cm(300000, 2.2, 3, 5000, 41)
+    a = run(ctx, g, precision, wedge_mode=0)
+    b = run(ctx, g, precision, wedge_mode=1)
+    np.testing.assert_array_equal(a["s"], b["s"])
+    if precision == "fp64":
+        np.testing.assert_allclose(a["t"], b["t"], rtol=1e-12)
+        np.testing.assert_allclose(a["ef"], b["ef"], rtol=1e-12)
+    else:
+        np.testing.assert_allclose(a["ef"], b["ef"], rtol=0, atol=EF_ATOL32)
 
 
 def test_fp32c_tracks_fp64(ctx):
