@@ -144,7 +144,7 @@ int ef_compute_ex(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
  *   stream has finished this call's work.  Input is validated.
  * Scratch lives in a fixed 32 MiB device array inside the library, held by
  * every GPU that loads it until the process exits.  Graphs whose scratch
- * would exceed it (about 128 n + 52 m + 24 min(n, m) bytes) are rejected with
+ * would exceed it (about 132 n + 76 m + 48 min(n, m) bytes) are rejected with
  * EF_ERR_ARG and a message naming the limit; nothing runs on the GPU then.
  * The first call on a device looks up the array's address (make it before
  * any stream capture).  All calls share the array: calls that overlap on the

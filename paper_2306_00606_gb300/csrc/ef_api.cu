@@ -1,19 +1,22 @@
 // C ABI of libef (declared in include/ef.h): contexts, scratch management and
 // the orchestration of the passes for one graph.
 //
-// Pass order on the context stream (one graph):
-//   prep A   degrees + row_ptr checks, per-row checks + sigma1/sigma2 +
-//            out-degrees, work bins
-//   prep B   oriented CSR, reverse slots, omega, big-item offsets
-//   [host]   one 4-byte-class readback of the error word and max degree
-//            (skipped with trust_input)
-//   f table  f(d) = d ln d, d < 3 maxdeg + 1
-//   wedge    small middle nodes (sub-warp), big middle nodes (CTA items)
-//   triangle warp owners, CTA owners
-//   finalize per-node sums, N, S, T, EF, flag
+// Pass order (one graph; "main" is the context stream, "side" a second stream
+// owned by the context):
+//   main  prep A   degrees + row_ptr checks + wedge bins; per-row checks,
+//                  sigma1/sigma2, out-degrees, slot rows
+//   host         one small readback: validation word and max degree
+//                  (skipped with trust_input)
+//   main  f table  f(d) = d ln d, d < 3 maxdeg + 1
+//   side  reverse slots                 (overlaps the three passes below)
+//   main  orientation, wedge pass (small, mid, hub), triangle pass
+//   main  waits for side; finalize (gathers slots through the reverse map)
+//   host  final readback of the validation word (asymmetric input is only
+//         detected by the reverse-slot pass)
 #include "ef_internal.cuh"
 
 #include <mutex>
+#include <new>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -21,17 +24,18 @@
 struct ef_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     int num_sms = 0;
     char err[512] = {0};
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     double *ftab = nullptr;
     int64_t ftab_cap = 0;
-    int32_t *h_counters = nullptr;   // pinned, 64 ints
+    int32_t *h_counters = nullptr;   // pinned, NUM_COUNTERS ints
     void *io = nullptr;              // device copies for host_io
     size_t io_bytes = 0;
     cudaEvent_t ev[8] = {};
-    bool events = false;
     ef_stats stats = {};
 };
 
@@ -40,9 +44,9 @@ namespace {
 thread_local char g_err[512];
 
 // Kernels one ef_compute_ex call launches (default wedge mode): prep A 3,
-// prep B 2 scans of 3 + reverse pairs 2 + orientation 2 + item counts,
-// f table 1, small wedges 4, class wedges 2, triangles 1, finalize 2.
-constexpr int64_t KERNELS_PER_CALL = 3 + 11 + 1 + 4 + 2 + 1 + 2;
+// reverse slots 1, orientation 2 scans of 3 + 2 + item counts, f table 1,
+// small wedges 4, class wedges 2, triangles 1, finalize 2.
+constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 9 + 1 + 4 + 2 + 1 + 2;
 
 void set_err(ef_ctx *c, const char *fmt, ...) {
     char *dst = c ? c->err : g_err;
@@ -62,45 +66,28 @@ void set_err(ef_ctx *c, const char *fmt, ...) {
         }                                                                                   \
     } while (0)
 
+#define LAUNCH(expr, what)                                       \
+    do {                                                         \
+        if (expr) {                                              \
+            set_err(ctx, "%s launch failed: %s", what,           \
+                    cudaGetErrorString(cudaGetLastError()));     \
+            return EF_ERR_CUDA;                                  \
+        }                                                        \
+    } while (0)
+
 inline size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int ensure_scratch(ef_ctx *ctx, size_t bytes) {
-    if (ctx->scratch_bytes >= bytes) return EF_OK;
-    if (ctx->scratch) {
+int ensure_buffer(ef_ctx *ctx, void **buf, size_t *have, size_t need, size_t slack) {
+    if (*have >= need) return EF_OK;
+    if (*buf) {
         CU(cudaStreamSynchronize(ctx->stream));
-        CU(cudaFree(ctx->scratch));
-        ctx->scratch = nullptr;
-        ctx->scratch_bytes = 0;
+        CU(cudaFree(*buf));
+        *buf = nullptr;
+        *have = 0;
     }
-    size_t want = bytes + bytes / 8;
-    CU(cudaMalloc(&ctx->scratch, want));
-    ctx->scratch_bytes = want;
-    return EF_OK;
-}
-
-int ensure_ftab(ef_ctx *ctx, int64_t cap) {
-    if (ctx->ftab_cap >= cap) return EF_OK;
-    if (ctx->ftab) {
-        CU(cudaStreamSynchronize(ctx->stream));
-        CU(cudaFree(ctx->ftab));
-        ctx->ftab = nullptr;
-        ctx->ftab_cap = 0;
-    }
-    CU(cudaMalloc(&ctx->ftab, (size_t)cap * sizeof(double)));
-    ctx->ftab_cap = cap;
-    return EF_OK;
-}
-
-int ensure_io(ef_ctx *ctx, size_t bytes) {
-    if (ctx->io_bytes >= bytes) return EF_OK;
-    if (ctx->io) {
-        CU(cudaStreamSynchronize(ctx->stream));
-        CU(cudaFree(ctx->io));
-        ctx->io = nullptr;
-        ctx->io_bytes = 0;
-    }
-    CU(cudaMalloc(&ctx->io, bytes));
-    ctx->io_bytes = bytes;
+    const size_t want = need + slack;
+    CU(cudaMalloc(buf, want));
+    *have = want;
     return EF_OK;
 }
 
@@ -126,6 +113,12 @@ const char *err_bits(int bits, char *buf, size_t len) {
     return buf;
 }
 
+int graph_error(ef_ctx *ctx, int bits) {
+    char buf[160];
+    set_err(ctx, "input is not a symmetric simple sorted CSR:%s", err_bits(bits, buf, sizeof buf));
+    return EF_ERR_GRAPH;
+}
+
 int compute_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const ef_options &o,
                    const ef_outputs &out) {
     using namespace ef;
@@ -135,49 +128,57 @@ int compute_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n,
         return EF_ERR_UNSUPPORTED;
     }
     Scratch s;
-    size_t need = carve_scratch(nullptr, n, m, s);
-    int rc = ensure_scratch(ctx, need);
+    const size_t need = carve_scratch(nullptr, n, m, s);
+    int rc = ensure_buffer(ctx, &ctx->scratch, &ctx->scratch_bytes, need, need / 8);
     if (rc) return rc;
     carve_scratch((char *)ctx->scratch, n, m, s);
     const bool prof = o.profile != 0;
     if (prof) CU(cudaEventRecord(ctx->ev[0], st));
 
     CU(cudaMemsetAsync(s.counters, 0, NUM_COUNTERS * sizeof(int32_t), st));
-    if (launch_prep_a(rp, ci, n, m, s, st)) { set_err(ctx, "prep A launch failed"); return EF_ERR_CUDA; }
-    if (launch_prep_b(rp, ci, n, m, s, st)) { set_err(ctx, "prep B launch failed"); return EF_ERR_CUDA; }
+    LAUNCH(launch_prep_a(rp, ci, n, m, s, st), "prep");
 
     int64_t fcap;
     if (!o.trust_input) {
         CU(cudaMemcpyAsync(ctx->h_counters, s.counters, NUM_COUNTERS * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
-        int bits = ctx->h_counters[CNT_ERR];
-        if (bits) {
-            char buf[160];
-            set_err(ctx, "input is not a symmetric simple sorted CSR:%s", err_bits(bits, buf, sizeof buf));
-            return EF_ERR_GRAPH;
-        }
+        if (ctx->h_counters[CNT_ERR]) return graph_error(ctx, ctx->h_counters[CNT_ERR]);
         fcap = 3 * (int64_t)ctx->h_counters[CNT_MAXDEG] + 1;
     } else {
-        int64_t bound = (int64_t)n - 1 < m ? (int64_t)n - 1 : m;
+        const int64_t bound = (int64_t)n - 1 < m ? (int64_t)n - 1 : m;
         fcap = 3 * (bound > 0 ? bound : 0) + 1;
     }
-    rc = ensure_ftab(ctx, fcap);
+    // f table (double) followed by the fixed-point triangle corrections (int64)
+    size_t have = (size_t)ctx->ftab_cap * 2 * sizeof(double);
+    rc = ensure_buffer(ctx, (void **)&ctx->ftab, &have, (size_t)fcap * 2 * sizeof(double), 0);
     if (rc) return rc;
+    ctx->ftab_cap = (int64_t)(have / (2 * sizeof(double)));
     s.ftab = ctx->ftab;
-    if (launch_ftab(s.ftab, s.counters + CNT_MAXDEG, fcap, st)) { set_err(ctx, "f table launch failed"); return EF_ERR_CUDA; }
-    CU(cudaMemsetAsync(s.t_own, 0, (size_t)n * sizeof(int64_t), st));
-    if (prof) CU(cudaEventRecord(ctx->ev[1], st));
+    s.tq = reinterpret_cast<int64_t *>(ctx->ftab + fcap);
+    LAUNCH(launch_ftab(s.ftab, s.tq, s.counters, fcap, st), "f table");
 
-    if (launch_wedge_small(rp, ci, s, o.precision, n, st)) { set_err(ctx, "wedge small launch failed"); return EF_ERR_CUDA; }
+    // reverse slots on the side stream, overlapping orientation, wedges and triangles
+    CU(cudaEventRecord(ctx->fork, st));
+    CU(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
+    LAUNCH(launch_rev(rp, ci, n, m, s, ctx->side), "reverse slots");
+    CU(cudaEventRecord(ctx->join, ctx->side));
+
+    LAUNCH(launch_orient(rp, ci, n, m, s, st), "orientation");
+    CU(cudaMemsetAsync(s.t_own, 0, (size_t)n * sizeof(int64_t), st));
+    CU(cudaMemsetAsync(s.q_own, 0, (size_t)n * sizeof(int64_t), st));
+    if (prof) CU(cudaEventRecord(ctx->ev[1], st));
+    LAUNCH(launch_wedge_small(rp, ci, s, o.precision, n, st), "small wedge");
     if (prof) CU(cudaEventRecord(ctx->ev[2], st));
-    if (launch_wedge_big(rp, ci, s, o.precision, o.wedge_mode, n, m, ctx->num_sms, st)) { set_err(ctx, "wedge big launch failed"); return EF_ERR_CUDA; }
-    // the count slots served as the hubs' class indices during the wedge pass
-    CU(cudaMemsetAsync(s.slotT, 0, (size_t)m * sizeof(int32_t), st));
+    LAUNCH(launch_wedge_big(rp, ci, s, o.precision, o.wedge_mode, n, m, ctx->num_sms, st), "big wedge");
     if (prof) CU(cudaEventRecord(ctx->ev[3], st));
-    if (launch_triangles(s, o.precision, n, m, ctx->num_sms, st)) { set_err(ctx, "triangle launch failed"); return EF_ERR_CUDA; }
+    LAUNCH(launch_triangles(s, o.precision, n, m, ctx->num_sms, st), "triangle");
     if (prof) CU(cudaEventRecord(ctx->ev[4], st));
-    if (launch_finalize(rp, ci, s, o.precision, n, out, ctx->num_sms, st)) { set_err(ctx, "finalize launch failed"); return EF_ERR_CUDA; }
+    CU(cudaStreamWaitEvent(st, ctx->join, 0));
+    LAUNCH(launch_finalize(rp, ci, s, o.precision, n, out, ctx->num_sms, st), "finalize");
     if (prof) CU(cudaEventRecord(ctx->ev[5], st));
+    if (!o.trust_input)
+        CU(cudaMemcpyAsync(ctx->h_counters + CNT_ERR, s.counters + CNT_ERR, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           st));
     return EF_OK;
 }
 
@@ -226,13 +227,15 @@ size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s) {
     s.out_ptr = (int32_t *)take(4 * (N + 1));
     s.out_col = (int32_t *)take(4 * (M + 1));
     s.out_D = (int32_t *)take(4 * (M + 1));
-    s.out_rslot = (int32_t *)take(4 * (M + 1));
+    s.out_pos = (int32_t *)take(4 * (M + 1));
     s.out_src = (int32_t *)take(4 * (M + 1));
     s.rev = (int32_t *)take(4 * (M + 1));
-    s.slotR = take(8 * (M + 1));
-    s.slotT = (int32_t *)take(4 * (M + 1));
-    s.Ccenter = (double *)take(8 * N);
+    s.srow = (int32_t *)take(4 * (M + 1));
+    s.slot = take(sizeof(Slot<true>) * (M + 1));
+    static_assert(sizeof(Slot<true>) == 32 && sizeof(Slot<false>) == 32, "slots are one 32-byte sector");
+    s.Ccenter = take(8 * N);
     s.t_own = (int64_t *)take(8 * N);
+    s.q_own = (int64_t *)take(8 * N);
     s.bins = (int32_t *)take(4 * N * NUM_BINS);
     s.counters = (int32_t *)take(4 * NUM_COUNTERS);
     s.big_chunks = (int32_t *)take(4 * (N + 1));
@@ -240,18 +243,19 @@ size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s) {
     s.scan_tmp = (int32_t *)take(4 * (N / 4096 + 4));
     s.hub_cls = take(8 * (M + N + 2));
     s.hub_q = take(8 * (M + N + 2));
+    s.hub_cidx = (int32_t *)take(4 * (M + 1));
     s.ftab = nullptr;
     return off;
 }
 
 // Message for ef_last_error(NULL), for entry points that run without a context.
 void set_global_error(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
 }  // namespace ef
 
 extern "C" {
 
 int ef_ctx_create(int device, void *stream, ef_ctx **out) {
-    ef_ctx *ctx = nullptr;
     if (!out) { set_err(nullptr, "null out pointer"); return EF_ERR_ARG; }
     *out = nullptr;
     int ndev = 0;
@@ -259,26 +263,21 @@ int ef_ctx_create(int device, void *stream, ef_ctx **out) {
         set_err(nullptr, "no CUDA device %d (count %d)", device, ndev);
         return EF_ERR_CUDA;
     }
-    ctx = new (std::nothrow) ef_ctx();
+    ef_ctx *ctx = new (std::nothrow) ef_ctx();
     if (!ctx) { set_err(nullptr, "host allocation failed"); return EF_ERR_OOM; }
     DeviceGuard dg(device);
     ctx->device = device;
     ctx->stream = (cudaStream_t)stream;
-    int rc = EF_OK;
-    do {
-        cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-        if (e != cudaSuccess) { set_err(nullptr, "device query failed: %s", cudaGetErrorString(e)); rc = EF_ERR_CUDA; break; }
-        e = cudaMallocHost(&ctx->h_counters, 64 * sizeof(int32_t));
-        if (e != cudaSuccess) { set_err(nullptr, "pinned allocation failed: %s", cudaGetErrorString(e)); rc = EF_ERR_OOM; break; }
-        for (int i = 0; i < 8; ++i) {
-            e = cudaEventCreate(&ctx->ev[i]);
-            if (e != cudaSuccess) { set_err(nullptr, "event creation failed: %s", cudaGetErrorString(e)); rc = EF_ERR_CUDA; break; }
-        }
-        ctx->events = rc == EF_OK;
-    } while (0);
-    if (rc != EF_OK) {
+    cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counters, ef::NUM_COUNTERS * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming);
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+    if (e != cudaSuccess) {
+        set_err(nullptr, "context set-up failed: %s", cudaGetErrorString(e));
         ef_ctx_destroy(ctx);
-        return rc;
+        return e == cudaErrorMemoryAllocation ? EF_ERR_OOM : EF_ERR_CUDA;
     }
     *out = ctx;
     return EF_OK;
@@ -287,13 +286,17 @@ int ef_ctx_create(int device, void *stream, ef_ctx **out) {
 int ef_ctx_destroy(ef_ctx *ctx) {
     if (!ctx) return EF_OK;
     DeviceGuard dg(ctx->device);
-    if (ctx->stream || ctx->scratch) cudaStreamSynchronize(ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
     cudaFree(ctx->scratch);
     cudaFree(ctx->ftab);
     cudaFree(ctx->io);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     for (int i = 0; i < 8; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->join) cudaEventDestroy(ctx->join);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     delete ctx;
     return EF_OK;
 }
@@ -329,11 +332,11 @@ int ef_compute_ex(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_o
         // device staging: row_ptr, col_idx, then every requested output
         const size_t N = (size_t)n;
         size_t off = 0;
-        auto slot = [&](size_t bytes) { size_t o_ = off; off += al(bytes); return o_; };
-        size_t o_rp = slot(4 * (N + 1)), o_ci = slot(4 * (size_t)(m + 1));
-        size_t o_ef = slot(8 * N), o_n = slot(8 * N), o_s = slot(8 * N), o_t = slot(8 * N), o_tr = slot(8 * N),
-               o_fl = slot(N);
-        rc = ensure_io(ctx, off);
+        auto place = [&](size_t bytes) { size_t o_ = off; off += al(bytes); return o_; };
+        const size_t o_rp = place(4 * (N + 1)), o_ci = place(4 * (size_t)(m + 1));
+        const size_t o_ef = place(8 * N), o_n = place(8 * N), o_s = place(8 * N), o_t = place(8 * N),
+                     o_tr = place(8 * N), o_fl = place(N);
+        rc = ensure_buffer(ctx, &ctx->io, &ctx->io_bytes, off, 0);
         if (rc) return rc;
         char *b = (char *)ctx->io;
         CU(cudaMemcpyAsync(b + o_rp, g->row_ptr, 4 * (N + 1), cudaMemcpyHostToDevice, ctx->stream));
@@ -358,6 +361,7 @@ int ef_compute_ex(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_o
     if (!o.async) {
         CU(cudaStreamSynchronize(ctx->stream));
         if (o.profile) accumulate_stats(ctx);
+        if (!o.trust_input && ctx->h_counters[ef::CNT_ERR]) return graph_error(ctx, ctx->h_counters[ef::CNT_ERR]);
     }
     CU(cudaGetLastError());
     return EF_OK;

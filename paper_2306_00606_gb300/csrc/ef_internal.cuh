@@ -15,15 +15,20 @@
 // sum = D_a + D_b + D_c.  So each node of the triangle gets
 // 4 * (f(sum-6) - f(sum-4)) added to T and -8 added to S.
 //
-// Per-edge credits travel through "slots": the slot at position e of row v
-// (e in [row_ptr[v], row_ptr[v+1]), column u) holds what v receives from u:
-// the open-degree credit R_u(v) of u as a middle node, plus the triangle
-// corrections u found as a triangle owner.  Each slot has exactly one writer
-// per pass, so no slot needs an atomic in the warp-level kernels.
+// Per-edge credits travel through "slots" stored at the sender's side: the
+// slot at position e of row u (column x) holds what u sends to x -- the
+// open-degree credit R_u(x) of u as a middle node, the triangle corrections
+// u found for x as a triangle owner, their count, and sigma1(u).  The wedge
+// pass writes every slot once (coalesced, no atomics); the triangle pass adds
+// its rare corrections with uncontended atomics; the finalize pass gathers
+// the slots addressed to v through the reverse-slot map rev (position of v in
+// u's row).
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "../../include/ef.h"
 
@@ -40,13 +45,13 @@ enum : int {
     ERRB_ASYM = 16,     // x in N(u) but u not in N(x)
 };
 
-// Work bins (each a list of node ids of capacity n).
+// Work bins (each a list of node ids of capacity n), filled from the degrees.
 enum : int {
     BIN_S4 = 0,    // 1 <= D <= 4   middle nodes, 8 per warp
     BIN_S8,        // 5..8          4 per warp
     BIN_S16,       // 9..16         2 per warp
     BIN_S32,       // 17..32        1 per warp
-    BIN_BIG,       // D > 32        (finalize warp list; direct wedge kernel)
+    BIN_BIG,       // D > 32        (direct wedge kernel)
     BIN_MID,       // 32 < D <= MID_MAX   degree-class wedge kernel, one warp each
     BIN_HUB0,      // D > MID_MAX, bucket floor(log2 D) - 9, capped at NUM_HUB_BUCKETS-1
     BIN_HUB_LAST = BIN_HUB0 + 6,
@@ -64,33 +69,68 @@ constexpr int BIG_ROWS = 256;          // rows per work item of the direct big-n
 constexpr int BIG_TILE = 4096;         // neighbour degrees staged per tile by the direct kernel
 constexpr int ROW_CTA = 512;           // threads of the per-hub-row kernels
 
+// Triangle corrections are integers in units of 2^-F (the pass adds only
+// integers: order-independent, no floating point in the pair loop).  F is
+// chosen per call from the maximum degree as the largest value, at most 52,
+// for which C(maxdeg, 2) triangles of the largest |g| cannot overflow int64
+// (F = 52 on small graphs, 27 on the 4M-node power-law workload).
+constexpr int TRI_FRAC_MAX = 52;
+
+// One slot (32 bytes, one DRAM sector): what the row owner sends to the column node.
+template <bool F64>
+struct Slot;
+template <>
+struct __align__(32) Slot<true> {
+    double val;   // open-degree credit (natural-log units)
+    int32_t cnt;  // triangles
+    int32_t sig;  // sigma1 of the sender
+    int64_t tri;  // triangle corrections, fixed point
+    int64_t pad;
+};
+template <>
+struct __align__(32) Slot<false> {
+    float val;
+    int32_t cnt;
+    int32_t sig;
+    int32_t pad0;
+    int64_t tri;
+    int64_t pad1;
+};
+
+// Precision-dependent accumulator type: double (FP64) or float (FP32C).
+template <bool F64>
+using AccT = typename std::conditional<F64, double, float>::type;
+
 // Scratch carved from one device allocation per call (sizes depend on n, m).
 struct Scratch {
     int32_t *D;          // n      degrees
-    int64_t *sig1;       // n      sum of neighbour degrees
+    int64_t *sig1;       // n      sum of neighbour degrees (< m, so int32 in slots)
     int64_t *sig2;       // n      sum of squared neighbour degrees
     int32_t *outdeg;     // n      out-degree in (degree, id) order
     int32_t *out_ptr;    // n+1    oriented CSR offsets
     int32_t *out_col;    // m+1    oriented neighbour ids (ascending id within a row)
     int32_t *out_D;      // m+1    their degrees
-    int32_t *out_rslot;  // m+1    slot of the owner in the neighbour's row
+    int32_t *out_pos;    // m+1    their position in the owner's own row (the owner's slot for them)
     int32_t *out_src;    // m+1    owner of each oriented edge
     int32_t *rev;        // m+1    rev[e] = position of u in N(x) for e = (u -> x)
-    void    *slotR;      // m+1    credit to the row owner from the column node (float or double)
-    int32_t *slotT;      // m+1    triangles credited the same way
-    double  *Ccenter;    // n      middle-node credit + own triangle corrections
+    int32_t *srow;       // m+1    row of each slot
+    void    *slot;       // m+1    Slot<F64>, 32 bytes each
+    void    *Ccenter;    // n      middle-node credit (AccT<F64>, 8 bytes reserved per node)
     int64_t *t_own;      // n      triangles found as owner
+    int64_t *q_own;      // n      their corrections, fixed point
+    int64_t *tq;         // 3*maxdeg+1 (capacity): 4 (f(s-6) - f(s-4)) * 2^F, rounded (F in counters)
     int32_t *bins;       // NUM_BINS * n   work lists
-    int32_t *counters;   // 64 ints: [0..NUM_BINS) bin counts, CNT_* below
+    int32_t *counters;   // NUM_COUNTERS ints: [0..NUM_BINS) bin counts, CNT_* below
     int32_t *big_chunks; // n+1    work items per big middle node (direct kernel), then their scan
     double  *big_partial;// m/BIG_ROWS + n + 2  per-item middle-node partial sums (direct kernel)
     int32_t *scan_tmp;   // scan block sums
     double  *ftab;       // 3*maxdeg+1 (capacity): f(d) = d ln d in FP64
     void    *hub_cls;    // m+n+2  class (degree, count) pairs of hubs with > HUB_SMEM_K classes
     void    *hub_q;      // m+n+2  their per-class credits
+    int32_t *hub_cidx;   // m+1    class index of each neighbour of a hub (at the hub's row positions)
 };
 
-enum : int { CNT_ERR = 32, CNT_MAXDEG = 33, CNT_BIGITEM = 34, CNT_HUB = 36, CNT_NOUT = 37, NUM_COUNTERS = 64 };
+enum : int { CNT_ERR = 32, CNT_MAXDEG = 33, CNT_BIGITEM = 34, CNT_HUB = 36, CNT_TRIFRAC = 37, NUM_COUNTERS = 64 };
 
 // Bytes of scratch for a graph (f table excluded), and its layout when base != nullptr.
 size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s);
@@ -141,8 +181,42 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     s = t;
 }
 
+// Running sum in T: plain for double, Kahan-compensated for float.
+template <typename T>
+struct SumAcc {
+    T s = 0, c = 0;
+    __device__ __forceinline__ void add(T x) {
+        if constexpr (sizeof(T) == 4) {
+            kahan_add(s, c, x);
+        } else {
+            s += x;
+        }
+    }
+    __device__ __forceinline__ T get() const { return s - c; }
+};
+
 // d * log2(d) for integral d >= 1 held in a float (MUFU lg2).
 __device__ __forceinline__ float dlog2d(float d) { return d * __log2f(d); }
+
+// Store a fresh slot (wedge pass): credit, no triangles yet, sender's sigma1.
+template <bool F64>
+__device__ __forceinline__ void put_slot(void *slots, int64_t e, AccT<F64> val, int32_t sig) {
+    Slot<F64> s{};
+    s.val = val;
+    s.cnt = 0;
+    s.sig = sig;
+    s.tri = 0;
+    reinterpret_cast<Slot<F64> *>(slots)[e] = s;
+}
+
+// Sum of a value over a group of G consecutive lanes (tree order), in the
+// accumulator's own precision.
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o, G);
+    return v;
+}
 
 constexpr double LN2 = 0.69314718055994530942;
 
@@ -151,9 +225,10 @@ constexpr double LN2 = 0.69314718055994530942;
 // ------------------------------------------------------------ launchers
 namespace ef {
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st);
-int launch_prep_b(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st);
+int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st);
+int launch_rev(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st);
 int launch_scan(const int32_t *in, int32_t *out, int32_t n, int32_t *tmp, cudaStream_t st);
-int launch_ftab(double *ftab, const int32_t *maxdeg_dev, int64_t cap, cudaStream_t st);
+int launch_ftab(double *ftab, int64_t *tq, int32_t *cnt, int64_t cap, cudaStream_t st);
 int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
                        cudaStream_t st);
 int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int wedge_mode,
@@ -161,5 +236,4 @@ int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int
 int launch_triangles(const Scratch &s, int precision, int32_t n, int64_t m, int num_sms, cudaStream_t st);
 int launch_finalize(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
                     const ef_outputs &out, int num_sms, cudaStream_t st);
-int hub_grid(int num_sms);
 }  // namespace ef

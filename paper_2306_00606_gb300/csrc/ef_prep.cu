@@ -133,7 +133,8 @@ struct RowStats {
     int64_t s1 = 0, s2 = 0;
     int od = 0, err = 0;
     __device__ __forceinline__ void slot(const int32_t *__restrict__ ci, const int32_t *__restrict__ D, int32_t n,
-                                         int v, int Dv, int a, int e) {
+                                         int v, int Dv, int a, int e, int32_t *__restrict__ srow) {
+        srow[e] = v;
         const int x = ci[e];
         if (x < 0 || x >= n) { err |= ERRB_RANGE; return; }
         if (x == v) err |= ERRB_SELFLOOP;
@@ -147,7 +148,7 @@ struct RowStats {
 
 __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
                             const int32_t *__restrict__ D, int64_t *__restrict__ sig1, int64_t *__restrict__ sig2,
-                            int32_t *__restrict__ outdeg, int32_t *__restrict__ cnt) {
+                            int32_t *__restrict__ outdeg, int32_t *__restrict__ srow, int32_t *__restrict__ cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
@@ -160,7 +161,7 @@ __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__res
         if (in && Dv <= SMALL_MAX) {
             RowStats r;
             if (ok)
-                for (int e = a; e < b; ++e) r.slot(ci, D, n, v, Dv, a, e);
+                for (int e = a; e < b; ++e) r.slot(ci, D, n, v, Dv, a, e, srow);
             sig1[v] = r.s1;
             sig2[v] = r.s2;
             outdeg[v] = r.od;
@@ -173,7 +174,7 @@ __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__res
             const int u = (int)(base + j);
             const int ua = __shfl_sync(FULL, a, j), ub = __shfl_sync(FULL, b, j);
             RowStats r;
-            for (int e = ua + lane; e < ub; e += 32) r.slot(ci, D, n, u, ub - ua, ua, e);
+            for (int e = ua + lane; e < ub; e += 32) r.slot(ci, D, n, u, ub - ua, ua, e, srow);
             const int64_t s1 = warp_sum(r.s1), s2 = warp_sum(r.s2);
             const int od = warp_sum(r.od);
             const int err = __reduce_or_sync(FULL, r.err);
@@ -192,14 +193,15 @@ __global__ void __launch_bounds__(ROW_CTA) k_row_stats_hub(const int32_t *__rest
                                                            const int32_t *__restrict__ D,
                                                            const int32_t *__restrict__ bins,
                                                            int64_t *__restrict__ sig1, int64_t *__restrict__ sig2,
-                                                           int32_t *__restrict__ outdeg, int32_t *__restrict__ cnt) {
+                                                           int32_t *__restrict__ outdeg, int32_t *__restrict__ srow,
+                                                           int32_t *__restrict__ cnt) {
     __shared__ int64_t s_buf[32];
     const int total = hub_total(cnt);
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         const int u = hub_row(bins, n, cnt, it);
         const int a = rp[u], b = rp[u + 1];
         RowStats r;
-        for (int e = a + threadIdx.x; e < b; e += ROW_CTA) r.slot(ci, D, n, u, b - a, a, e);
+        for (int e = a + threadIdx.x; e < b; e += ROW_CTA) r.slot(ci, D, n, u, b - a, a, e, srow);
         const int64_t s1 = block_sum<int64_t>(r.s1, s_buf);
         const int64_t s2 = block_sum<int64_t>(r.s2, s_buf);
         const int64_t od = block_sum<int64_t>(r.od, s_buf);
@@ -224,12 +226,12 @@ __global__ void __launch_bounds__(ROW_CTA) k_row_stats_hub(const int32_t *__rest
 __device__ __forceinline__ int rev_slot(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
                                         int64_t m, const int32_t *__restrict__ D, int32_t *__restrict__ rev, int v,
                                         int Dv, int e) {
+    (void)D;
     const int x = ci[e];
     if (x < 0 || x >= n) return 0;
-    const int Dx = D[x];
-    if (!rank_less(Dx, x, Dv, v)) return 0;
-    const int xa = rp[x], xb = rp[x + 1];
+    const int xa = rp[x], xb = rp[x + 1];   // D_x = xb - xa: no separate degree load
     if (!(xa >= 0 && xa <= xb && (int64_t)xb <= m)) return ERRB_ASYM;
+    if (!rank_less(xb - xa, x, Dv, v)) return 0;
     const int pos = xa + lower_bound_i32(ci + xa, xb - xa, v);
     if (pos < xb && ci[pos] == v) {
         rev[e] = pos;
@@ -239,72 +241,50 @@ __device__ __forceinline__ int rev_slot(const int32_t *__restrict__ rp, const in
     return ERRB_ASYM;
 }
 
-__global__ void k_rev_pairs(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
-                            const int32_t *__restrict__ D, int32_t *__restrict__ rev, int32_t *__restrict__ cnt) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
-         base += nwarps * 32) {
-        const int v = (int)(base + lane);
-        const bool in = base + lane < n;
-        const int a = in ? rp[v] : 0, b = in ? rp[v + 1] : 0;
-        const bool ok = in && a >= 0 && a <= b && (int64_t)b <= m;
-        const int Dv = ok ? b - a : 0;
-        int err = 0;
-        if (ok && Dv <= SMALL_MAX)
-            for (int e = a; e < b; ++e) err |= rev_slot(rp, ci, n, m, D, rev, v, Dv, e);
-        unsigned mid = __ballot_sync(FULL, Dv > SMALL_MAX && Dv <= MID_MAX);
-        while (mid) {
-            const int j = __ffs(mid) - 1;
-            mid &= mid - 1;
-            const int u = (int)(base + j);
-            const int ua = __shfl_sync(FULL, a, j), ub = __shfl_sync(FULL, b, j);
-            for (int e = ua + lane; e < ub; e += 32) err |= rev_slot(rp, ci, n, m, D, rev, u, ub - ua, e);
-        }
-        err = __reduce_or_sync(FULL, err);
-        if (lane == 0 && err) atomicOr(cnt + CNT_ERR, err);
-    }
-}
-
-__global__ void __launch_bounds__(ROW_CTA) k_rev_pairs_hub(const int32_t *__restrict__ rp,
-                                                           const int32_t *__restrict__ ci, int32_t n, int64_t m,
-                                                           const int32_t *__restrict__ D,
-                                                           const int32_t *__restrict__ bins,
-                                                           int32_t *__restrict__ rev, int32_t *__restrict__ cnt) {
-    const int total = hub_total(cnt);
+// One thread per slot: its row comes from srow (written by the row-stats
+// pass); only slots pointing to a lower-ranked node search.
+__global__ void k_rev_flat(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
+                           const int32_t *__restrict__ D, const int32_t *__restrict__ srow, int32_t *__restrict__ rev,
+                           int32_t *__restrict__ cnt) {
     int err = 0;
-    for (int it = blockIdx.x; it < total; it += gridDim.x) {
-        const int u = hub_row(bins, n, cnt, it);
-        const int a = rp[u], b = rp[u + 1];
-        for (int e = a + threadIdx.x; e < b; e += ROW_CTA) err |= rev_slot(rp, ci, n, m, D, rev, u, b - a, e);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // four independent slots per thread keep four search chains in flight
+    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e0 < m; e0 += 4 * stride) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t e = e0 + u * stride;
+            if (e >= m) break;
+            const int v = srow[e];
+            if (v < 0 || v >= n) continue;
+            const int va = rp[v], vb = rp[v + 1];
+            if (va > e || vb <= e) continue;   // slot of a row that failed validation
+            err |= rev_slot(rp, ci, n, m, D, rev, v, vb - va, (int)e);
+        }
     }
     err = __reduce_or_sync(FULL, err);
     if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
 }
 
 // ------------------------------------------------------------- orientation
-// Checks that every slot was paired and appends the out-neighbours x of u
-// (in (degree, id) order) to the oriented CSR in ascending id order, with
-// D_x, the slot of u in x's row (rev[e]) and the owner u.
+// Appends the out-neighbours x of u (in (degree, id) order) to the oriented
+// CSR in ascending id order, with D_x, the position e of x in u's own row
+// (u's slot for x) and the owner u.
 struct Orient {
-    const int32_t *ci, *D, *rev;
-    int32_t *out_col, *out_D, *out_rslot, *out_src;
+    const int32_t *ci, *D;
+    int32_t *out_col, *out_D, *out_pos, *out_src;
     int32_t n;
     __device__ __forceinline__ bool probe(int u, int Du, int e, int &x, int &Dx, int &r, int &err) const {
+        (void)err;
         x = ci[e];
         const bool xin = x >= 0 && x < n;
         Dx = xin ? D[x] : 0;
-        r = rev[e];
-        if (r < 0) {
-            err |= ERRB_ASYM;
-            r = e;
-        }
+        r = e;
         return xin && rank_less(Du, u, Dx, x);
     }
     __device__ __forceinline__ void put(int k, int u, int x, int Dx, int r) const {
         out_col[k] = x;
         out_D[k] = Dx;
-        out_rslot[k] = r;
+        out_pos[k] = r;
         out_src[k] = u;
     }
 };
@@ -384,11 +364,29 @@ __global__ void k_big_chunks(const int32_t *__restrict__ D, const int32_t *__res
 }
 
 // -------------------------------------------------------------- f(d) table
-__global__ void k_ftab(double *__restrict__ ftab, const int32_t *__restrict__ maxdeg, int64_t cap) {
-    int64_t L = 3 * (int64_t)(*maxdeg) + 1;
+// ftab[d] = d ln d; tq[s] = 4 (f(s-6) - f(s-4)) in units of 2^-F, the
+// correction one triangle of degree sum s brings to each of its nodes.  F is
+// the largest value <= TRI_FRAC_MAX with C(maxdeg, 2) * max|g| * 2^F < 2^62
+// (|g| <= 8 (ln(3 maxdeg) + 1) + 8); every thread derives the same F and
+// thread 0 publishes it for the finalize pass.
+__global__ void k_ftab(double *__restrict__ ftab, int64_t *__restrict__ tq, int32_t *__restrict__ cnt, int64_t cap) {
+    const int64_t maxdeg = cnt[CNT_MAXDEG];
+    int64_t L = 3 * maxdeg + 1;
     if (L > cap) L = cap;
-    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < L; d += (int64_t)gridDim.x * blockDim.x)
+    const double tmax = 0.5 * (double)maxdeg * (double)(maxdeg > 0 ? maxdeg - 1 : 0) + 1.0;
+    const double gmax = 8.0 * (log(3.0 * (double)maxdeg + 8.0) + 1.0) + 8.0;
+    int F = (int)floor(62.0 - log2(tmax * gmax));
+    F = F > TRI_FRAC_MAX ? TRI_FRAC_MAX : (F < 0 ? 0 : F);
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CNT_TRIFRAC] = F;
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < L; d += (int64_t)gridDim.x * blockDim.x) {
         ftab[d] = d > 1 ? (double)d * log((double)d) : 0.0;
+        double g = 0.0;
+        if (d >= 6) {
+            const double a = (double)(d - 6), b = (double)(d - 4);
+            g = 4.0 * ((a > 1.0 ? a * log(a) : 0.0) - b * log(b));
+        }
+        tq[d] = llrint(ldexp(g, F));
+    }
 }
 
 // ------------------------------------------------------------ exclusive scan
@@ -454,11 +452,11 @@ int launch_scan(const int32_t *in, int32_t *out, int32_t n, int32_t *tmp, cudaSt
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_ftab(double *ftab, const int32_t *maxdeg_dev, int64_t cap, cudaStream_t st) {
+int launch_ftab(double *ftab, int64_t *tq, int32_t *cnt, int64_t cap, cudaStream_t st) {
     int64_t blocks = (cap + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
-    k_ftab<<<(unsigned)blocks, 256, 0, st>>>(ftab, maxdeg_dev, cap);
+    k_ftab<<<(unsigned)blocks, 256, 0, st>>>(ftab, tq, cnt, cap);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -472,23 +470,29 @@ static inline unsigned grid_for(int64_t work, int per_block, int64_t cap) {
 // Degrees + wedge bins, per-row checks and neighbour sums.
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
     k_degrees<<<grid_for(n, 1024, 1 << 30), 1024, 0, st>>>(rp, n, m, s.D, s.bins, s.counters);
-    k_row_stats<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, s.sig1, s.sig2, s.outdeg, s.counters);
-    k_row_stats_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, ci, n, s.D, s.bins, s.sig1, s.sig2, s.outdeg, s.counters);
+    k_row_stats<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, s.sig1, s.sig2, s.outdeg, s.srow,
+                                                            s.counters);
+    k_row_stats_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, ci, n, s.D, s.bins, s.sig1, s.sig2, s.outdeg, s.srow,
+                                                 s.counters);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Reverse slots, oriented CSR, big-item offsets (direct kernel).
-int launch_prep_b(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
-    if (cudaMemsetAsync(s.rev, 0xff, (size_t)m * sizeof(int32_t), st) != cudaSuccess) return -1;
+// Oriented CSR and the direct kernel's item offsets.
+int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
     if (launch_scan(s.outdeg, s.out_ptr, n, s.scan_tmp, st)) return -1;
-    k_rev_pairs<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, s.rev, s.counters);
-    k_rev_pairs_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, ci, n, m, s.D, s.bins, s.rev, s.counters);
-    Orient o{ci, s.D, s.rev, s.out_col, s.out_D, s.out_rslot, s.out_src, n};
+    Orient o{ci, s.D, s.out_col, s.out_D, s.out_pos, s.out_src, n};
     k_orient<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, n, m, o, s.out_ptr, s.counters);
     k_orient_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters);
     // outdeg is free after the scan: reuse it for the direct kernel's item counts
     k_big_chunks<<<grid_for(n, 256, 1 << 30), 256, 0, st>>>(s.D, s.bins + (size_t)BIN_BIG * n, s.counters, n, s.outdeg);
     if (launch_scan(s.outdeg, s.big_chunks, n, s.scan_tmp, st)) return -1;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Reverse slots (independent of the orientation: may run on another stream).
+int launch_rev(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
+    if (cudaMemsetAsync(s.rev, 0xff, (size_t)m * sizeof(int32_t), st) != cudaSuccess) return -1;
+    k_rev_flat<<<grid_for(m, 256, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, s.srow, s.rev, s.counters);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

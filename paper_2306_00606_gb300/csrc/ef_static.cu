@@ -61,12 +61,12 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     const int64_t bound = (int64_t)n - 1 < m ? (int64_t)n - 1 : m;
     const int64_t fcap = 3 * (bound > 0 ? bound : 0) + 1;
     Scratch s;
-    const size_t need = carve_scratch(nullptr, n, m, s) + al256(8 * (size_t)fcap);
+    const size_t need = carve_scratch(nullptr, n, m, s) + al256(16 * (size_t)fcap);
     if (need > EF_STATIC_SCRATCH_BYTES) {
         char msg[200];
         snprintf(msg, sizeof msg,
                  "ef_compute_static: graph needs %zu bytes of scratch, above the fixed %zu-byte maximum "
-                 "(about 128 n + 52 m + 24 min(n, m) bytes); use ef_compute_ex",
+                 "(about 132 n + 76 m + 48 min(n, m) bytes); use ef_compute_ex",
                  need, EF_STATIC_SCRATCH_BYTES);
         return fail(EF_ERR_ARG, msg);
     }
@@ -87,6 +87,7 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
         base = g_static_addr[dev];
     }
     s.ftab = (double *)((char *)base + carve_scratch((char *)base, n, m, s));
+    s.tq = reinterpret_cast<int64_t *>(s.ftab + fcap);
     int num_sms = 0;
     if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: device query failed");
@@ -95,7 +96,7 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     const int32_t *rp = g->row_ptr, *ci = g->col_idx;
     if (cudaMemsetAsync(s.counters, 0, NUM_COUNTERS * sizeof(int32_t), st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: memset failed");
-    if (launch_prep_a(rp, ci, n, m, s, st) || launch_prep_b(rp, ci, n, m, s, st))
+    if (launch_prep_a(rp, ci, n, m, s, st))
         return fail(EF_ERR_CUDA, "ef_compute_static: prep launch failed");
     int32_t h_cnt[NUM_COUNTERS];
     if (cudaMemcpyAsync(h_cnt, s.counters, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -104,15 +105,19 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     if (h_cnt[CNT_ERR]) return fail(EF_ERR_GRAPH, "ef_compute_static: input is not a symmetric simple sorted CSR");
     ef_outputs out = {};
     out.ef = out_ef;
-    if (launch_ftab(s.ftab, s.counters + CNT_MAXDEG, fcap, st) ||
+    if (launch_ftab(s.ftab, s.tq, s.counters, fcap, st) || launch_rev(rp, ci, n, m, s, st) ||
+        cudaMemsetAsync(s.q_own, 0, (size_t)n * sizeof(int64_t), st) != cudaSuccess ||
+        launch_orient(rp, ci, n, m, s, st) ||
         cudaMemsetAsync(s.t_own, 0, (size_t)n * sizeof(int64_t), st) != cudaSuccess ||
         launch_wedge_small(rp, ci, s, precision, n, st) ||
         launch_wedge_big(rp, ci, s, precision, 0, n, m, num_sms, st) ||
-        cudaMemsetAsync(s.slotT, 0, (size_t)m * sizeof(int32_t), st) != cudaSuccess ||
         launch_triangles(s, precision, n, m, num_sms, st) ||
-        launch_finalize(rp, ci, s, precision, n, out, num_sms, st))
+        launch_finalize(rp, ci, s, precision, n, out, num_sms, st) ||
+        cudaMemcpyAsync(h_cnt, s.counters, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: launch failed");
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: kernel execution failed");
+    // asymmetric input is only detected by the reverse-slot and finalize passes
+    if (h_cnt[CNT_ERR]) return fail(EF_ERR_GRAPH, "ef_compute_static: input is not a symmetric simple sorted CSR");
     return EF_OK;
 }

@@ -2,83 +2,152 @@
 //
 // The wedge pass credits every cluster with its open degree; clusters whose
 // ends are adjacent (triangles) need d - 2 instead.  Edges are oriented from
-// lower to higher (degree, id); each triangle {a, b, c} with a < b < c in
-// that order is found exactly once, on the oriented edge a -> b, as an
-// element c of N+(a) and N+(b).  Its three nodes each hold 4 credits of
-// degree sum-6 that the wedge pass counted at sum-4 (sum = D_a + D_b + D_c),
-// so each receives g = 4 (f(sum-6) - f(sum-4)) and one triangle count.
+// lower to higher (degree, id); each triangle is found exactly once, at its
+// lowest-ranked node a, as an adjacent pair {b, c} of a's out-neighbours
+// N+(a) (b before c in N+(a)'s id order).  Its three nodes each hold 4
+// credits of degree sum-6 that the wedge pass counted at sum-4
+// (sum = D_a + D_b + D_c), so each receives g = 4 (f(sum-6) - f(sum-4)) and
+// one triangle count.
 //
-// One thread per oriented edge a -> b merges the two id-sorted out-lists
-// (the whole oriented CSR is a few tens of MB and stays in L2).  Credits go
-// where the wedge pass put a's credits to b and c -- the slot of a in their
-// rows -- and a's own to Ccenter[a].  A hit is rare (in the power-law
-// workload 2.7M of 20.6M oriented edges close a triangle), so credits to c
-// use uncontended global atomics; credits to a and b are summed per thread
-// and added once.
+// Pair tests: b and c are adjacent iff the higher-ranked of the two is in the
+// lower-ranked one's out-list (binary search; the oriented CSR is a few tens
+// of MB and stays in L2).  That is sum_a C(|N+(a)|, 2) independent tests --
+// 1.1e8 on the 4M-node power-law workload, against 1.15e9 dependent steps
+// for merging the two out-lists of every edge.  A warp takes 32 consecutive
+// oriented edges and spreads all their pairs evenly over its lanes.
+//
+// The pass is integer-only: g comes from a table in fixed point (units of
+// 2^-F, F chosen per call from the maximum degree), so sums are exact and independent of the order of the
+// atomics, and no FP64 instruction (one lane per clock per SM sub-partition
+// on this GPU) sits in a divergent branch.  Credits go to a's own slots for b
+// and c (where the wedge pass put a's open-degree credits to them) and a's own
+// to q_own[a]; each lane merges consecutive hits on the same edge before
+// adding.
 #include "ef_internal.cuh"
-
-#include <type_traits>
 
 namespace ef {
 
+constexpr int TRI_WARPS = 8;
+
 template <bool F64>
-__global__ void __launch_bounds__(256) k_tri_edges(
+__device__ __forceinline__ void credit_slot(void *slots, int pos, int64_t q, int cnt) {
+    Slot<F64> *s = reinterpret_cast<Slot<F64> *>(slots) + pos;
+    atomicAdd((unsigned long long *)&s->tri, (unsigned long long)q);
+    atomicAdd(&s->cnt, cnt);
+}
+
+template <bool F64>
+__global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_pairs(
     const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_D,
-    const int32_t *__restrict__ out_rslot, const int32_t *__restrict__ out_src, const int32_t *__restrict__ D,
-    int32_t n, const double *__restrict__ ftab, void *__restrict__ slot_, int32_t *__restrict__ slotT,
-    double *__restrict__ Ccenter, int64_t *__restrict__ t_own) {
-    using Acc = typename std::conditional<F64, double, float>::type;
-    Acc *slot = reinterpret_cast<Acc *>(slot_);
+    const int32_t *__restrict__ out_pos, const int32_t *__restrict__ out_src, const int32_t *__restrict__ D,
+    int32_t n, const int64_t *__restrict__ tq, void *__restrict__ slots, int64_t *__restrict__ q_own,
+    int64_t *__restrict__ t_own) {
+    __shared__ int s_ex[TRI_WARPS][32];   // exclusive prefix of pair counts
+    __shared__ int s_k[TRI_WARPS][32], s_b[TRI_WARPS][32], s_Db[TRI_WARPS][32], s_bs[TRI_WARPS][32];
+    __shared__ int s_be[TRI_WARPS][32], s_Dab[TRI_WARPS][32], s_a[TRI_WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t total = out_ptr[n];
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-        const int a = out_src[k];
-        const int b = out_col[k];
-        int x = out_ptr[a], xe = out_ptr[a + 1];
-        int y = out_ptr[b], ye = out_ptr[b + 1];
-        if (x >= xe || y >= ye) continue;
-        const int Dab = D[a] + out_D[k];
-        double acc = 0.0;
-        int hits = 0;
-        int va = out_col[x], vb = out_col[y];
-        for (;;) {
-            if (va < vb) {
-                if (++x >= xe) break;
-                va = out_col[x];
-            } else if (va > vb) {
-                if (++y >= ye) break;
-                vb = out_col[y];
+    const int64_t stride = (int64_t)gridDim.x * TRI_WARPS * 32;
+    for (int64_t K0 = ((int64_t)blockIdx.x * TRI_WARPS + w) * 32; K0 < total; K0 += stride) {
+        const int64_t k = K0 + lane;
+        int np = 0;
+        if (k < total) {
+            const int a = out_src[k];
+            const int kend = out_ptr[a + 1];
+            np = kend - (int)k - 1;
+            if (np > 0) {
+                const int b = out_col[k];
+                const int Db = out_D[k];
+                s_k[w][lane] = (int)k;
+                s_b[w][lane] = b;
+                s_Db[w][lane] = Db;
+                s_bs[w][lane] = out_ptr[b];
+                s_be[w][lane] = out_ptr[b + 1];
+                s_Dab[w][lane] = D[a] + Db;
+                s_a[w][lane] = a;
             } else {
-                const int sum = Dab + out_D[x];
-                const double g = 4.0 * (__ldg(ftab + (sum - 6)) - __ldg(ftab + (sum - 4)));
-                const int rc = out_rslot[x];
-                atomicAdd(slot + rc, (Acc)g);
-                atomicAdd(slotT + rc, 1);
-                acc += g;
-                ++hits;
-                if (++x >= xe || ++y >= ye) break;
-                va = out_col[x];
-                vb = out_col[y];
+                np = 0;
             }
         }
-        if (hits) {
-            const int rb = out_rslot[k];
-            atomicAdd(slot + rb, (Acc)acc);
-            atomicAdd(slotT + rb, hits);
-            atomicAdd(Ccenter + a, acc);
-            atomicAdd((unsigned long long *)(t_own + a), (unsigned long long)hits);
+        int inc = np;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
         }
+        s_ex[w][lane] = inc - np;
+        const int P = __shfl_sync(FULL, inc, 31);
+        __syncwarp();
+        int cur_i = -1, cur_a = -1, hit_b = 0, hit_a = 0;
+        int64_t acc_b = 0, acc_a = 0;
+        // the warp edge i owning pair t is the last i with s_ex[i] <= t; its fields are cached
+        int i = -1, ki = 0, exi = 0, b = 0, Db = 0, bs = 0, be = 0, Dab = 0, ai = 0;
+        for (int t = lane; t < P; t += 32) {
+            // t only grows, so the lane's edge index only moves forward
+            int ni = i < 0 ? 0 : i;
+            while (ni < 31 && s_ex[w][ni + 1] <= t) ++ni;
+            if (ni != i) {
+                i = ni;
+                ki = s_k[w][i];
+                exi = s_ex[w][i];
+                b = s_b[w][i];
+                Db = s_Db[w][i];
+                bs = s_bs[w][i];
+                be = s_be[w][i];
+                Dab = s_Dab[w][i];
+                ai = s_a[w][i];
+            }
+            const int j = ki + 1 + (t - exi);
+            const int c = out_col[j];
+            const int Dc = out_D[j];
+            const bool b_low = rank_less(Db, b, Dc, c);
+            const int ls = b_low ? bs : out_ptr[c];
+            const int le = b_low ? be : out_ptr[c + 1];
+            const int key = b_low ? c : b;
+            const int pos = ls + lower_bound_i32(out_col + ls, le - ls, key);
+            if (pos < le && out_col[pos] == key) {
+                const int64_t q = tq[Dab + Dc];
+                credit_slot<F64>(slots, out_pos[j], q, 1);
+                if (i != cur_i) {
+                    if (hit_b) credit_slot<F64>(slots, out_pos[s_k[w][cur_i]], acc_b, hit_b);
+                    cur_i = i;
+                    acc_b = 0;
+                    hit_b = 0;
+                }
+                acc_b += q;
+                ++hit_b;
+                const int a = ai;
+                if (a != cur_a) {
+                    if (hit_a) {
+                        atomicAdd((unsigned long long *)(q_own + cur_a), (unsigned long long)acc_a);
+                        atomicAdd((unsigned long long *)(t_own + cur_a), (unsigned long long)hit_a);
+                    }
+                    cur_a = a;
+                    acc_a = 0;
+                    hit_a = 0;
+                }
+                acc_a += q;
+                ++hit_a;
+            }
+        }
+        if (hit_b) credit_slot<F64>(slots, out_pos[s_k[w][cur_i]], acc_b, hit_b);
+        if (hit_a) {
+            atomicAdd((unsigned long long *)(q_own + cur_a), (unsigned long long)acc_a);
+            atomicAdd((unsigned long long *)(t_own + cur_a), (unsigned long long)hit_a);
+        }
+        __syncwarp();
     }
 }
 
 int launch_triangles(const Scratch &s, int precision, int32_t n, int64_t m, int num_sms, cudaStream_t st) {
-    int64_t g = (m / 2 + 255) / 256;
-    unsigned grid = (unsigned)(g < 1 ? 1 : (g > (int64_t)num_sms * 64 ? (int64_t)num_sms * 64 : g));
+    int64_t g = (m / 2 + TRI_WARPS * 32 - 1) / (TRI_WARPS * 32);
+    unsigned grid = (unsigned)(g < 1 ? 1 : (g > (int64_t)num_sms * 16 ? (int64_t)num_sms * 16 : g));
     if (precision == EF_PREC_FP64)
-        k_tri_edges<true><<<grid, 256, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_rslot, s.out_src, s.D, n, s.ftab,
-                                                s.slotR, s.slotT, s.Ccenter, s.t_own);
+        k_tri_pairs<true><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pos, s.out_src, s.D,
+                                                           n, s.tq, s.slot, s.q_own, s.t_own);
     else
-        k_tri_edges<false><<<grid, 256, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_rslot, s.out_src, s.D, n,
-                                                 s.ftab, s.slotR, s.slotT, s.Ccenter, s.t_own);
+        k_tri_pairs<false><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pos, s.out_src,
+                                                            s.D, n, s.tq, s.slot, s.q_own, s.t_own);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

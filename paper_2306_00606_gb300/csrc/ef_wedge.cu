@@ -4,9 +4,10 @@
 //     R_u(x) = sum_{j in N(u), j != x} f(D_u + D_x + D_j - 4),
 // and the middle node's own credit is sum over ordered pairs = sum_x R_u(x)
 // (each unordered pair (i, j) appears twice, matching the weight 2 that
-// Algorithm 1 gives the middle node).  R_u(x) is written to the slot of u in
-// x's row (slot rev[e] for e = (u -> x)), so every slot is written by exactly
-// one thread and each node later sums its own row: no atomics.
+// Algorithm 1 gives the middle node).  R_u(x) is written, with sigma1(u), to
+// u's own slot for x (position e of x in u's row): coalesced stores, one
+// writer per slot, no atomics.  The finalize pass gathers each node's slots
+// through the reverse-slot map.
 //
 // Precision modes: FP64 reads f from an FP64 table; FP32C evaluates
 // d log2 d with the MUFU lg2 unit, sums in FP32 with Kahan compensation per
@@ -22,12 +23,11 @@ namespace ef {
 // sums f over the other neighbours of the same middle node, fetched by shuffles.
 template <int G, bool F64>
 __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                                     const int32_t *__restrict__ D, const int32_t *__restrict__ rev,
+                                                     const int32_t *__restrict__ D, const int64_t *__restrict__ sig1,
                                                      const int32_t *__restrict__ list, const int32_t *__restrict__ cnt,
                                                      int bin, const double *__restrict__ ftab, void *__restrict__ slot_,
-                                                     double *__restrict__ Ccenter) {
+                                                     void *__restrict__ Ccenter) {
     using Acc = typename std::conditional<F64, double, float>::type;
-    Acc *slot = reinterpret_cast<Acc *>(slot_);
     constexpr int PER = 32 / G;
     const int lane = threadIdx.x & 31, grp = lane / G, k = lane % G;
     const int count = cnt[bin];
@@ -53,12 +53,10 @@ __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__
                 else acc += dlog2d(fmaxf((float)d, 1.0f));
             }
         }
-        double r = own ? (F64 ? (double)acc : (double)acc * LN2) : 0.0;
-        if (own) slot[rev[e]] = (Acc)r;
-        double c = r;
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o, G);
-        if (k == 0 && vc) Ccenter[u] = c;
+        const Acc r = own ? (F64 ? acc : acc * (Acc)LN2) : (Acc)0;
+        if (own) put_slot<F64>(slot_, e, r, vc ? (int32_t)sig1[u] : 0);
+        const Acc c = group_sum<G>(r);
+        if (k == 0 && vc) reinterpret_cast<Acc *>(Ccenter)[u] = c;
     }
 }
 
@@ -71,11 +69,10 @@ __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__
 template <bool F64>
 __global__ void __launch_bounds__(BIG_ROWS) k_wedge_big_direct(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
-    const int32_t *__restrict__ rev, const int32_t *__restrict__ list, int32_t *__restrict__ cnt,
+    const int64_t *__restrict__ sig1, const int32_t *__restrict__ list, int32_t *__restrict__ cnt,
     const int32_t *__restrict__ item_ptr, const double *__restrict__ ftab, void *__restrict__ slot_,
     double *__restrict__ partial) {
     using Acc = typename std::conditional<F64, double, float>::type;
-    Acc *slot = reinterpret_cast<Acc *>(slot_);
     using Elt = typename std::conditional<F64, int, float>::type;
     __shared__ __align__(16) Elt s_a[BIG_TILE];   // FP32C: D_j as float; FP64: D_j as a table offset
     __shared__ int s_item;
@@ -135,7 +132,7 @@ __global__ void __launch_bounds__(BIG_ROWS) k_wedge_big_direct(
                 double sum = ((double)s0 - (double)c0) + ((double)s1 - (double)c1);
                 r = (sum - (double)dlog2d(fb0 + (float)ak)) * LN2;
             }
-            slot[rev[start + k]] = (Acc)r;
+            put_slot<F64>(slot_, start + k, (Acc)r, (int32_t)sig1[u]);
         }
         double t = warp_sum(r);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = t;
@@ -149,14 +146,16 @@ __global__ void __launch_bounds__(BIG_ROWS) k_wedge_big_direct(
 }
 
 // Middle-node credit of each big node: ordered sum of its items' partials.
+template <bool F64>
 __global__ void k_big_reduce(const int32_t *__restrict__ list, const int32_t *__restrict__ cnt,
                              const int32_t *__restrict__ item_ptr, const double *__restrict__ partial,
-                             double *__restrict__ Ccenter) {
+                             void *__restrict__ Ccenter_) {
+    AccT<F64> *Ccenter = reinterpret_cast<AccT<F64> *>(Ccenter_);
     const int nb = cnt[BIN_BIG];
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
         double c = 0.0;
         for (int i = item_ptr[b]; i < item_ptr[b + 1]; ++i) c += partial[i];
-        Ccenter[list[b]] = c;
+        Ccenter[list[b]] = (AccT<F64>)c;
     }
 }
 
@@ -195,8 +194,8 @@ struct ClassEval<false> {
             kahan_add(s1, c1, q.w * dlog2d(fb + q.z));
         }
         if (j < K) kahan_add(s0, c0, cls[j].y * dlog2d(fb + cls[j].x));
-        const double sum = ((double)s0 - (double)c0) + ((double)s1 - (double)c1);
-        return (float)((sum - (double)dlog2d(fb + ci.x)) * LN2);
+        const float sum = (s0 - c0) + (s1 - c1);
+        return (sum - dlog2d(fb + ci.x)) * (float)LN2;
     }
 };
 
@@ -227,12 +226,11 @@ constexpr int MID_WARPS = 4;
 template <bool F64>
 __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
-    const int32_t *__restrict__ rev, const int32_t *__restrict__ list, const int32_t *__restrict__ cnt,
-    const double *__restrict__ ftab, void *__restrict__ slot_, double *__restrict__ Ccenter) {
+    const int64_t *__restrict__ sig1, const int32_t *__restrict__ list, const int32_t *__restrict__ cnt,
+    const double *__restrict__ ftab, void *__restrict__ slot_, void *__restrict__ Ccenter) {
     using E = ClassEval<F64>;
     using Cls = typename E::Cls;
     using R = typename E::R;
-    R *slot = reinterpret_cast<R *>(slot_);
     __shared__ int32_t s_hist[MID_WARPS][MID_HIST];
     __shared__ int32_t s_cidx[MID_WARPS][MID_MAX];
     __shared__ __align__(16) Cls s_cls[MID_WARPS][MID_MAX];
@@ -286,17 +284,18 @@ __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
             K += __popc(bal);
         }
         __syncwarp();
-        double center = 0.0;
+        SumAcc<R> center;
         for (int i = lane; i < K; i += 32) {
             const Cls c_i = cls[i];
             const R r = E::row(cls, K, base, c_i, ftab);
             cq[i] = r;
-            center += (double)E::cval(c_i) * (double)r;
+            center.add((R)E::cval(c_i) * r);
         }
         __syncwarp();
-        for (int k = lane; k < Du; k += 32) slot[rev[start + k]] = cq[cidx[k]];
-        center = warp_sum(center);
-        if (lane == 0) Ccenter[u] = center;
+        const int32_t sigu = (int32_t)sig1[u];
+        for (int k = lane; k < Du; k += 32) put_slot<F64>(slot_, start + k, cq[cidx[k]], sigu);
+        const R ctot = warp_sum(center.get());
+        if (lane == 0) reinterpret_cast<R *>(Ccenter)[u] = ctot;
         __syncwarp();
     }
 }
@@ -337,13 +336,12 @@ __device__ __forceinline__ int hub_scan(int x, int *s_w, int &total) {
 template <bool F64>
 __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
-    const int32_t *__restrict__ rev, const int32_t *__restrict__ bins, int32_t n, int32_t *__restrict__ cnt,
-    const double *__restrict__ ftab, void *__restrict__ slot_, double *__restrict__ Ccenter,
+    const int64_t *__restrict__ sig1, const int32_t *__restrict__ bins, int32_t n, int32_t *__restrict__ cnt,
+    const double *__restrict__ ftab, void *__restrict__ slot_, void *__restrict__ Ccenter,
     int32_t *__restrict__ cidx_g, void *__restrict__ cls_g_, void *__restrict__ q_g_) {
     using E = ClassEval<F64>;
     using Cls = typename E::Cls;
     using R = typename E::R;
-    R *slot = reinterpret_cast<R *>(slot_);
     Cls *cls_g = reinterpret_cast<Cls *>(cls_g_);
     R *q_g = reinterpret_cast<R *>(q_g_);
     extern __shared__ __align__(16) unsigned char hub_smem[];
@@ -432,14 +430,15 @@ __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
             center += (double)E::cval(c_i) * (double)r;
         }
         __syncthreads();
-        for (int k = tid; k < Du; k += HUB_THREADS) slot[rev[start + k]] = cq[cidx[k]];
+        const int32_t sigu = (int32_t)sig1[u];
+        for (int k = tid; k < Du; k += HUB_THREADS) put_slot<F64>(slot_, start + k, cq[cidx[k]], sigu);
         center = warp_sum(center);
         if ((tid & 31) == 0) s_red[tid >> 5] = center;
         __syncthreads();
         if (tid < 32) {
             double v = tid < HUB_THREADS / 32 ? s_red[tid] : 0.0;
             v = warp_sum(v);
-            if (tid == 0) Ccenter[u] = v;
+            if (tid == 0) reinterpret_cast<R *>(Ccenter)[u] = (R)v;
         }
     }
 }
@@ -450,14 +449,14 @@ template <bool F64>
 static void small_all(const int32_t *rp, const int32_t *ci, const Scratch &s, int32_t n, cudaStream_t st,
                       unsigned grid) {
     const int32_t *B = s.bins;
-    k_wedge_small<4, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.rev, B + (size_t)BIN_S4 * n, s.counters, BIN_S4,
-                                                s.ftab, s.slotR, s.Ccenter);
-    k_wedge_small<8, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.rev, B + (size_t)BIN_S8 * n, s.counters, BIN_S8,
-                                                s.ftab, s.slotR, s.Ccenter);
-    k_wedge_small<16, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.rev, B + (size_t)BIN_S16 * n, s.counters, BIN_S16,
-                                                 s.ftab, s.slotR, s.Ccenter);
-    k_wedge_small<32, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.rev, B + (size_t)BIN_S32 * n, s.counters, BIN_S32,
-                                                 s.ftab, s.slotR, s.Ccenter);
+    k_wedge_small<4, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.sig1, B + (size_t)BIN_S4 * n, s.counters, BIN_S4,
+                                                s.ftab, s.slot, s.Ccenter);
+    k_wedge_small<8, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.sig1, B + (size_t)BIN_S8 * n, s.counters, BIN_S8,
+                                                s.ftab, s.slot, s.Ccenter);
+    k_wedge_small<16, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.sig1, B + (size_t)BIN_S16 * n, s.counters, BIN_S16,
+                                                 s.ftab, s.slot, s.Ccenter);
+    k_wedge_small<32, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.sig1, B + (size_t)BIN_S32 * n, s.counters, BIN_S32,
+                                                 s.ftab, s.slot, s.Ccenter);
 }
 
 int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
@@ -474,14 +473,14 @@ static int big_classes(const int32_t *rp, const int32_t *ci, const Scratch &s, i
                        cudaStream_t st) {
     using E = ClassEval<F64>;
     const int32_t *mid = s.bins + (size_t)BIN_MID * n;
-    k_wedge_mid<F64><<<(unsigned)(num_sms * 8), MID_WARPS * 32, 0, st>>>(rp, ci, s.D, s.rev, mid, s.counters, s.ftab,
-                                                                         s.slotR, s.Ccenter);
+    k_wedge_mid<F64><<<(unsigned)(num_sms * 8), MID_WARPS * 32, 0, st>>>(rp, ci, s.D, s.sig1, mid, s.counters, s.ftab,
+                                                                         s.slot, s.Ccenter);
     const size_t smem = HUB_HIST * sizeof(int32_t) + HUB_SMEM_K * (sizeof(typename E::Cls) + sizeof(typename E::R));
     if (cudaFuncSetAttribute(k_wedge_hub<F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
     k_wedge_hub<F64><<<(unsigned)hub_grid(num_sms), HUB_THREADS, smem, st>>>(
-        rp, ci, s.D, s.rev, s.bins, n, s.counters, s.ftab, s.slotR, s.Ccenter, s.slotT, s.hub_cls, s.hub_q);
+        rp, ci, s.D, s.sig1, s.bins, n, s.counters, s.ftab, s.slot, s.Ccenter, s.hub_cidx, s.hub_cls, s.hub_q);
     return 0;
 }
 
@@ -492,13 +491,17 @@ int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int
     if (wedge_mode == 1) {
         unsigned grid = (unsigned)(num_sms * 4);
         if (precision == EF_PREC_FP64)
-            k_wedge_big_direct<true><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, s.rev, big, s.counters, s.big_chunks,
-                                                                s.ftab, s.slotR, s.big_partial);
+            k_wedge_big_direct<true><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, s.sig1, big, s.counters, s.big_chunks,
+                                                                s.ftab, s.slot, s.big_partial);
         else
-            k_wedge_big_direct<false><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, s.rev, big, s.counters, s.big_chunks,
-                                                                 s.ftab, s.slotR, s.big_partial);
-        k_big_reduce<<<(unsigned)(num_sms * 2), 256, 0, st>>>(big, s.counters, s.big_chunks, s.big_partial,
-                                                              s.Ccenter);
+            k_wedge_big_direct<false><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, s.sig1, big, s.counters, s.big_chunks,
+                                                                 s.ftab, s.slot, s.big_partial);
+        if (precision == EF_PREC_FP64)
+            k_big_reduce<true><<<(unsigned)(num_sms * 2), 256, 0, st>>>(big, s.counters, s.big_chunks,
+                                                                        s.big_partial, s.Ccenter);
+        else
+            k_big_reduce<false><<<(unsigned)(num_sms * 2), 256, 0, st>>>(big, s.counters, s.big_chunks,
+                                                                         s.big_partial, s.Ccenter);
     } else {
         int rc = precision == EF_PREC_FP64 ? big_classes<true>(rp, ci, s, n, num_sms, st)
                                            : big_classes<false>(rp, ci, s, n, num_sms, st);
