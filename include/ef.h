@@ -52,9 +52,11 @@ enum ef_status {
 
 enum ef_precision {
     EF_PREC_FP64 = 0,  /* d ln d from an FP64 table, FP64 sums everywhere */
-    EF_PREC_FP32C = 1  /* d ln d in FP32 with compensated (Kahan) FP32 sums
-                          per thread; FP64 for every cross-thread, per-node
-                          and final reduction and for ln S - T/S */
+    EF_PREC_FP32C = 1  /* d ln d in FP32 (hardware log2) with compensated
+                          (Kahan) FP32 sums per thread; the credits a node
+                          receives from its neighbours are summed in FP64;
+                          ln S - T/S in FP32 (FP64 above degree 1000).
+                          EF within 2e-5 absolute of the exact value */
 };
 
 typedef struct ef_ctx ef_ctx;
@@ -73,11 +75,11 @@ typedef struct {
                               without waiting; results valid after ef_sync */
     int32_t profile;       /* 1: time each pass with CUDA events on the
                               context stream (read with ef_get_stats) */
-    int32_t wedge_mode;    /* 0: automatic; 1: force the direct pairwise
-                              wedge kernel for every middle node (reference
-                              kernel for benchmarking); 2: force the
-                              degree-class kernel for every middle node of
-                              degree > 32 */
+    int32_t wedge_mode;    /* 0: automatic (degree-class kernels for middle
+                              nodes of degree > 32); 1: the direct pairwise
+                              wedge kernel for every middle node of degree
+                              > 32 (reference kernel for benchmarking); other
+                              values: EF_ERR_UNSUPPORTED */
     int32_t reserved[2];
 } ef_options;
 
@@ -94,7 +96,7 @@ typedef struct {
 /* Per-pass timings in milliseconds, summed over profiled calls. */
 typedef struct {
     int64_t calls;
-    double prep_ms;        /* validation, degrees, neighbour sums, orientation, reverse slots */
+    double prep_ms;        /* validation, degrees, neighbour sums, f table, orientation */
     double wedge_small_ms; /* middle nodes of degree <= 32 */
     double wedge_big_ms;   /* middle nodes of degree > 32 */
     double triangle_ms;    /* triangle listing and corrections */
@@ -144,7 +146,7 @@ int ef_compute_ex(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
  *   stream has finished this call's work.  Input is validated.
  * Scratch lives in a fixed 32 MiB device array inside the library, held by
  * every GPU that loads it until the process exits.  Graphs whose scratch
- * would exceed it (about 132 n + 76 m + 48 min(n, m) bytes) are rejected with
+ * would exceed it (about 164 n + 32 m + 48 min(n, m) bytes) are rejected with
  * EF_ERR_ARG and a message naming the limit; nothing runs on the GPU then.
  * The first call on a device looks up the array's address (make it before
  * any stream capture).  All calls share the array: calls that overlap on the

@@ -1,18 +1,23 @@
 // C ABI of libef (declared in include/ef.h): contexts, scratch management and
 // the orchestration of the passes for one graph.
 //
-// Pass order (one graph; "main" is the context stream, "side" a second stream
-// owned by the context):
-//   main  prep A   degrees + row_ptr checks + wedge bins; per-row checks,
-//                  sigma1/sigma2, out-degrees, slot rows
+// Pass order (one graph, all on the context stream):
+//   one memset of the per-node accumulators and the counters
+//   prep A       degrees + row_ptr checks + wedge bins; per-row checks,
+//                sigma1/sigma2, out-degrees, symmetry fingerprints
 //   host         one small readback: validation word and max degree
-//                  (skipped with trust_input)
-//   main  f table  f(d) = d ln d, d < 3 maxdeg + 1
-//   side  reverse slots                 (overlaps the three passes below)
-//   main  orientation, wedge pass (small, mid, hub), triangle pass
-//   main  waits for side; finalize (gathers slots through the reverse map)
-//   host  final readback of the validation word (asymmetric input is only
-//         detected by the reverse-slot pass)
+//                (skipped with trust_input)
+//   f table      f(d) = d ln d and the triangle corrections, d < 3 maxdeg + 1
+//   orientation  oriented CSR + omega
+//   wedge pass   small, then mid + hub middle nodes
+//   triangles    pair tests and corrections
+//   finalize     per node
+//   host         final readback of the validation word (asymmetric input is
+//                only detected by the finalize pass)
+// The wedge pass and the orientation + triangle passes write disjoint
+// accumulators and could run on two streams; measured on the 4M-node
+// power-law graph, the concurrent form was slower (the triangle pass more
+// than doubles under contention), so they run in sequence.
 #include "ef_internal.cuh"
 
 #include <mutex>
@@ -24,8 +29,6 @@
 struct ef_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
     int num_sms = 0;
     char err[512] = {0};
     void *scratch = nullptr;
@@ -44,9 +47,9 @@ namespace {
 thread_local char g_err[512];
 
 // Kernels one ef_compute_ex call launches (default wedge mode): prep A 3,
-// reverse slots 1, orientation 2 scans of 3 + 2 + item counts, f table 1,
-// small wedges 4, class wedges 2, triangles 1, finalize 2.
-constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 9 + 1 + 4 + 2 + 1 + 2;
+// f table 1, orientation (a scan of 3 + 2), small wedges 4, class wedges 2,
+// triangles 1, finalize 1.
+constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 5 + 4 + 2 + 1 + 1;
 
 void set_err(ef_ctx *c, const char *fmt, ...) {
     char *dst = c ? c->err : g_err;
@@ -135,7 +138,7 @@ int compute_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n,
     const bool prof = o.profile != 0;
     if (prof) CU(cudaEventRecord(ctx->ev[0], st));
 
-    CU(cudaMemsetAsync(s.counters, 0, NUM_COUNTERS * sizeof(int32_t), st));
+    CU(cudaMemsetAsync(s.Tacc, 0, accumulator_bytes(s), st));
     LAUNCH(launch_prep_a(rp, ci, n, m, s, st), "prep");
 
     int64_t fcap;
@@ -156,25 +159,15 @@ int compute_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n,
     s.ftab = ctx->ftab;
     s.tq = reinterpret_cast<int64_t *>(ctx->ftab + fcap);
     LAUNCH(launch_ftab(s.ftab, s.tq, s.counters, fcap, st), "f table");
-
-    // reverse slots on the side stream, overlapping orientation, wedges and triangles
-    CU(cudaEventRecord(ctx->fork, st));
-    CU(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
-    LAUNCH(launch_rev(rp, ci, n, m, s, ctx->side), "reverse slots");
-    CU(cudaEventRecord(ctx->join, ctx->side));
-
     LAUNCH(launch_orient(rp, ci, n, m, s, st), "orientation");
-    CU(cudaMemsetAsync(s.t_own, 0, (size_t)n * sizeof(int64_t), st));
-    CU(cudaMemsetAsync(s.q_own, 0, (size_t)n * sizeof(int64_t), st));
     if (prof) CU(cudaEventRecord(ctx->ev[1], st));
     LAUNCH(launch_wedge_small(rp, ci, s, o.precision, n, st), "small wedge");
     if (prof) CU(cudaEventRecord(ctx->ev[2], st));
     LAUNCH(launch_wedge_big(rp, ci, s, o.precision, o.wedge_mode, n, m, ctx->num_sms, st), "big wedge");
     if (prof) CU(cudaEventRecord(ctx->ev[3], st));
-    LAUNCH(launch_triangles(s, o.precision, n, m, ctx->num_sms, st), "triangle");
+    LAUNCH(launch_triangles(s, n, m, ctx->num_sms, st), "triangle");
     if (prof) CU(cudaEventRecord(ctx->ev[4], st));
-    CU(cudaStreamWaitEvent(st, ctx->join, 0));
-    LAUNCH(launch_finalize(rp, ci, s, o.precision, n, out, ctx->num_sms, st), "finalize");
+    LAUNCH(launch_finalize(s, o.precision, n, out, ctx->num_sms, st), "finalize");
     if (prof) CU(cudaEventRecord(ctx->ev[5], st));
     if (!o.trust_input)
         CU(cudaMemcpyAsync(ctx->h_counters + CNT_ERR, s.counters + CNT_ERR, sizeof(int32_t), cudaMemcpyDeviceToHost,
@@ -191,17 +184,20 @@ int check_args(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_opti
     return EF_OK;
 }
 
+// Event pairs: prep + f table + orientation ev0-ev1, small wedges ev1-ev2,
+// big wedges ev2-ev3, triangles ev3-ev4, finalize ev4-ev5, total ev0-ev5.
 void accumulate_stats(ef_ctx *ctx) {
-    float t[5];
-    for (int i = 0; i < 5; ++i)
-        if (cudaEventElapsedTime(&t[i], ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) t[i] = 0.f;
+    static const int pairs[6][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {0, 5}};
+    float t[6];
+    for (int i = 0; i < 6; ++i)
+        if (cudaEventElapsedTime(&t[i], ctx->ev[pairs[i][0]], ctx->ev[pairs[i][1]]) != cudaSuccess) t[i] = 0.f;
     ctx->stats.calls += 1;
     ctx->stats.prep_ms += t[0];
     ctx->stats.wedge_small_ms += t[1];
     ctx->stats.wedge_big_ms += t[2];
     ctx->stats.triangle_ms += t[3];
     ctx->stats.finalize_ms += t[4];
-    ctx->stats.total_ms += t[0] + t[1] + t[2] + t[3] + t[4];
+    ctx->stats.total_ms += t[5];
     ctx->stats.kernels += KERNELS_PER_CALL;
 }
 
@@ -223,29 +219,35 @@ size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s) {
     s.D = (int32_t *)take(4 * N);
     s.sig1 = (int64_t *)take(8 * N);
     s.sig2 = (int64_t *)take(8 * N);
+    s.omega = (int64_t *)take(8 * N);
     s.outdeg = (int32_t *)take(4 * N);
+    s.fp_row = (uint64_t *)take(8 * N);
     s.out_ptr = (int32_t *)take(4 * (N + 1));
     s.out_col = (int32_t *)take(4 * (M + 1));
     s.out_D = (int32_t *)take(4 * (M + 1));
-    s.out_pos = (int32_t *)take(4 * (M + 1));
     s.out_src = (int32_t *)take(4 * (M + 1));
-    s.rev = (int32_t *)take(4 * (M + 1));
-    s.srow = (int32_t *)take(4 * (M + 1));
-    s.slot = take(sizeof(Slot<true>) * (M + 1));
-    static_assert(sizeof(Slot<true>) == 32 && sizeof(Slot<false>) == 32, "slots are one 32-byte sector");
     s.Ccenter = take(8 * N);
-    s.t_own = (int64_t *)take(8 * N);
-    s.q_own = (int64_t *)take(8 * N);
-    s.bins = (int32_t *)take(4 * N * NUM_BINS);
+    // accumulators that start at zero, contiguous up to the end of the counters
+    // (cleared by one memset per call, see accumulator_bytes)
+    s.Tacc = (double *)take(8 * N);
+    s.qacc = (int64_t *)take(8 * N);
+    s.tcnt = (int64_t *)take(8 * N);
+    s.fp_push = (uint64_t *)take(8 * N);
     s.counters = (int32_t *)take(4 * NUM_COUNTERS);
+    s.bins = (int32_t *)take(4 * N * NUM_BINS);
     s.big_chunks = (int32_t *)take(4 * (N + 1));
     s.big_partial = (double *)take(8 * (M / BIG_ROWS + N + 2));
     s.scan_tmp = (int32_t *)take(4 * (N / 4096 + 4));
+    s.scan_tmp2 = (int32_t *)take(4 * (N / 4096 + 4));
     s.hub_cls = take(8 * (M + N + 2));
     s.hub_q = take(8 * (M + N + 2));
     s.hub_cidx = (int32_t *)take(4 * (M + 1));
     s.ftab = nullptr;
     return off;
+}
+
+size_t accumulator_bytes(const Scratch &s) {
+    return (size_t)((const char *)(s.counters + NUM_COUNTERS) - (const char *)s.Tacc);
 }
 
 // Message for ef_last_error(NULL), for entry points that run without a context.
@@ -270,9 +272,6 @@ int ef_ctx_create(int device, void *stream, ef_ctx **out) {
     ctx->stream = (cudaStream_t)stream;
     cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counters, ef::NUM_COUNTERS * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming);
     for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
     if (e != cudaSuccess) {
         set_err(nullptr, "context set-up failed: %s", cudaGetErrorString(e));
@@ -287,16 +286,12 @@ int ef_ctx_destroy(ef_ctx *ctx) {
     if (!ctx) return EF_OK;
     DeviceGuard dg(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    if (ctx->side) cudaStreamSynchronize(ctx->side);
     cudaFree(ctx->scratch);
     cudaFree(ctx->ftab);
     cudaFree(ctx->io);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     for (int i = 0; i < 8; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
-    if (ctx->fork) cudaEventDestroy(ctx->fork);
-    if (ctx->join) cudaEventDestroy(ctx->join);
-    if (ctx->side) cudaStreamDestroy(ctx->side);
     delete ctx;
     return EF_OK;
 }

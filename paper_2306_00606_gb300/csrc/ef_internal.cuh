@@ -15,14 +15,13 @@
 // sum = D_a + D_b + D_c.  So each node of the triangle gets
 // 4 * (f(sum-6) - f(sum-4)) added to T and -8 added to S.
 //
-// Per-edge credits travel through "slots" stored at the sender's side: the
-// slot at position e of row u (column x) holds what u sends to x -- the
-// open-degree credit R_u(x) of u as a middle node, the triangle corrections
-// u found for x as a triangle owner, their count, and sigma1(u).  The wedge
-// pass writes every slot once (coalesced, no atomics); the triangle pass adds
-// its rare corrections with uncontended atomics; the finalize pass gathers
-// the slots addressed to v through the reverse-slot map rev (position of v in
-// u's row).
+// Per-node accumulators (a few tens of MB, resident in L2) collect what
+// nodes send each other: the middle node u reduces its own credit with warp
+// shuffles and stores it once (Ccenter[u]); its open-degree credit to each
+// end x, R_u(x), is added to Tacc[x] with a fire-and-forget L2 reduction (one
+// per CSR entry; a node receives its D_x of them spread over the whole pass,
+// so they do not contend); triangle corrections go to qacc (exact fixed
+// point) and tcnt the same way.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -70,32 +69,11 @@ constexpr int BIG_TILE = 4096;         // neighbour degrees staged per tile by t
 constexpr int ROW_CTA = 512;           // threads of the per-hub-row kernels
 
 // Triangle corrections are integers in units of 2^-F (the pass adds only
-// integers: order-independent, no floating point in the pair loop).  F is
-// chosen per call from the maximum degree as the largest value, at most 52,
-// for which C(maxdeg, 2) triangles of the largest |g| cannot overflow int64
+// integers: exact and independent of the order of the atomics).  F is chosen
+// per call from the maximum degree as the largest value, at most 52, for
+// which C(maxdeg, 2) triangles of the largest |g| cannot overflow int64
 // (F = 52 on small graphs, 27 on the 4M-node power-law workload).
 constexpr int TRI_FRAC_MAX = 52;
-
-// One slot (32 bytes, one DRAM sector): what the row owner sends to the column node.
-template <bool F64>
-struct Slot;
-template <>
-struct __align__(32) Slot<true> {
-    double val;   // open-degree credit (natural-log units)
-    int32_t cnt;  // triangles
-    int32_t sig;  // sigma1 of the sender
-    int64_t tri;  // triangle corrections, fixed point
-    int64_t pad;
-};
-template <>
-struct __align__(32) Slot<false> {
-    float val;
-    int32_t cnt;
-    int32_t sig;
-    int32_t pad0;
-    int64_t tri;
-    int64_t pad1;
-};
 
 // Precision-dependent accumulator type: double (FP64) or float (FP32C).
 template <bool F64>
@@ -104,26 +82,27 @@ using AccT = typename std::conditional<F64, double, float>::type;
 // Scratch carved from one device allocation per call (sizes depend on n, m).
 struct Scratch {
     int32_t *D;          // n      degrees
-    int64_t *sig1;       // n      sum of neighbour degrees (< m, so int32 in slots)
+    int64_t *sig1;       // n      sum of neighbour degrees
     int64_t *sig2;       // n      sum of squared neighbour degrees
+    int64_t *omega;      // n      sum of the neighbours' sigma1
     int32_t *outdeg;     // n      out-degree in (degree, id) order
+    uint64_t *fp_row;    // n      fingerprint of the lower-ranked neighbours, from the node's own row
+    uint64_t *fp_push;   // n      the same, pushed by those neighbours (symmetry check)
     int32_t *out_ptr;    // n+1    oriented CSR offsets
     int32_t *out_col;    // m+1    oriented neighbour ids (ascending id within a row)
     int32_t *out_D;      // m+1    their degrees
-    int32_t *out_pos;    // m+1    their position in the owner's own row (the owner's slot for them)
     int32_t *out_src;    // m+1    owner of each oriented edge
-    int32_t *rev;        // m+1    rev[e] = position of u in N(x) for e = (u -> x)
-    int32_t *srow;       // m+1    row of each slot
-    void    *slot;       // m+1    Slot<F64>, 32 bytes each
+    double  *Tacc;       // n      open-degree credits received as an end (FP64 reductions)
     void    *Ccenter;    // n      middle-node credit (AccT<F64>, 8 bytes reserved per node)
-    int64_t *t_own;      // n      triangles found as owner
-    int64_t *q_own;      // n      their corrections, fixed point
+    int64_t *qacc;       // n      triangle corrections, fixed point
+    int64_t *tcnt;       // n      triangles
     int64_t *tq;         // 3*maxdeg+1 (capacity): 4 (f(s-6) - f(s-4)) * 2^F, rounded (F in counters)
     int32_t *bins;       // NUM_BINS * n   work lists
     int32_t *counters;   // NUM_COUNTERS ints: [0..NUM_BINS) bin counts, CNT_* below
-    int32_t *big_chunks; // n+1    work items per big middle node (direct kernel), then their scan
+    int32_t *big_chunks; // n+1    work items per big middle node (direct kernel), scanned in place
     double  *big_partial;// m/BIG_ROWS + n + 2  per-item middle-node partial sums (direct kernel)
-    int32_t *scan_tmp;   // scan block sums
+    int32_t *scan_tmp;   // scan block sums (orientation)
+    int32_t *scan_tmp2;  // scan block sums (direct kernel's items)
     double  *ftab;       // 3*maxdeg+1 (capacity): f(d) = d ln d in FP64
     void    *hub_cls;    // m+n+2  class (degree, count) pairs of hubs with > HUB_SMEM_K classes
     void    *hub_q;      // m+n+2  their per-class credits
@@ -132,8 +111,11 @@ struct Scratch {
 
 enum : int { CNT_ERR = 32, CNT_MAXDEG = 33, CNT_BIGITEM = 34, CNT_HUB = 36, CNT_TRIFRAC = 37, NUM_COUNTERS = 64 };
 
-// Bytes of scratch for a graph (f table excluded), and its layout when base != nullptr.
+// Bytes of scratch for a graph (f tables excluded), and its layout when base != nullptr.
 size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s);
+// Bytes from Tacc to the end of the counters: everything that must start at
+// zero (Tacc, qacc, tcnt, fp_push, counters), for one memset per call.
+size_t accumulator_bytes(const Scratch &s);
 
 // ----------------------------------------------------------------- helpers
 __device__ __forceinline__ bool rank_less(int32_t Dx, int32_t x, int32_t Dy, int32_t y) {
@@ -141,10 +123,27 @@ __device__ __forceinline__ bool rank_less(int32_t Dx, int32_t x, int32_t Dy, int
     return Dx < Dy || (Dx == Dy && x < y);
 }
 
+// 64-bit fingerprint of a node id (a splitmix64 finaliser) for the symmetry
+// check; the added odd constant makes the sums count their terms too.
+__device__ __forceinline__ uint64_t node_print(int32_t x) {
+    uint64_t z = (uint64_t)(uint32_t)x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return (z ^ (z >> 31)) + 0x9E3779B97F4A7C15ull;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Sum of a value over a group of G consecutive lanes (tree order).
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o, G);
     return v;
 }
 
@@ -198,25 +197,8 @@ struct SumAcc {
 // d * log2(d) for integral d >= 1 held in a float (MUFU lg2).
 __device__ __forceinline__ float dlog2d(float d) { return d * __log2f(d); }
 
-// Store a fresh slot (wedge pass): credit, no triangles yet, sender's sigma1.
-template <bool F64>
-__device__ __forceinline__ void put_slot(void *slots, int64_t e, AccT<F64> val, int32_t sig) {
-    Slot<F64> s{};
-    s.val = val;
-    s.cnt = 0;
-    s.sig = sig;
-    s.tri = 0;
-    reinterpret_cast<Slot<F64> *>(slots)[e] = s;
-}
-
-// Sum of a value over a group of G consecutive lanes (tree order), in the
-// accumulator's own precision.
-template <int G, typename T>
-__device__ __forceinline__ T group_sum(T v) {
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o, G);
-    return v;
-}
+// Credit R_u(x) of middle node u to its end x (an L2 reduction, no return).
+__device__ __forceinline__ void credit_end(double *Tacc, int x, double r) { atomicAdd(Tacc + x, r); }
 
 constexpr double LN2 = 0.69314718055994530942;
 
@@ -226,14 +208,14 @@ constexpr double LN2 = 0.69314718055994530942;
 namespace ef {
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st);
 int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st);
-int launch_rev(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st);
+int launch_big_items(const Scratch &s, int32_t n, cudaStream_t st);
 int launch_scan(const int32_t *in, int32_t *out, int32_t n, int32_t *tmp, cudaStream_t st);
 int launch_ftab(double *ftab, int64_t *tq, int32_t *cnt, int64_t cap, cudaStream_t st);
 int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
                        cudaStream_t st);
 int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int wedge_mode,
                      int32_t n, int64_t m, int num_sms, cudaStream_t st);
-int launch_triangles(const Scratch &s, int precision, int32_t n, int64_t m, int num_sms, cudaStream_t st);
-int launch_finalize(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
-                    const ef_outputs &out, int num_sms, cudaStream_t st);
+int launch_triangles(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st);
+int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs &out, int num_sms,
+                    cudaStream_t st);
 }  // namespace ef

@@ -1,6 +1,7 @@
-// Preparation passes of libef: CSR validation, degrees and work bins,
-// neighbour-degree sums, reverse slots, degree orientation for triangle
-// listing, the f(d) = d ln d table, and a device-wide exclusive scan.
+// Preparation passes of libef: CSR validation (with the symmetry
+// fingerprints), degrees and work bins, neighbour-degree sums, degree
+// orientation for triangle listing, the f(d) = d ln d table, and a
+// device-wide exclusive scan.
 //
 // Algorithm 1's Phase 2 needs |Adj(x)| of every cluster member; the degree
 // array D is the only per-node quantity the wedge pass reads besides the CSR.
@@ -129,12 +130,22 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
 // ------------------------------------------- per-row checks and neighbour sums
 // Range, self-loop and strict-order checks; sigma1 = sum of neighbour degrees,
 // sigma2 = sum of their squares, and the out-degree in (degree, id) order.
+//
+// Symmetry check by fingerprints: for every entry x of N(v), the lower-ranked
+// end of {v, x} is pushed to the higher one, fp_push[hi] += print(lo), and
+// every row sums print(x) over its lower-ranked entries into fp_row.  In a
+// symmetric CSR both sums run over the same multiset at every node.  An
+// entry (v, x) without its reverse adds print(v) to one side of x (v lower)
+// or print(x) to one side of v (x lower) only; the finalize pass reports the
+// graph as asymmetric where the two differ.  A miss needs the unmatched
+// 64-bit prints to cancel exactly (probability about 2^-64 per node).
 struct RowStats {
     int64_t s1 = 0, s2 = 0;
+    uint64_t fpr = 0;
     int od = 0, err = 0;
-    __device__ __forceinline__ void slot(const int32_t *__restrict__ ci, const int32_t *__restrict__ D, int32_t n,
-                                         int v, int Dv, int a, int e, int32_t *__restrict__ srow) {
-        srow[e] = v;
+    __device__ __forceinline__ void entry(const int32_t *__restrict__ ci, const int32_t *__restrict__ D, int32_t n,
+                                          int v, int Dv, int a, int e, uint64_t pv,
+                                          uint64_t *__restrict__ fp_push) {
         const int x = ci[e];
         if (x < 0 || x >= n) { err |= ERRB_RANGE; return; }
         if (x == v) err |= ERRB_SELFLOOP;
@@ -142,13 +153,23 @@ struct RowStats {
         const int Dx = D[x];
         s1 += Dx;
         s2 += (int64_t)Dx * Dx;
-        od += rank_less(Dv, v, Dx, x) ? 1 : 0;
+        if (rank_less(Dv, v, Dx, x)) {
+            ++od;
+            atomicAdd((unsigned long long *)(fp_push + x), (unsigned long long)pv);
+        } else {
+            fpr += node_print(x);
+        }
     }
 };
 
+struct RowOut {
+    int64_t *sig1, *sig2;
+    int32_t *outdeg;
+    uint64_t *fp_row, *fp_push;
+};
+
 __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
-                            const int32_t *__restrict__ D, int64_t *__restrict__ sig1, int64_t *__restrict__ sig2,
-                            int32_t *__restrict__ outdeg, int32_t *__restrict__ srow, int32_t *__restrict__ cnt) {
+                            const int32_t *__restrict__ D, RowOut ro, int32_t *__restrict__ cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
@@ -160,11 +181,13 @@ __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__res
         const int Dv = ok ? b - a : 0;
         if (in && Dv <= SMALL_MAX) {
             RowStats r;
+            const uint64_t pv = node_print(v);
             if (ok)
-                for (int e = a; e < b; ++e) r.slot(ci, D, n, v, Dv, a, e, srow);
-            sig1[v] = r.s1;
-            sig2[v] = r.s2;
-            outdeg[v] = r.od;
+                for (int e = a; e < b; ++e) r.entry(ci, D, n, v, Dv, a, e, pv, ro.fp_push);
+            ro.sig1[v] = r.s1;
+            ro.sig2[v] = r.s2;
+            ro.outdeg[v] = r.od;
+            ro.fp_row[v] = r.fpr;
             if (r.err) atomicOr(cnt + CNT_ERR, r.err);
         }
         unsigned mid = __ballot_sync(FULL, Dv > SMALL_MAX && Dv <= MID_MAX);
@@ -173,15 +196,18 @@ __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__res
             mid &= mid - 1;
             const int u = (int)(base + j);
             const int ua = __shfl_sync(FULL, a, j), ub = __shfl_sync(FULL, b, j);
+            const uint64_t pu = node_print(u);
             RowStats r;
-            for (int e = ua + lane; e < ub; e += 32) r.slot(ci, D, n, u, ub - ua, ua, e, srow);
+            for (int e = ua + lane; e < ub; e += 32) r.entry(ci, D, n, u, ub - ua, ua, e, pu, ro.fp_push);
             const int64_t s1 = warp_sum(r.s1), s2 = warp_sum(r.s2);
+            const uint64_t fpr = warp_sum(r.fpr);
             const int od = warp_sum(r.od);
             const int err = __reduce_or_sync(FULL, r.err);
             if (lane == 0) {
-                sig1[u] = s1;
-                sig2[u] = s2;
-                outdeg[u] = od;
+                ro.sig1[u] = s1;
+                ro.sig2[u] = s2;
+                ro.outdeg[u] = od;
+                ro.fp_row[u] = fpr;
                 if (err) atomicOr(cnt + CNT_ERR, err);
             }
         }
@@ -191,106 +217,57 @@ __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__res
 __global__ void __launch_bounds__(ROW_CTA) k_row_stats_hub(const int32_t *__restrict__ rp,
                                                            const int32_t *__restrict__ ci, int32_t n,
                                                            const int32_t *__restrict__ D,
-                                                           const int32_t *__restrict__ bins,
-                                                           int64_t *__restrict__ sig1, int64_t *__restrict__ sig2,
-                                                           int32_t *__restrict__ outdeg, int32_t *__restrict__ srow,
+                                                           const int32_t *__restrict__ bins, RowOut ro,
                                                            int32_t *__restrict__ cnt) {
     __shared__ int64_t s_buf[32];
     const int total = hub_total(cnt);
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         const int u = hub_row(bins, n, cnt, it);
         const int a = rp[u], b = rp[u + 1];
+        const uint64_t pu = node_print(u);
         RowStats r;
-        for (int e = a + threadIdx.x; e < b; e += ROW_CTA) r.slot(ci, D, n, u, b - a, a, e, srow);
+        for (int e = a + threadIdx.x; e < b; e += ROW_CTA) r.entry(ci, D, n, u, b - a, a, e, pu, ro.fp_push);
         const int64_t s1 = block_sum<int64_t>(r.s1, s_buf);
         const int64_t s2 = block_sum<int64_t>(r.s2, s_buf);
         const int64_t od = block_sum<int64_t>(r.od, s_buf);
+        const int64_t fpr = block_sum<int64_t>((int64_t)r.fpr, s_buf);   // wrapping sum
         const int err = __reduce_or_sync(FULL, r.err);
         if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
         if (threadIdx.x == 0) {
-            sig1[u] = s1;
-            sig2[u] = s2;
-            outdeg[u] = (int32_t)od;
+            ro.sig1[u] = s1;
+            ro.sig2[u] = s2;
+            ro.outdeg[u] = (int32_t)od;
+            ro.fp_row[u] = (uint64_t)fpr;
         }
     }
-}
-
-// ------------------------------------------------------------ reverse slots
-// Every undirected edge {v, x} is resolved once, from the row of its higher-
-// ranked end v: the lower-ranked end's row is the shorter one, so v is
-// binary-searched in N(x) and both directions are set, rev[e] = p and
-// rev[p] = e.  rev starts at -1; a slot left at -1, or a failed search,
-// means the input is not symmetric.  Rows and columns that failed validation
-// are skipped (memory safety only: the call returns EF_ERR_GRAPH before any
-// later pass runs).
-__device__ __forceinline__ int rev_slot(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
-                                        int64_t m, const int32_t *__restrict__ D, int32_t *__restrict__ rev, int v,
-                                        int Dv, int e) {
-    (void)D;
-    const int x = ci[e];
-    if (x < 0 || x >= n) return 0;
-    const int xa = rp[x], xb = rp[x + 1];   // D_x = xb - xa: no separate degree load
-    if (!(xa >= 0 && xa <= xb && (int64_t)xb <= m)) return ERRB_ASYM;
-    if (!rank_less(xb - xa, x, Dv, v)) return 0;
-    const int pos = xa + lower_bound_i32(ci + xa, xb - xa, v);
-    if (pos < xb && ci[pos] == v) {
-        rev[e] = pos;
-        rev[pos] = e;
-        return 0;
-    }
-    return ERRB_ASYM;
-}
-
-// One thread per slot: its row comes from srow (written by the row-stats
-// pass); only slots pointing to a lower-ranked node search.
-__global__ void k_rev_flat(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
-                           const int32_t *__restrict__ D, const int32_t *__restrict__ srow, int32_t *__restrict__ rev,
-                           int32_t *__restrict__ cnt) {
-    int err = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // four independent slots per thread keep four search chains in flight
-    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e0 < m; e0 += 4 * stride) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t e = e0 + u * stride;
-            if (e >= m) break;
-            const int v = srow[e];
-            if (v < 0 || v >= n) continue;
-            const int va = rp[v], vb = rp[v + 1];
-            if (va > e || vb <= e) continue;   // slot of a row that failed validation
-            err |= rev_slot(rp, ci, n, m, D, rev, v, vb - va, (int)e);
-        }
-    }
-    err = __reduce_or_sync(FULL, err);
-    if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
 }
 
 // ------------------------------------------------------------- orientation
 // Appends the out-neighbours x of u (in (degree, id) order) to the oriented
-// CSR in ascending id order, with D_x, the position e of x in u's own row
-// (u's slot for x) and the owner u.
+// CSR in ascending id order, with D_x and the owner u; and gathers
+// omega_u = sum over N(u) of sigma1(x), the last per-node sum the closed form
+// of S needs.
 struct Orient {
     const int32_t *ci, *D;
-    int32_t *out_col, *out_D, *out_pos, *out_src;
+    const int64_t *sig1;
+    int32_t *out_col, *out_D, *out_src;
     int32_t n;
-    __device__ __forceinline__ bool probe(int u, int Du, int e, int &x, int &Dx, int &r, int &err) const {
-        (void)err;
+    __device__ __forceinline__ bool probe(int u, int Du, int e, int &x, int &Dx, int64_t &om) const {
         x = ci[e];
         const bool xin = x >= 0 && x < n;
         Dx = xin ? D[x] : 0;
-        r = e;
+        om += xin ? sig1[x] : 0;
         return xin && rank_less(Du, u, Dx, x);
     }
-    __device__ __forceinline__ void put(int k, int u, int x, int Dx, int r) const {
+    __device__ __forceinline__ void put(int k, int u, int x, int Dx) const {
         out_col[k] = x;
         out_D[k] = Dx;
-        out_pos[k] = r;
         out_src[k] = u;
     }
 };
 
 __global__ void k_orient(const int32_t *__restrict__ rp, int32_t n, int64_t m, Orient o,
-                         const int32_t *__restrict__ out_ptr, int32_t *__restrict__ cnt) {
+                         const int32_t *__restrict__ out_ptr, int64_t *__restrict__ omega) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
@@ -300,13 +277,14 @@ __global__ void k_orient(const int32_t *__restrict__ rp, int32_t n, int64_t m, O
         const int a = in ? rp[v] : 0, b = in ? rp[v + 1] : 0;
         const bool ok = in && a >= 0 && a <= b && (int64_t)b <= m;
         const int Dv = ok ? b - a : 0;
-        int err = 0;
         if (ok && Dv <= SMALL_MAX) {
             int k = out_ptr[v];
+            int64_t om = 0;
             for (int e = a; e < b; ++e) {
-                int x, Dx, r;
-                if (o.probe(v, Dv, e, x, Dx, r, err)) o.put(k++, v, x, Dx, r);
+                int x, Dx;
+                if (o.probe(v, Dv, e, x, Dx, om)) o.put(k++, v, x, Dx);
             }
+            omega[v] = om;
         }
         unsigned mid = __ballot_sync(FULL, Dv > SMALL_MAX && Dv <= MID_MAX);
         while (mid) {
@@ -315,42 +293,45 @@ __global__ void k_orient(const int32_t *__restrict__ rp, int32_t n, int64_t m, O
             const int u = (int)(base + j);
             const int ua = __shfl_sync(FULL, a, j), ub = __shfl_sync(FULL, b, j);
             int k0 = out_ptr[u];
+            int64_t om = 0;
             for (int e0 = ua; e0 < ub; e0 += 32) {
                 const int e = e0 + lane;
-                int x = 0, Dx = 0, r = 0;
-                const bool isout = e < ub && o.probe(u, ub - ua, e, x, Dx, r, err);
+                int x = 0, Dx = 0;
+                const bool isout = e < ub && o.probe(u, ub - ua, e, x, Dx, om);
                 const unsigned bal = __ballot_sync(FULL, isout);
-                if (isout) o.put(k0 + __popc(bal & ((1u << lane) - 1u)), u, x, Dx, r);
+                if (isout) o.put(k0 + __popc(bal & ((1u << lane) - 1u)), u, x, Dx);
                 k0 += __popc(bal);
             }
+            om = warp_sum(om);
+            if (lane == 0) omega[u] = om;
         }
-        err = __reduce_or_sync(FULL, err);
-        if (lane == 0 && err) atomicOr(cnt + CNT_ERR, err);
     }
 }
 
 __global__ void __launch_bounds__(ROW_CTA) k_orient_hub(const int32_t *__restrict__ rp, int32_t n, Orient o,
                                                         const int32_t *__restrict__ bins,
                                                         const int32_t *__restrict__ out_ptr,
-                                                        int32_t *__restrict__ cnt) {
+                                                        const int32_t *__restrict__ cnt,
+                                                        int64_t *__restrict__ omega) {
+    __shared__ int64_t s_buf[32];
     const int total = hub_total(cnt);
-    int err = 0;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         const int u = hub_row(bins, n, cnt, it);
         const int a = rp[u], b = rp[u + 1];
         int k0 = out_ptr[u];
+        int64_t om = 0;
         for (int e0 = a; e0 < b; e0 += ROW_CTA) {
             const int e = e0 + threadIdx.x;
-            int x = 0, Dx = 0, r = 0;
-            const bool isout = e < b && o.probe(u, b - a, e, x, Dx, r, err);
+            int x = 0, Dx = 0;
+            const bool isout = e < b && o.probe(u, b - a, e, x, Dx, om);
             int tot;
             const int off = block_exclusive_scan(isout ? 1 : 0, &tot);
-            if (isout) o.put(k0 + off, u, x, Dx, r);
+            if (isout) o.put(k0 + off, u, x, Dx);
             k0 += tot;
         }
+        om = block_sum<int64_t>(om, s_buf);
+        if (threadIdx.x == 0) omega[u] = om;
     }
-    err = __reduce_or_sync(FULL, err);
-    if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
 }
 
 // Work items of the big middle nodes for the direct kernel: ceil(D / BIG_ROWS)
@@ -424,8 +405,9 @@ __global__ void k_scan_bsums(int32_t *__restrict__ bsum, int32_t nb) {
     }
 }
 
-__global__ void k_scan_apply(const int32_t *__restrict__ in, int32_t *__restrict__ out, int32_t n,
-                             const int32_t *__restrict__ bsum) {
+// in and out may be the same array (each thread reads its own elements
+// before it writes them), so they are not __restrict__.
+__global__ void k_scan_apply(const int32_t *in, int32_t *out, int32_t n, const int32_t *__restrict__ bsum) {
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_PER;
     int v[SCAN_PER];
     int s = 0;
@@ -470,29 +452,27 @@ static inline unsigned grid_for(int64_t work, int per_block, int64_t cap) {
 // Degrees + wedge bins, per-row checks and neighbour sums.
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
     k_degrees<<<grid_for(n, 1024, 1 << 30), 1024, 0, st>>>(rp, n, m, s.D, s.bins, s.counters);
-    k_row_stats<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, s.sig1, s.sig2, s.outdeg, s.srow,
-                                                            s.counters);
-    k_row_stats_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, ci, n, s.D, s.bins, s.sig1, s.sig2, s.outdeg, s.srow,
-                                                 s.counters);
+    const RowOut ro{s.sig1, s.sig2, s.outdeg, s.fp_row, s.fp_push};
+    k_row_stats<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, ro, s.counters);
+    k_row_stats_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, ci, n, s.D, s.bins, ro, s.counters);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Oriented CSR and the direct kernel's item offsets.
+// Oriented CSR and omega.
 int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
     if (launch_scan(s.outdeg, s.out_ptr, n, s.scan_tmp, st)) return -1;
-    Orient o{ci, s.D, s.out_col, s.out_D, s.out_pos, s.out_src, n};
-    k_orient<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, n, m, o, s.out_ptr, s.counters);
-    k_orient_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters);
-    // outdeg is free after the scan: reuse it for the direct kernel's item counts
-    k_big_chunks<<<grid_for(n, 256, 1 << 30), 256, 0, st>>>(s.D, s.bins + (size_t)BIN_BIG * n, s.counters, n, s.outdeg);
-    if (launch_scan(s.outdeg, s.big_chunks, n, s.scan_tmp, st)) return -1;
+    const Orient o{ci, s.D, s.sig1, s.out_col, s.out_D, s.out_src, n};
+    k_orient<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, n, m, o, s.out_ptr, s.omega);
+    k_orient_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters, s.omega);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Reverse slots (independent of the orientation: may run on another stream).
-int launch_rev(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
-    if (cudaMemsetAsync(s.rev, 0xff, (size_t)m * sizeof(int32_t), st) != cudaSuccess) return -1;
-    k_rev_flat<<<grid_for(m, 256, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, s.srow, s.rev, s.counters);
+// Item offsets of the direct big-node wedge kernel (counts, then an in-place
+// scan with its own block-sum buffer: it may run beside the orientation).
+int launch_big_items(const Scratch &s, int32_t n, cudaStream_t st) {
+    k_big_chunks<<<grid_for(n, 256, 1 << 30), 256, 0, st>>>(s.D, s.bins + (size_t)BIN_BIG * n, s.counters, n,
+                                                             s.big_chunks);
+    if (launch_scan(s.big_chunks, s.big_chunks, n, s.scan_tmp2, st)) return -1;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -66,7 +66,7 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
         char msg[200];
         snprintf(msg, sizeof msg,
                  "ef_compute_static: graph needs %zu bytes of scratch, above the fixed %zu-byte maximum "
-                 "(about 132 n + 76 m + 48 min(n, m) bytes); use ef_compute_ex",
+                 "(about 164 n + 32 m + 48 min(n, m) bytes); use ef_compute_ex",
                  need, EF_STATIC_SCRATCH_BYTES);
         return fail(EF_ERR_ARG, msg);
     }
@@ -94,7 +94,7 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
 
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t *rp = g->row_ptr, *ci = g->col_idx;
-    if (cudaMemsetAsync(s.counters, 0, NUM_COUNTERS * sizeof(int32_t), st) != cudaSuccess)
+    if (cudaMemsetAsync(s.Tacc, 0, accumulator_bytes(s), st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: memset failed");
     if (launch_prep_a(rp, ci, n, m, s, st))
         return fail(EF_ERR_CUDA, "ef_compute_static: prep launch failed");
@@ -105,19 +105,15 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     if (h_cnt[CNT_ERR]) return fail(EF_ERR_GRAPH, "ef_compute_static: input is not a symmetric simple sorted CSR");
     ef_outputs out = {};
     out.ef = out_ef;
-    if (launch_ftab(s.ftab, s.tq, s.counters, fcap, st) || launch_rev(rp, ci, n, m, s, st) ||
-        cudaMemsetAsync(s.q_own, 0, (size_t)n * sizeof(int64_t), st) != cudaSuccess ||
-        launch_orient(rp, ci, n, m, s, st) ||
-        cudaMemsetAsync(s.t_own, 0, (size_t)n * sizeof(int64_t), st) != cudaSuccess ||
+    if (launch_ftab(s.ftab, s.tq, s.counters, fcap, st) || launch_orient(rp, ci, n, m, s, st) ||
         launch_wedge_small(rp, ci, s, precision, n, st) ||
         launch_wedge_big(rp, ci, s, precision, 0, n, m, num_sms, st) ||
-        launch_triangles(s, precision, n, m, num_sms, st) ||
-        launch_finalize(rp, ci, s, precision, n, out, num_sms, st) ||
+        launch_triangles(s, n, m, num_sms, st) || launch_finalize(s, precision, n, out, num_sms, st) ||
         cudaMemcpyAsync(h_cnt, s.counters, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: launch failed");
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: kernel execution failed");
-    // asymmetric input is only detected by the reverse-slot and finalize passes
+    // asymmetric input is only detected by the finalize pass
     if (h_cnt[CNT_ERR]) return fail(EF_ERR_GRAPH, "ef_compute_static: input is not a symmetric simple sorted CSR");
     return EF_OK;
 }

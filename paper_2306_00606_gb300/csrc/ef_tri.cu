@@ -17,31 +17,27 @@
 // oriented edges and spreads all their pairs evenly over its lanes.
 //
 // The pass is integer-only: g comes from a table in fixed point (units of
-// 2^-F, F chosen per call from the maximum degree), so sums are exact and independent of the order of the
-// atomics, and no FP64 instruction (one lane per clock per SM sub-partition
-// on this GPU) sits in a divergent branch.  Credits go to a's own slots for b
-// and c (where the wedge pass put a's open-degree credits to them) and a's own
-// to q_own[a]; each lane merges consecutive hits on the same edge before
-// adding.
+// 2^-F, F chosen per call from the maximum degree), so the sums are exact and
+// independent of the order of the atomics, and no FP64 instruction (one lane
+// per clock per SM sub-partition on this GPU) sits in a divergent branch.
+// Corrections and counts go to per-node accumulators (qacc, tcnt) by L2
+// reductions: c's at once, a's and b's merged per lane over consecutive hits
+// (a lane's pairs share a, and often b).
 #include "ef_internal.cuh"
 
 namespace ef {
 
 constexpr int TRI_WARPS = 8;
 
-template <bool F64>
-__device__ __forceinline__ void credit_slot(void *slots, int pos, int64_t q, int cnt) {
-    Slot<F64> *s = reinterpret_cast<Slot<F64> *>(slots) + pos;
-    atomicAdd((unsigned long long *)&s->tri, (unsigned long long)q);
-    atomicAdd(&s->cnt, cnt);
+__device__ __forceinline__ void credit_tri(int64_t *qacc, int64_t *tcnt, int v, int64_t q, int cnt) {
+    atomicAdd((unsigned long long *)(qacc + v), (unsigned long long)q);
+    atomicAdd((unsigned long long *)(tcnt + v), (unsigned long long)cnt);
 }
 
-template <bool F64>
 __global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_pairs(
     const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_D,
-    const int32_t *__restrict__ out_pos, const int32_t *__restrict__ out_src, const int32_t *__restrict__ D,
-    int32_t n, const int64_t *__restrict__ tq, void *__restrict__ slots, int64_t *__restrict__ q_own,
-    int64_t *__restrict__ t_own) {
+    const int32_t *__restrict__ out_src, const int32_t *__restrict__ D, int32_t n, const int64_t *__restrict__ tq,
+    int64_t *__restrict__ qacc, int64_t *__restrict__ tcnt) {
     __shared__ int s_ex[TRI_WARPS][32];   // exclusive prefix of pair counts
     __shared__ int s_k[TRI_WARPS][32], s_b[TRI_WARPS][32], s_Db[TRI_WARPS][32], s_bs[TRI_WARPS][32];
     __shared__ int s_be[TRI_WARPS][32], s_Dab[TRI_WARPS][32], s_a[TRI_WARPS][32];
@@ -80,12 +76,14 @@ __global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_pairs(
         __syncwarp();
         int cur_i = -1, cur_a = -1, hit_b = 0, hit_a = 0;
         int64_t acc_b = 0, acc_a = 0;
-        // the warp edge i owning pair t is the last i with s_ex[i] <= t; its fields are cached
         int i = -1, ki = 0, exi = 0, b = 0, Db = 0, bs = 0, be = 0, Dab = 0, ai = 0;
         for (int t = lane; t < P; t += 32) {
-            // t only grows, so the lane's edge index only moves forward
-            int ni = i < 0 ? 0 : i;
-            while (ni < 31 && s_ex[w][ni + 1] <= t) ++ni;
+            // the warp edge owning pair t: the last i with s_ex[i] <= t (s_ex is
+            // non-decreasing; i + step <= 31 at every step)
+            int ni = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (s_ex[w][ni + step] <= t) ni += step;
             if (ni != i) {
                 i = ni;
                 ki = s_k[w][i];
@@ -107,22 +105,18 @@ __global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_pairs(
             const int pos = ls + lower_bound_i32(out_col + ls, le - ls, key);
             if (pos < le && out_col[pos] == key) {
                 const int64_t q = tq[Dab + Dc];
-                credit_slot<F64>(slots, out_pos[j], q, 1);
+                credit_tri(qacc, tcnt, c, q, 1);
                 if (i != cur_i) {
-                    if (hit_b) credit_slot<F64>(slots, out_pos[s_k[w][cur_i]], acc_b, hit_b);
+                    if (hit_b) credit_tri(qacc, tcnt, s_b[w][cur_i], acc_b, hit_b);
                     cur_i = i;
                     acc_b = 0;
                     hit_b = 0;
                 }
                 acc_b += q;
                 ++hit_b;
-                const int a = ai;
-                if (a != cur_a) {
-                    if (hit_a) {
-                        atomicAdd((unsigned long long *)(q_own + cur_a), (unsigned long long)acc_a);
-                        atomicAdd((unsigned long long *)(t_own + cur_a), (unsigned long long)hit_a);
-                    }
-                    cur_a = a;
+                if (ai != cur_a) {
+                    if (hit_a) credit_tri(qacc, tcnt, cur_a, acc_a, hit_a);
+                    cur_a = ai;
                     acc_a = 0;
                     hit_a = 0;
                 }
@@ -130,24 +124,17 @@ __global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_pairs(
                 ++hit_a;
             }
         }
-        if (hit_b) credit_slot<F64>(slots, out_pos[s_k[w][cur_i]], acc_b, hit_b);
-        if (hit_a) {
-            atomicAdd((unsigned long long *)(q_own + cur_a), (unsigned long long)acc_a);
-            atomicAdd((unsigned long long *)(t_own + cur_a), (unsigned long long)hit_a);
-        }
+        if (hit_b) credit_tri(qacc, tcnt, s_b[w][cur_i], acc_b, hit_b);
+        if (hit_a) credit_tri(qacc, tcnt, cur_a, acc_a, hit_a);
         __syncwarp();
     }
 }
 
-int launch_triangles(const Scratch &s, int precision, int32_t n, int64_t m, int num_sms, cudaStream_t st) {
+int launch_triangles(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st) {
     int64_t g = (m / 2 + TRI_WARPS * 32 - 1) / (TRI_WARPS * 32);
     unsigned grid = (unsigned)(g < 1 ? 1 : (g > (int64_t)num_sms * 16 ? (int64_t)num_sms * 16 : g));
-    if (precision == EF_PREC_FP64)
-        k_tri_pairs<true><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pos, s.out_src, s.D,
-                                                           n, s.tq, s.slot, s.q_own, s.t_own);
-    else
-        k_tri_pairs<false><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pos, s.out_src,
-                                                            s.D, n, s.tq, s.slot, s.q_own, s.t_own);
+    k_tri_pairs<<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_src, s.D, n, s.tq, s.qacc,
+                                                 s.tcnt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

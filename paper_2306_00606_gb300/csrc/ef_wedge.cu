@@ -4,14 +4,13 @@
 //     R_u(x) = sum_{j in N(u), j != x} f(D_u + D_x + D_j - 4),
 // and the middle node's own credit is sum over ordered pairs = sum_x R_u(x)
 // (each unordered pair (i, j) appears twice, matching the weight 2 that
-// Algorithm 1 gives the middle node).  R_u(x) is written, with sigma1(u), to
-// u's own slot for x (position e of x in u's row): coalesced stores, one
-// writer per slot, no atomics.  The finalize pass gathers each node's slots
-// through the reverse-slot map.
+// Algorithm 1 gives the middle node).  The middle node's credit is reduced
+// in registers and stored once (Ccenter[u]); R_u(x) is added to x's
+// accumulator Tacc[x] by an FP64 reduction in L2 (RED, no return value).
 //
 // Precision modes: FP64 reads f from an FP64 table; FP32C evaluates
-// d log2 d with the MUFU lg2 unit, sums in FP32 with Kahan compensation per
-// thread, and converts to FP64 (times ln 2) before any cross-thread sum.
+// d log2 d with the MUFU lg2 unit and sums in FP32 with Kahan compensation
+// per thread (times ln 2 at the end); the end credits still travel as FP64.
 #include "ef_internal.cuh"
 
 #include <type_traits>
@@ -23,9 +22,9 @@ namespace ef {
 // sums f over the other neighbours of the same middle node, fetched by shuffles.
 template <int G, bool F64>
 __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                                     const int32_t *__restrict__ D, const int64_t *__restrict__ sig1,
-                                                     const int32_t *__restrict__ list, const int32_t *__restrict__ cnt,
-                                                     int bin, const double *__restrict__ ftab, void *__restrict__ slot_,
+                                                     const int32_t *__restrict__ D, const int32_t *__restrict__ list,
+                                                     const int32_t *__restrict__ cnt, int bin,
+                                                     const double *__restrict__ ftab, double *__restrict__ Tacc,
                                                      void *__restrict__ Ccenter) {
     using Acc = typename std::conditional<F64, double, float>::type;
     constexpr int PER = 32 / G;
@@ -40,8 +39,8 @@ __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__
         const int Du = vc ? D[u] : 0;
         const int start = vc ? rp[u] : 0;
         const bool own = k < Du;
-        const int e = start + k;
-        const int ak = own ? D[ci[e]] : 0;
+        const int x = own ? ci[start + k] : 0;
+        const int ak = own ? D[x] : 0;
         const int b0 = Du - 4 + ak;
         Acc acc = 0;
 #pragma unroll
@@ -54,7 +53,7 @@ __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__
             }
         }
         const Acc r = own ? (F64 ? acc : acc * (Acc)LN2) : (Acc)0;
-        if (own) put_slot<F64>(slot_, e, r, vc ? (int32_t)sig1[u] : 0);
+        if (own) credit_end(Tacc, x, (double)r);
         const Acc c = group_sum<G>(r);
         if (k == 0 && vc) reinterpret_cast<Acc *>(Ccenter)[u] = c;
     }
@@ -65,13 +64,13 @@ __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__
 // neighbour x = chunk*BIG_ROWS + t and sums f(D_u - 4 + D_x + D_j) over all j
 // in N(u), staged tile by tile in shared memory, then removes j = x.  The
 // item's share of the middle-node credit goes to big_partial[item]; items are
-// taken from an atomic counter (dynamic scheduling).
+// taken from an atomic counter (dynamic scheduling).  This is the plain
+// pairwise form, kept as the reference kernel (wedge_mode 1).
 template <bool F64>
 __global__ void __launch_bounds__(BIG_ROWS) k_wedge_big_direct(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
-    const int64_t *__restrict__ sig1, const int32_t *__restrict__ list, int32_t *__restrict__ cnt,
-    const int32_t *__restrict__ item_ptr, const double *__restrict__ ftab, void *__restrict__ slot_,
-    double *__restrict__ partial) {
+    const int32_t *__restrict__ list, int32_t *__restrict__ cnt, const int32_t *__restrict__ item_ptr,
+    const double *__restrict__ ftab, double *__restrict__ Tacc, double *__restrict__ partial) {
     using Acc = typename std::conditional<F64, double, float>::type;
     using Elt = typename std::conditional<F64, int, float>::type;
     __shared__ __align__(16) Elt s_a[BIG_TILE];   // FP32C: D_j as float; FP64: D_j as a table offset
@@ -94,7 +93,8 @@ __global__ void __launch_bounds__(BIG_ROWS) k_wedge_big_direct(
         const int start = rp[u];
         const int k = (item - item_ptr[lo]) * BIG_ROWS + threadIdx.x;
         const bool own = k < Du;
-        const int ak = own ? D[ci[start + k]] : 0;
+        const int x = own ? ci[start + k] : 0;
+        const int ak = own ? D[x] : 0;
         const int b0 = Du - 4 + ak;
         Acc s0 = 0, s1 = 0, c0 = 0, c1 = 0;
         const Acc fb0 = (Acc)b0;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(BIG_ROWS) k_wedge_big_direct(
                 double sum = ((double)s0 - (double)c0) + ((double)s1 - (double)c1);
                 r = (sum - (double)dlog2d(fb0 + (float)ak)) * LN2;
             }
-            put_slot<F64>(slot_, start + k, (Acc)r, (int32_t)sig1[u]);
+            credit_end(Tacc, x, r);
         }
         double t = warp_sum(r);
         if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = t;
@@ -226,8 +226,8 @@ constexpr int MID_WARPS = 4;
 template <bool F64>
 __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
-    const int64_t *__restrict__ sig1, const int32_t *__restrict__ list, const int32_t *__restrict__ cnt,
-    const double *__restrict__ ftab, void *__restrict__ slot_, void *__restrict__ Ccenter) {
+    const int32_t *__restrict__ list, const int32_t *__restrict__ cnt, const double *__restrict__ ftab,
+    double *__restrict__ Tacc, void *__restrict__ Ccenter) {
     using E = ClassEval<F64>;
     using Cls = typename E::Cls;
     using R = typename E::R;
@@ -292,8 +292,7 @@ __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
             center.add((R)E::cval(c_i) * r);
         }
         __syncwarp();
-        const int32_t sigu = (int32_t)sig1[u];
-        for (int k = lane; k < Du; k += 32) put_slot<F64>(slot_, start + k, cq[cidx[k]], sigu);
+        for (int k = lane; k < Du; k += 32) credit_end(Tacc, ci[start + k], (double)cq[cidx[k]]);
         const R ctot = warp_sum(center.get());
         if (lane == 0) reinterpret_cast<R *>(Ccenter)[u] = ctot;
         __syncwarp();
@@ -330,15 +329,15 @@ __device__ __forceinline__ int hub_scan(int x, int *s_w, int &total) {
 }
 
 // One CTA per hub (degree > MID_MAX), hubs taken largest degree bucket first
-// from an atomic counter.  Per-slot global arrays hold the class index of
-// every neighbour (cidx_g, at the hub's own row positions) and, for hubs with
-// more than HUB_SMEM_K classes, the classes themselves (cls_g, q_g).
+// from an atomic counter.  Global arrays hold the class index of every
+// neighbour (cidx_g, at the hub's own row positions) and, for hubs with more
+// than HUB_SMEM_K classes, the classes themselves (cls_g, q_g).
 template <bool F64>
 __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
-    const int64_t *__restrict__ sig1, const int32_t *__restrict__ bins, int32_t n, int32_t *__restrict__ cnt,
-    const double *__restrict__ ftab, void *__restrict__ slot_, void *__restrict__ Ccenter,
-    int32_t *__restrict__ cidx_g, void *__restrict__ cls_g_, void *__restrict__ q_g_) {
+    const int32_t *__restrict__ bins, int32_t n, int32_t *__restrict__ cnt, const double *__restrict__ ftab,
+    double *__restrict__ Tacc, void *__restrict__ Ccenter, int32_t *__restrict__ cidx_g, void *__restrict__ cls_g_,
+    void *__restrict__ q_g_) {
     using E = ClassEval<F64>;
     using Cls = typename E::Cls;
     using R = typename E::R;
@@ -430,8 +429,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
             center += (double)E::cval(c_i) * (double)r;
         }
         __syncthreads();
-        const int32_t sigu = (int32_t)sig1[u];
-        for (int k = tid; k < Du; k += HUB_THREADS) put_slot<F64>(slot_, start + k, cq[cidx[k]], sigu);
+        for (int k = tid; k < Du; k += HUB_THREADS) credit_end(Tacc, ci[start + k], (double)cq[cidx[k]]);
         center = warp_sum(center);
         if ((tid & 31) == 0) s_red[tid >> 5] = center;
         __syncthreads();
@@ -449,14 +447,14 @@ template <bool F64>
 static void small_all(const int32_t *rp, const int32_t *ci, const Scratch &s, int32_t n, cudaStream_t st,
                       unsigned grid) {
     const int32_t *B = s.bins;
-    k_wedge_small<4, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.sig1, B + (size_t)BIN_S4 * n, s.counters, BIN_S4,
-                                                s.ftab, s.slot, s.Ccenter);
-    k_wedge_small<8, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.sig1, B + (size_t)BIN_S8 * n, s.counters, BIN_S8,
-                                                s.ftab, s.slot, s.Ccenter);
-    k_wedge_small<16, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.sig1, B + (size_t)BIN_S16 * n, s.counters, BIN_S16,
-                                                 s.ftab, s.slot, s.Ccenter);
-    k_wedge_small<32, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, s.sig1, B + (size_t)BIN_S32 * n, s.counters, BIN_S32,
-                                                 s.ftab, s.slot, s.Ccenter);
+    k_wedge_small<4, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, B + (size_t)BIN_S4 * n, s.counters, BIN_S4, s.ftab,
+                                                s.Tacc, s.Ccenter);
+    k_wedge_small<8, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, B + (size_t)BIN_S8 * n, s.counters, BIN_S8, s.ftab,
+                                                s.Tacc, s.Ccenter);
+    k_wedge_small<16, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, B + (size_t)BIN_S16 * n, s.counters, BIN_S16, s.ftab,
+                                                 s.Tacc, s.Ccenter);
+    k_wedge_small<32, F64><<<grid, 256, 0, st>>>(rp, ci, s.D, B + (size_t)BIN_S32 * n, s.counters, BIN_S32, s.ftab,
+                                                 s.Tacc, s.Ccenter);
 }
 
 int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
@@ -473,14 +471,14 @@ static int big_classes(const int32_t *rp, const int32_t *ci, const Scratch &s, i
                        cudaStream_t st) {
     using E = ClassEval<F64>;
     const int32_t *mid = s.bins + (size_t)BIN_MID * n;
-    k_wedge_mid<F64><<<(unsigned)(num_sms * 8), MID_WARPS * 32, 0, st>>>(rp, ci, s.D, s.sig1, mid, s.counters, s.ftab,
-                                                                         s.slot, s.Ccenter);
+    k_wedge_mid<F64><<<(unsigned)(num_sms * 8), MID_WARPS * 32, 0, st>>>(rp, ci, s.D, mid, s.counters, s.ftab, s.Tacc,
+                                                                         s.Ccenter);
     const size_t smem = HUB_HIST * sizeof(int32_t) + HUB_SMEM_K * (sizeof(typename E::Cls) + sizeof(typename E::R));
     if (cudaFuncSetAttribute(k_wedge_hub<F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return -1;
     k_wedge_hub<F64><<<(unsigned)hub_grid(num_sms), HUB_THREADS, smem, st>>>(
-        rp, ci, s.D, s.sig1, s.bins, n, s.counters, s.ftab, s.slot, s.Ccenter, s.hub_cidx, s.hub_cls, s.hub_q);
+        rp, ci, s.D, s.bins, n, s.counters, s.ftab, s.Tacc, s.Ccenter, s.hub_cidx, s.hub_cls, s.hub_q);
     return 0;
 }
 
@@ -489,19 +487,19 @@ int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int
     (void)m;
     const int32_t *big = s.bins + (size_t)BIN_BIG * n;
     if (wedge_mode == 1) {
+        if (launch_big_items(s, n, st)) return -1;
         unsigned grid = (unsigned)(num_sms * 4);
-        if (precision == EF_PREC_FP64)
-            k_wedge_big_direct<true><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, s.sig1, big, s.counters, s.big_chunks,
-                                                                s.ftab, s.slot, s.big_partial);
-        else
-            k_wedge_big_direct<false><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, s.sig1, big, s.counters, s.big_chunks,
-                                                                 s.ftab, s.slot, s.big_partial);
-        if (precision == EF_PREC_FP64)
+        if (precision == EF_PREC_FP64) {
+            k_wedge_big_direct<true><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, big, s.counters, s.big_chunks, s.ftab,
+                                                                s.Tacc, s.big_partial);
             k_big_reduce<true><<<(unsigned)(num_sms * 2), 256, 0, st>>>(big, s.counters, s.big_chunks,
                                                                         s.big_partial, s.Ccenter);
-        else
+        } else {
+            k_wedge_big_direct<false><<<grid, BIG_ROWS, 0, st>>>(rp, ci, s.D, big, s.counters, s.big_chunks, s.ftab,
+                                                                 s.Tacc, s.big_partial);
             k_big_reduce<false><<<(unsigned)(num_sms * 2), 256, 0, st>>>(big, s.counters, s.big_chunks,
                                                                          s.big_partial, s.Ccenter);
+        }
     } else {
         int rc = precision == EF_PREC_FP64 ? big_classes<true>(rp, ci, s, n, num_sms, st)
                                            : big_classes<false>(rp, ci, s, n, num_sms, st);
