@@ -37,10 +37,56 @@ WORKLOADS = {
     "ba1m": (2, "Barabasi-Albert n=1000000 m=5 seed=20230608"),
     "er2000": (1, "Erdos-Renyi G(n=2000, p=0.004) seed=20230607"),
 }
-MUFU_PER_SM_CLK = 16     # lg2 results per SM per clock (MUFU pipe)
-NUM_SMS = 152
-SM_MAX_MHZ = 2070.0
-L2_BYTES = 129 * 2 ** 20
+PASSES = ("prep_ms", "orient_ms", "wedge_small_ms", "wedge_big_ms", "tri_hash_ms", "tri_pairs_ms", "finalize_ms")
+PASS_KERNEL = {"prep_ms": "k_degrees+k_row_stats+k_row_stats_hub+k_ftab",
+               "orient_ms": "scan+k_orient+k_orient_hub", "wedge_small_ms": "k_wedge_small<4,8,16,32>",
+               "wedge_big_ms": "k_wedge_mid+k_wedge_hub", "tri_hash_ms": "k_out_hash",
+               "tri_pairs_ms": "k_tri_pairs", "finalize_ms": "k_finalize"}
+PASS_NOTE = {"prep_ms": "bound by random L2 gathers of neighbour degrees",
+             "orient_ms": "bound by random L2 gathers of neighbour degrees and sigma1",
+             "wedge_small_ms": "bound by MUFU lg2 and FP32 adds (one f evaluation per ordered pair)",
+             "wedge_big_ms": "bound by MUFU lg2 and FP32 adds over degree classes, and L2 reductions",
+             "tri_hash_ms": "bound by L2 atomics",
+             "tri_pairs_ms": "bound by dependent L2 round trips (1.1e8 membership tests), not HBM bandwidth",
+             "finalize_ms": "streaming, HBM-bound"}
+
+
+def algorithmic_bytes(g, st):
+    """Bytes each pass must move at least once (inputs read once, outputs
+    written once; gathers that hit L2 are not counted)."""
+    n, m = g.n, g.nnz
+    d = g.degrees.astype(np.int64)
+    small = d[(d >= 1) & (d <= 32)]
+    big = d[d > 32]
+    csr = 4 * (n + 1) + 4 * m
+    return {
+        # row_ptr + col_idx read; D, sigma1, sigma2, outdeg, fp_row written
+        "prep_ms": csr + 4 * n + 16 * n + 4 * n + 8 * n,
+        # CSR + outdeg read; out_ptr, out_col/out_D/out_src (m/2 each), omega written
+        "orient_ms": csr + 4 * n + 4 * (n + 1) + 12 * (m // 2) + 8 * n,
+        # rows of the middle nodes read; Ccenter written, one 8-byte credit per row entry
+        "wedge_small_ms": 4 * len(small) * 2 + 4 * int(small.sum()) + 8 * len(small) + 8 * int(small.sum()),
+        "wedge_big_ms": 4 * len(big) * 2 + 4 * int(big.sum()) + 8 * len(big) + 8 * int(big.sum()),
+        # out_ptr + out_col read, tables written (2 slots per entry of a long list)
+        "tri_hash_ms": 4 * (n + 1) + 4 * (m // 2) + 8 * (m // 2),
+        # out_ptr, out_col, out_D, out_src read; qacc, tcnt written
+        "tri_pairs_ms": 4 * (n + 1) + 12 * (m // 2) + 16 * n,
+        # D and 9 eight-byte per-node arrays read, EF written
+        "finalize_ms": 4 * n + 9 * 8 * n + 8 * n,
+    }
+
+
+def committed_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json), or None when there is none for this workload or
+    the kernel's source has changed since it was taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[workload][kernel]
+        h = hashlib.sha256(open(os.path.join(ROOT, rec["source"]), "rb").read()).hexdigest()[:16]
+        return rec["dram_bytes_per_launch"] if h == rec["source_sha256_16"] else None
+    except (OSError, KeyError, ValueError, TypeError):
+        return None
 
 
 def parse():
@@ -53,6 +99,9 @@ def parse():
     p.add_argument("--precision", choices=["fp32c", "fp64"], default="fp32c")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="shrink the workload's node count (small cases for profiling; not a bench line)")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     return p.parse_args()
 
 
@@ -198,7 +247,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     idx, desc = WORKLOADS[args.workload]
-    g = synth.workload(idx)
+    g = synth.workload(idx, args.scale)
+    if args.scale != 1.0:
+        desc += f" scaled by {args.scale}"
     st = graph_stats(g)
     rp = torch.from_numpy(g.row_ptr).to(dev)
     ci = torch.from_numpy(g.col_idx).to(dev)
@@ -241,49 +292,49 @@ def run_ours(args):
     value = st["W"] * args.steps * world / (ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers (H2D + compute + D2H) ----
-    h_rp = torch.from_numpy(g.row_ptr).pin_memory()
-    h_ci = torch.from_numpy(g.col_idx).pin_memory()
-    h_out = torch.empty(n, dtype=torch.float64).pin_memory()
-    for _ in range(2):
-        ef.ef_compute_ex(ctx.handle, h_rp, h_ci, precision=args.precision, ef=h_out, host_io=True)
-    barrier()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ef.ef_compute_ex(ctx.handle, h_rp, h_ci, precision=args.precision, ef=h_out, host_io=True)
-    torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = st["W"] * args.steps * world / e2e_s
     h2d = 4 * (n + 1) + 4 * g.nnz
     d2h = 8 * n
+    e2e = None
+    if not args.no_e2e:
+        h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+        h_ci = torch.from_numpy(g.col_idx).pin_memory()
+        h_out = torch.empty(n, dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            ef.ef_compute_ex(ctx.handle, h_rp, h_ci, precision=args.precision, ef=h_out, host_io=True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ef.ef_compute_ex(ctx.handle, h_rp, h_ci, precision=args.precision, ef=h_out, host_io=True)
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": st["W"] * args.steps * world / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
 
     # ---- roofline of the dominant pass ----
-    per = {k: passes[k] / max(passes["calls"], 1) for k in
-           ("prep_ms", "wedge_small_ms", "wedge_big_ms", "triangle_ms", "finalize_ms", "total_ms")}
+    per = {k: passes[k] / max(passes["calls"], 1) for k in PASSES + ("total_ms",)}
     clocks = clk.summary()
-    dom = max(("prep_ms", "wedge_small_ms", "wedge_big_ms", "triangle_ms", "finalize_ms"), key=lambda k: per[k])
-    peak_evals = NUM_SMS * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6
-    if dom in ("wedge_big_ms", "wedge_small_ms"):
-        evals = st["big_evals"] if dom == "wedge_big_ms" else st["small_evals"]
-        achieved = evals / (per[dom] / 1e3)
-        roofline = {"kernel": dom[:-3], "bound": "alu", "achieved": achieved / 1e12, "peak": peak_evals / 1e12,
-                    "unit": "T(d log2 d evals)/s", "frac": achieved / peak_evals, "traffic": None,
-                    "peak_source": "152 SMs x 16 MUFU lg2/clk x 2070 MHz (recipe unit counts and max clock)"}
-    else:
-        try:
-            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-            hbm = float(peaks["hbm_gbs"])
-            src = "measured"
-        except (OSError, KeyError, ValueError):
-            hbm, src = 6800.0, "fallback"
-        bytes_alg = 4 * (n + 1) + 4 * g.nnz + 8 * n
-        achieved = bytes_alg / (per[dom] / 1e3) / 1e9
-        roofline = {"kernel": dom[:-3], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": None, "peak_source": src}
+    dom = max(PASSES, key=lambda k: per[k])
+    alg = algorithmic_bytes(g, st)
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm, src = float(peaks["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+    except (OSError, KeyError, ValueError):
+        hbm, src = 6800.0, "fallback"
+    achieved = alg[dom] / (per[dom] / 1e3) / 1e9
+    roofline = {"kernel": PASS_KERNEL[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": committed_traffic(PASS_KERNEL[dom], args.workload),
+                "algorithmic_bytes": alg[dom], "launch_ms": per[dom], "peak_source": src,
+                "note": "bytes = each input read once and each output written once (per-pass formulas "
+                        "in DESIGN.md); " + PASS_NOTE[dom]}
+    path_bytes = 4 * (n + 1) + 4 * g.nnz + 8 * n
+    roofline_path = {"bound": "hbm", "algorithmic_bytes": path_bytes,
+                     "achieved": path_bytes / (ms_step / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": path_bytes / (ms_step / 1e3) / 1e9 / hbm}
 
     line = {
         "metric": "clusters/s", "value": value, "unit": "clusters/s", "n_gpus": world, "steps": args.steps,
@@ -296,7 +347,9 @@ def run_ours(args):
         "ef_wall_ms_per_graph": ms_step,
         "passes_ms": per,
         "roofline": roofline,
-        "e2e": {"value": e2e_value, "unit": "clusters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline_path": roofline_path,
+        "passes_gbs": {k: alg[k] / (per[k] / 1e3) / 1e9 if per[k] > 0 else None for k in PASSES},
+        "e2e": e2e,
         "gpu_launches": int(passes["kernels"]),
         "clocks": clocks,
     }

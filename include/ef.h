@@ -93,13 +93,16 @@ typedef struct {
     uint8_t *flag;        /* 1: degenerate (S_v = 0), EF = 0 */
 } ef_outputs;
 
-/* Per-pass timings in milliseconds, summed over profiled calls. */
+/* Per-pass timings in milliseconds, summed over profiled calls (CUDA events
+ * on the context stream between the passes). */
 typedef struct {
     int64_t calls;
-    double prep_ms;        /* validation, degrees, neighbour sums, f table, orientation */
+    double prep_ms;        /* validation, degrees, neighbour sums, f table */
+    double orient_ms;      /* degree orientation (scan + oriented CSR) and omega */
     double wedge_small_ms; /* middle nodes of degree <= 32 */
     double wedge_big_ms;   /* middle nodes of degree > 32 */
-    double triangle_ms;    /* triangle listing and corrections */
+    double tri_hash_ms;    /* hash tables of the long out-lists */
+    double tri_pairs_ms;   /* triangle pair tests and corrections (one kernel) */
     double finalize_ms;    /* per-node sums, S, N, EF */
     double total_ms;
     int64_t kernels;       /* kernels launched by profiled calls */
@@ -146,7 +149,7 @@ int ef_compute_ex(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
  *   stream has finished this call's work.  Input is validated.
  * Scratch lives in a fixed 32 MiB device array inside the library, held by
  * every GPU that loads it until the process exits.  Graphs whose scratch
- * would exceed it (about 164 n + 32 m + 48 min(n, m) bytes) are rejected with
+ * would exceed it (about 164 n + 36 m + 48 min(n, m) bytes) are rejected with
  * EF_ERR_ARG and a message naming the limit; nothing runs on the GPU then.
  * The first call on a device looks up the array's address (make it before
  * any stream capture).  All calls share the array: calls that overlap on the

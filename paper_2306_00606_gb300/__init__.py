@@ -50,8 +50,9 @@ class ef_outputs(ctypes.Structure):
 
 
 class ef_stats(ctypes.Structure):
-    _fields_ = [("calls", ctypes.c_int64), ("prep_ms", ctypes.c_double), ("wedge_small_ms", ctypes.c_double),
-                ("wedge_big_ms", ctypes.c_double), ("triangle_ms", ctypes.c_double),
+    _fields_ = [("calls", ctypes.c_int64), ("prep_ms", ctypes.c_double), ("orient_ms", ctypes.c_double),
+                ("wedge_small_ms", ctypes.c_double), ("wedge_big_ms", ctypes.c_double),
+                ("tri_hash_ms", ctypes.c_double), ("tri_pairs_ms", ctypes.c_double),
                 ("finalize_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("kernels", ctypes.c_int64)]
 
     def as_dict(self) -> dict:

@@ -48,8 +48,8 @@ thread_local char g_err[512];
 
 // Kernels one ef_compute_ex call launches (default wedge mode): prep A 3,
 // f table 1, orientation (a scan of 3 + 2), small wedges 4, class wedges 2,
-// triangles 1, finalize 1.
-constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 5 + 4 + 2 + 1 + 1;
+// triangles 2 (hash tables, pair tests), finalize 1.
+constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 5 + 4 + 2 + 2 + 1;
 
 void set_err(ef_ctx *c, const char *fmt, ...) {
     char *dst = c ? c->err : g_err;
@@ -159,16 +159,19 @@ int compute_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n,
     s.ftab = ctx->ftab;
     s.tq = reinterpret_cast<int64_t *>(ctx->ftab + fcap);
     LAUNCH(launch_ftab(s.ftab, s.tq, s.counters, fcap, st), "f table");
-    LAUNCH(launch_orient(rp, ci, n, m, s, st), "orientation");
     if (prof) CU(cudaEventRecord(ctx->ev[1], st));
-    LAUNCH(launch_wedge_small(rp, ci, s, o.precision, n, st), "small wedge");
+    LAUNCH(launch_orient(rp, ci, n, m, s, st), "orientation");
     if (prof) CU(cudaEventRecord(ctx->ev[2], st));
-    LAUNCH(launch_wedge_big(rp, ci, s, o.precision, o.wedge_mode, n, m, ctx->num_sms, st), "big wedge");
+    LAUNCH(launch_wedge_small(rp, ci, s, o.precision, n, st), "small wedge");
     if (prof) CU(cudaEventRecord(ctx->ev[3], st));
-    LAUNCH(launch_triangles(s, n, m, ctx->num_sms, st), "triangle");
+    LAUNCH(launch_wedge_big(rp, ci, s, o.precision, o.wedge_mode, n, m, ctx->num_sms, st), "big wedge");
     if (prof) CU(cudaEventRecord(ctx->ev[4], st));
-    LAUNCH(launch_finalize(s, o.precision, n, out, ctx->num_sms, st), "finalize");
+    LAUNCH(launch_out_hash(s, n, m, ctx->num_sms, st), "out-list hash");
     if (prof) CU(cudaEventRecord(ctx->ev[5], st));
+    LAUNCH(launch_tri_pairs(s, n, m, ctx->num_sms, st), "triangle");
+    if (prof) CU(cudaEventRecord(ctx->ev[6], st));
+    LAUNCH(launch_finalize(s, o.precision, n, out, ctx->num_sms, st), "finalize");
+    if (prof) CU(cudaEventRecord(ctx->ev[7], st));
     if (!o.trust_input)
         CU(cudaMemcpyAsync(ctx->h_counters + CNT_ERR, s.counters + CNT_ERR, sizeof(int32_t), cudaMemcpyDeviceToHost,
                            st));
@@ -184,21 +187,24 @@ int check_args(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_opti
     return EF_OK;
 }
 
-// Event pairs: prep + f table + orientation ev0-ev1, small wedges ev1-ev2,
-// big wedges ev2-ev3, triangles ev3-ev4, finalize ev4-ev5, total ev0-ev5.
+// Events 0..7 bracket, in order: prep + f table, orientation, small wedges,
+// big wedges, hash tables, pair tests, finalize.
 void accumulate_stats(ef_ctx *ctx) {
-    static const int pairs[6][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {0, 5}};
-    float t[6];
-    for (int i = 0; i < 6; ++i)
-        if (cudaEventElapsedTime(&t[i], ctx->ev[pairs[i][0]], ctx->ev[pairs[i][1]]) != cudaSuccess) t[i] = 0.f;
-    ctx->stats.calls += 1;
-    ctx->stats.prep_ms += t[0];
-    ctx->stats.wedge_small_ms += t[1];
-    ctx->stats.wedge_big_ms += t[2];
-    ctx->stats.triangle_ms += t[3];
-    ctx->stats.finalize_ms += t[4];
-    ctx->stats.total_ms += t[5];
-    ctx->stats.kernels += KERNELS_PER_CALL;
+    float t[7], tot;
+    for (int i = 0; i < 7; ++i)
+        if (cudaEventElapsedTime(&t[i], ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) t[i] = 0.f;
+    if (cudaEventElapsedTime(&tot, ctx->ev[0], ctx->ev[7]) != cudaSuccess) tot = 0.f;
+    ef_stats &st = ctx->stats;
+    st.calls += 1;
+    st.prep_ms += t[0];
+    st.orient_ms += t[1];
+    st.wedge_small_ms += t[2];
+    st.wedge_big_ms += t[3];
+    st.tri_hash_ms += t[4];
+    st.tri_pairs_ms += t[5];
+    st.finalize_ms += t[6];
+    st.total_ms += tot;
+    st.kernels += KERNELS_PER_CALL;
 }
 
 std::mutex g_default_mu;
@@ -223,8 +229,10 @@ size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s) {
     s.outdeg = (int32_t *)take(4 * N);
     s.fp_row = (uint64_t *)take(8 * N);
     s.out_ptr = (int32_t *)take(4 * (N + 1));
-    s.out_col = (int32_t *)take(4 * (M + 1));
+    s.out_col = (int32_t *)take(4 * (M + 8));
     s.out_D = (int32_t *)take(4 * (M + 1));
+    s.out_rng = (int2 *)take(8 * (M + 1));
+    s.out_hash = (int32_t *)take(4 * (M + 8));
     s.out_src = (int32_t *)take(4 * (M + 1));
     s.Ccenter = take(8 * N);
     // accumulators that start at zero, contiguous up to the end of the counters

@@ -67,6 +67,7 @@ constexpr int HUB_SMEM_K = 4096;       // classes held in shared memory by the C
 constexpr int BIG_ROWS = 256;          // rows per work item of the direct big-node kernel
 constexpr int BIG_TILE = 4096;         // neighbour degrees staged per tile by the direct kernel
 constexpr int ROW_CTA = 512;           // threads of the per-hub-row kernels
+constexpr int SHORT_MAX = 5;           // out-lists longer than this get a hash table for the triangle pass
 
 // Triangle corrections are integers in units of 2^-F (the pass adds only
 // integers: exact and independent of the order of the atomics).  F is chosen
@@ -89,8 +90,10 @@ struct Scratch {
     uint64_t *fp_row;    // n      fingerprint of the lower-ranked neighbours, from the node's own row
     uint64_t *fp_push;   // n      the same, pushed by those neighbours (symmetry check)
     int32_t *out_ptr;    // n+1    oriented CSR offsets
-    int32_t *out_col;    // m+1    oriented neighbour ids (ascending id within a row)
+    int32_t *out_col;    // m+8    oriented neighbour ids (ascending id within a row)
     int32_t *out_D;      // m+1    their degrees
+    int2    *out_rng;    // m+1    their own out-list ranges [out_ptr[x], out_ptr[x+1])
+    int32_t *out_hash;   // m+8    hash tables of the out-lists longer than SHORT_MAX
     int32_t *out_src;    // m+1    owner of each oriented edge
     double  *Tacc;       // n      open-degree credits received as an end (FP64 reductions)
     void    *Ccenter;    // n      middle-node credit (AccT<F64>, 8 bytes reserved per node)
@@ -215,7 +218,8 @@ int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, i
                        cudaStream_t st);
 int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int wedge_mode,
                      int32_t n, int64_t m, int num_sms, cudaStream_t st);
-int launch_triangles(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st);
+int launch_out_hash(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st);
+int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st);
 int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs &out, int num_sms,
                     cudaStream_t st);
 }  // namespace ef

@@ -244,13 +244,15 @@ __global__ void __launch_bounds__(ROW_CTA) k_row_stats_hub(const int32_t *__rest
 
 // ------------------------------------------------------------- orientation
 // Appends the out-neighbours x of u (in (degree, id) order) to the oriented
-// CSR in ascending id order, with D_x and the owner u; and gathers
-// omega_u = sum over N(u) of sigma1(x), the last per-node sum the closed form
-// of S needs.
+// CSR in ascending id order, with D_x, x's own out-list range and the owner
+// u; and gathers omega_u = sum over N(u) of sigma1(x), the last per-node sum
+// the closed form of S needs.
 struct Orient {
     const int32_t *ci, *D;
     const int64_t *sig1;
+    const int32_t *out_ptr;
     int32_t *out_col, *out_D, *out_src;
+    int2 *out_rng;
     int32_t n;
     __device__ __forceinline__ bool probe(int u, int Du, int e, int &x, int &Dx, int64_t &om) const {
         x = ci[e];
@@ -263,6 +265,7 @@ struct Orient {
         out_col[k] = x;
         out_D[k] = Dx;
         out_src[k] = u;
+        out_rng[k] = make_int2(out_ptr[x], out_ptr[x + 1]);
     }
 };
 
@@ -461,7 +464,7 @@ int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
 // Oriented CSR and omega.
 int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
     if (launch_scan(s.outdeg, s.out_ptr, n, s.scan_tmp, st)) return -1;
-    const Orient o{ci, s.D, s.sig1, s.out_col, s.out_D, s.out_src, n};
+    const Orient o{ci, s.D, s.sig1, s.out_ptr, s.out_col, s.out_D, s.out_src, s.out_rng, n};
     k_orient<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, n, m, o, s.out_ptr, s.omega);
     k_orient_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters, s.omega);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -66,7 +66,7 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
         char msg[200];
         snprintf(msg, sizeof msg,
                  "ef_compute_static: graph needs %zu bytes of scratch, above the fixed %zu-byte maximum "
-                 "(about 164 n + 32 m + 48 min(n, m) bytes); use ef_compute_ex",
+                 "(about 164 n + 36 m + 48 min(n, m) bytes); use ef_compute_ex",
                  need, EF_STATIC_SCRATCH_BYTES);
         return fail(EF_ERR_ARG, msg);
     }
@@ -108,7 +108,8 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     if (launch_ftab(s.ftab, s.tq, s.counters, fcap, st) || launch_orient(rp, ci, n, m, s, st) ||
         launch_wedge_small(rp, ci, s, precision, n, st) ||
         launch_wedge_big(rp, ci, s, precision, 0, n, m, num_sms, st) ||
-        launch_triangles(s, n, m, num_sms, st) || launch_finalize(s, precision, n, out, num_sms, st) ||
+        launch_out_hash(s, n, m, num_sms, st) || launch_tri_pairs(s, n, m, num_sms, st) ||
+        launch_finalize(s, precision, n, out, num_sms, st) ||
         cudaMemcpyAsync(h_cnt, s.counters, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: launch failed");
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)

@@ -10,75 +10,203 @@
 // one triangle count.
 //
 // Pair tests: b and c are adjacent iff the higher-ranked of the two is in the
-// lower-ranked one's out-list (binary search; the oriented CSR is a few tens
-// of MB and stays in L2).  That is sum_a C(|N+(a)|, 2) independent tests --
-// 1.1e8 on the 4M-node power-law workload, against 1.15e9 dependent steps
+// lower-ranked one's out-list.  That is sum_a C(|N+(a)|, 2) independent tests
+// -- 1.1e8 on the 4M-node power-law workload, against 1.15e9 dependent steps
 // for merging the two out-lists of every edge.  A warp takes 32 consecutive
-// oriented edges and spreads all their pairs evenly over its lanes.
+// oriented edges, cuts each edge's candidates c into units of TRI_UNIT and
+// spreads the units evenly over its lanes.
+//
+// The pass is bound by L2 latency, so every membership test is one round of
+// two independent 16-byte loads, the same instructions for every lane: an
+// out-list of at most SHORT_MAX entries is read whole (it spans at most two
+// aligned quads); a longer one has a bucketed hash table (4 slots per
+// 16-byte bucket, load factor <= 0.5 + small rounding, built by k_out_hash)
+// and the key's bucket and the next one are loaded together, which settles
+// the test but for rare long probe runs.  The oriented CSR carries each
+// out-neighbour's own list range, so no test waits for an out_ptr load.
 //
 // The pass is integer-only: g comes from a table in fixed point (units of
 // 2^-F, F chosen per call from the maximum degree), so the sums are exact and
 // independent of the order of the atomics, and no FP64 instruction (one lane
 // per clock per SM sub-partition on this GPU) sits in a divergent branch.
 // Corrections and counts go to per-node accumulators (qacc, tcnt) by L2
-// reductions: c's at once, a's and b's merged per lane over consecutive hits
-// (a lane's pairs share a, and often b).
+// reductions: c's at once, b's once per unit, a's merged per lane over
+// consecutive units of the same owner.
 #include "ef_internal.cuh"
 
 namespace ef {
 
 constexpr int TRI_WARPS = 8;
+// Candidate pairs per lane step and resident blocks per SM the registers are
+// sized for: measured on the 4M-node power-law graph, (2, 4) 1.80 ms,
+// (2, 3) 1.98, (2, 5) 2.06, (4, 3) 2.28, (4, 4) 2.51 (register spills).
+constexpr int TRI_UNIT = 2;
+constexpr int TRI_BLOCKS = 4;
+
+// Table of the out-list [ls, le) of one node: slots [base, base + 4 nb) of
+// out_hash, base = 2 ls rounded up to a multiple of 4 and 4 nb = 2 (le - ls)
+// rounded down to one, so the tables of consecutive out-lists never overlap
+// and every bucket is 16-byte aligned.  Only lists longer than SHORT_MAX have
+// one, and only when it lies inside the array (always, for a symmetric CSR:
+// the out-lists then hold m/2 entries in all).
+__device__ __forceinline__ bool out_table(int ls, int le, int64_t hash_cap, int64_t &base, int &nb) {
+    const int p = le - ls;
+    base = ((int64_t)2 * ls + 3) & ~(int64_t)3;
+    nb = (2 * p) >> 2;
+    return p > SHORT_MAX && base + 4 * (int64_t)nb <= hash_cap;
+}
+
+__device__ __forceinline__ int bucket_of(int key, int nb) {
+    const uint32_t h = (uint32_t)key * 0x9E3779B1u;
+    return (int)(((uint64_t)h * (uint32_t)nb) >> 32);
+}
+
+// Thread per oriented entry: insert it into its owner's table (cleared to -1
+// beforehand) by linear probing over slots from the key's bucket.
+__global__ void k_out_hash(const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_col,
+                           const int32_t *__restrict__ out_src, int32_t n, int64_t hash_cap,
+                           int32_t *__restrict__ out_hash) {
+    const int64_t total = out_ptr[n];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int a = out_src[k];
+        int64_t hb;
+        int nb;
+        if (!out_table(out_ptr[a], out_ptr[a + 1], hash_cap, hb, nb)) continue;
+        const int key = out_col[k];
+        const int cap = 4 * nb;
+        int sl = 4 * bucket_of(key, nb);
+        for (int tries = 0; tries < cap; ++tries) {
+            const int prev = atomicCAS(out_hash + hb + sl, -1, key);
+            if (prev == -1 || prev == key) break;
+            sl = sl + 1 == cap ? 0 : sl + 1;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned match4(int4 v, int key) {
+    return (unsigned)(v.x == key) | (unsigned)(v.y == key) << 1 | (unsigned)(v.z == key) << 2 |
+           (unsigned)(v.w == key) << 3;
+}
+
+__device__ __forceinline__ bool has_empty(int4 v) { return (v.x | v.y | v.z | v.w) < 0; }
+
+// Bits of the quad of entries [e0, e0 + 4) that lie in [ls, le).
+__device__ __forceinline__ unsigned range_bits(int e0, int ls, int le) {
+    const int lo = max(ls - e0, 0), hi = min(le - e0, 4);
+    return hi > lo ? ((1u << hi) - 1u) & ~((1u << lo) - 1u) : 0u;
+}
+
+// One membership test "key in the out-list [ls, le)", split so that a lane
+// issues the loads of all its tests before it waits for any: the quads p0
+// and p0 + d1, and which of their entries count (info bits 0-3 and 4-7) and
+// the kind of list (bits 8-9: 0 short, 1 hashed, 2 long without a table).
+struct Probe {
+    const int4 *p0;
+    int d1;
+    unsigned info;
+};
+
+__device__ __forceinline__ Probe probe_of(const int32_t *out_col, const int32_t *out_hash, int64_t hash_cap, int ls,
+                                          int le, int key) {
+    Probe r;
+    int64_t hb;
+    int nb;
+    if (out_table(ls, le, hash_cap, hb, nb)) {
+        const int b0 = bucket_of(key, nb);
+        r.p0 = reinterpret_cast<const int4 *>(out_hash + hb) + b0;
+        r.d1 = b0 + 1 == nb ? -b0 : 1;
+        r.info = 0xffu | 1u << 8;
+    } else {
+        const int q0 = ls >> 2;
+        r.p0 = reinterpret_cast<const int4 *>(out_col) + q0;
+        r.d1 = 1;
+        r.info = range_bits(4 * q0, ls, le) | range_bits(4 * q0 + 4, ls, le) << 4 |
+                 (le - ls > SHORT_MAX ? 2u : 0u) << 8;
+    }
+    return r;
+}
+
+// Resolve a probe from its two loaded quads.  The rare ends -- a hashed probe
+// whose two buckets were full without the key (continue the run), a long
+// list without a table (malformed input only: binary search) -- reload what
+// they need.
+__device__ __forceinline__ bool probe_done(const Probe &r, int4 x, int4 y, const int32_t *out_col,
+                                           const int32_t *out_hash, int64_t hash_cap, int ls, int le, int key) {
+    if ((match4(x, key) & r.info) | (match4(y, key) & (r.info >> 4) & 0xfu)) return true;
+    const unsigned kind = (r.info >> 8) & 3u;
+    if (kind == 0 || (kind == 1 && (has_empty(x) || has_empty(y)))) return false;
+    if (kind == 1) {
+        int64_t hb;
+        int nb;
+        out_table(ls, le, hash_cap, hb, nb);
+        const int4 *t = reinterpret_cast<const int4 *>(out_hash + hb);
+        int b = (int)(r.p0 + r.d1 - t);
+        b = b + 1 == nb ? 0 : b + 1;
+        for (int tries = 2; tries < nb; ++tries) {
+            const int4 q = __ldg(t + b);
+            if (match4(q, key)) return true;
+            if (has_empty(q)) return false;
+            b = b + 1 == nb ? 0 : b + 1;
+        }
+        return false;
+    }
+    const int pos = ls + lower_bound_i32(out_col + ls, le - ls, key);
+    return pos < le && out_col[pos] == key;
+}
 
 __device__ __forceinline__ void credit_tri(int64_t *qacc, int64_t *tcnt, int v, int64_t q, int cnt) {
     atomicAdd((unsigned long long *)(qacc + v), (unsigned long long)q);
     atomicAdd((unsigned long long *)(tcnt + v), (unsigned long long)cnt);
 }
 
-__global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_pairs(
+__global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
     const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_D,
-    const int32_t *__restrict__ out_src, const int32_t *__restrict__ D, int32_t n, const int64_t *__restrict__ tq,
+    const int2 *__restrict__ out_rng, const int32_t *__restrict__ out_src, const int32_t *__restrict__ out_hash,
+    int64_t hash_cap, const int32_t *__restrict__ D, int32_t n, const int64_t *__restrict__ tq,
     int64_t *__restrict__ qacc, int64_t *__restrict__ tcnt) {
-    __shared__ int s_ex[TRI_WARPS][32];   // exclusive prefix of pair counts
-    __shared__ int s_k[TRI_WARPS][32], s_b[TRI_WARPS][32], s_Db[TRI_WARPS][32], s_bs[TRI_WARPS][32];
-    __shared__ int s_be[TRI_WARPS][32], s_Dab[TRI_WARPS][32], s_a[TRI_WARPS][32];
+    __shared__ int s_ex[TRI_WARPS][32];   // exclusive prefix of unit counts
+    __shared__ int s_k[TRI_WARPS][32], s_kend[TRI_WARPS][32], s_b[TRI_WARPS][32], s_Db[TRI_WARPS][32];
+    __shared__ int s_bs[TRI_WARPS][32], s_be[TRI_WARPS][32], s_Dab[TRI_WARPS][32], s_a[TRI_WARPS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t total = out_ptr[n];
     const int64_t stride = (int64_t)gridDim.x * TRI_WARPS * 32;
     for (int64_t K0 = ((int64_t)blockIdx.x * TRI_WARPS + w) * 32; K0 < total; K0 += stride) {
         const int64_t k = K0 + lane;
-        int np = 0;
+        int nu = 0;
         if (k < total) {
             const int a = out_src[k];
             const int kend = out_ptr[a + 1];
-            np = kend - (int)k - 1;
+            const int np = kend - (int)k - 1;
             if (np > 0) {
                 const int b = out_col[k];
                 const int Db = out_D[k];
+                const int2 rb = out_rng[k];
                 s_k[w][lane] = (int)k;
+                s_kend[w][lane] = kend;
                 s_b[w][lane] = b;
                 s_Db[w][lane] = Db;
-                s_bs[w][lane] = out_ptr[b];
-                s_be[w][lane] = out_ptr[b + 1];
+                s_bs[w][lane] = rb.x;
+                s_be[w][lane] = rb.y;
                 s_Dab[w][lane] = D[a] + Db;
                 s_a[w][lane] = a;
-            } else {
-                np = 0;
+                nu = (np + TRI_UNIT - 1) / TRI_UNIT;
             }
         }
-        int inc = np;
+        int inc = nu;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(FULL, inc, o);
             if (lane >= o) inc += y;
         }
-        s_ex[w][lane] = inc - np;
-        const int P = __shfl_sync(FULL, inc, 31);
+        s_ex[w][lane] = inc - nu;
+        const int U = __shfl_sync(FULL, inc, 31);
         __syncwarp();
-        int cur_i = -1, cur_a = -1, hit_b = 0, hit_a = 0;
-        int64_t acc_b = 0, acc_a = 0;
-        int i = -1, ki = 0, exi = 0, b = 0, Db = 0, bs = 0, be = 0, Dab = 0, ai = 0;
-        for (int t = lane; t < P; t += 32) {
-            // the warp edge owning pair t: the last i with s_ex[i] <= t (s_ex is
+        int cur_a = -1, hit_a = 0;
+        int64_t acc_a = 0;
+        int i = -1, ki = 0, kend = 0, exi = 0, b = 0, Db = 0, bs = 0, be = 0, Dab = 0, ai = 0;
+        for (int t = lane; t < U; t += 32) {
+            // the warp edge owning unit t: the last i with s_ex[i] <= t (s_ex is
             // non-decreasing; i + step <= 31 at every step)
             int ni = 0;
 #pragma unroll
@@ -87,6 +215,7 @@ __global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_pairs(
             if (ni != i) {
                 i = ni;
                 ki = s_k[w][i];
+                kend = s_kend[w][i];
                 exi = s_ex[w][i];
                 b = s_b[w][i];
                 Db = s_Db[w][i];
@@ -95,46 +224,81 @@ __global__ void __launch_bounds__(TRI_WARPS * 32) k_tri_pairs(
                 Dab = s_Dab[w][i];
                 ai = s_a[w][i];
             }
-            const int j = ki + 1 + (t - exi);
-            const int c = out_col[j];
-            const int Dc = out_D[j];
-            const bool b_low = rank_less(Db, b, Dc, c);
-            const int ls = b_low ? bs : out_ptr[c];
-            const int le = b_low ? be : out_ptr[c + 1];
-            const int key = b_low ? c : b;
-            const int pos = ls + lower_bound_i32(out_col + ls, le - ls, key);
-            if (pos < le && out_col[pos] == key) {
-                const int64_t q = tq[Dab + Dc];
-                credit_tri(qacc, tcnt, c, q, 1);
-                if (i != cur_i) {
-                    if (hit_b) credit_tri(qacc, tcnt, s_b[w][cur_i], acc_b, hit_b);
-                    cur_i = i;
-                    acc_b = 0;
-                    hit_b = 0;
+            const int j0 = ki + 1 + TRI_UNIT * (t - exi);
+            const int jn = min(TRI_UNIT, kend - j0);
+            // issue every test's two quad loads first (bit 10 of info: b is the lower-ranked end)
+            Probe pr[TRI_UNIT];
+            int4 x[TRI_UNIT], y[TRI_UNIT];
+            int c[TRI_UNIT], Dc[TRI_UNIT];
+#pragma unroll
+            for (int q = 0; q < TRI_UNIT; ++q) {
+                if (q < jn) {
+                    c[q] = out_col[j0 + q];
+                    Dc[q] = out_D[j0 + q];
+                    const int2 r = out_rng[j0 + q];
+                    const bool b_low = rank_less(Db, b, Dc[q], c[q]);
+                    pr[q] = probe_of(out_col, out_hash, hash_cap, b_low ? bs : r.x, b_low ? be : r.y,
+                                     b_low ? c[q] : b);
+                    pr[q].info |= (unsigned)b_low << 10;
+                    x[q] = __ldg(pr[q].p0);
+                    y[q] = __ldg(pr[q].p0 + pr[q].d1);
                 }
-                acc_b += q;
-                ++hit_b;
+            }
+            int hits = 0;
+            int64_t gsum = 0;
+#pragma unroll
+            for (int q = 0; q < TRI_UNIT; ++q) {
+                if (q < jn) {
+                    const bool b_low = (pr[q].info >> 10) & 1u;
+                    int ls = bs, le = be;
+                    if (!b_low && (pr[q].info >> 8) & 3u) {   // rare ends only: c's own range
+                        const int2 r = out_rng[j0 + q];
+                        ls = r.x;
+                        le = r.y;
+                    }
+                    if (probe_done(pr[q], x[q], y[q], out_col, out_hash, hash_cap, ls, le, b_low ? c[q] : b)) {
+                        const int64_t g = __ldg(tq + Dab + Dc[q]);
+                        credit_tri(qacc, tcnt, c[q], g, 1);
+                        gsum += g;
+                        ++hits;
+                    }
+                }
+            }
+            if (hits) {
+                credit_tri(qacc, tcnt, b, gsum, hits);
                 if (ai != cur_a) {
                     if (hit_a) credit_tri(qacc, tcnt, cur_a, acc_a, hit_a);
                     cur_a = ai;
                     acc_a = 0;
                     hit_a = 0;
                 }
-                acc_a += q;
-                ++hit_a;
+                acc_a += gsum;
+                hit_a += hits;
             }
         }
-        if (hit_b) credit_tri(qacc, tcnt, s_b[w][cur_i], acc_b, hit_b);
         if (hit_a) credit_tri(qacc, tcnt, cur_a, acc_a, hit_a);
         __syncwarp();
     }
 }
 
-int launch_triangles(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st) {
-    int64_t g = (m / 2 + TRI_WARPS * 32 - 1) / (TRI_WARPS * 32);
-    unsigned grid = (unsigned)(g < 1 ? 1 : (g > (int64_t)num_sms * 16 ? (int64_t)num_sms * 16 : g));
-    k_tri_pairs<<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_src, s.D, n, s.tq, s.qacc,
-                                                 s.tcnt);
+static inline int64_t hash_slots(int64_t m) { return m + 8; }   // slots of out_hash
+
+static inline unsigned grid_of(int64_t work, int per_block, int64_t cap) {
+    int64_t g = (work + per_block - 1) / per_block;
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+int launch_out_hash(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st) {
+    if (cudaMemsetAsync(s.out_hash, 0xff, (size_t)hash_slots(m) * sizeof(int32_t), st) != cudaSuccess) return -1;
+    k_out_hash<<<grid_of(m / 2, 256, (int64_t)num_sms * 32), 256, 0, st>>>(s.out_ptr, s.out_col, s.out_src, n,
+                                                                          hash_slots(m), s.out_hash);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st) {
+    k_tri_pairs<<<grid_of(m / 2, TRI_WARPS * 32, (int64_t)num_sms * 16), TRI_WARPS * 32, 0, st>>>(
+        s.out_ptr, s.out_col, s.out_D, s.out_rng, s.out_src, s.out_hash, hash_slots(m), s.D, n, s.tq, s.qacc,
+        s.tcnt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -297,4 +297,4 @@ def test_profile_stats(ctx):
     ctx.stats(reset=True)
     run(ctx, g, "fp32c", profile=True)
     st = ctx.stats(reset=True)
-    assert st["calls"] == 1 and st["total_ms"] > 0 and st["wedge_big_ms"] > 0
+    assert st["calls"] == 1 and st["total_ms"] > 0 and st["wedge_big_ms"] > 0 and st["tri_pairs_ms"] > 0
