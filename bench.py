@@ -36,7 +36,10 @@ WORKLOADS = {
     "plcm4m": (3, "power-law configuration model n=4000000 gamma=2.3 degrees in [3,20000] seed=20230609"),
     "ba1m": (2, "Barabasi-Albert n=1000000 m=5 seed=20230608"),
     "er2000": (1, "Erdos-Renyi G(n=2000, p=0.004) seed=20230607"),
+    "ws4096": (4, "batch of 4096 Watts-Strogatz graphs, n ~ U[200,20000], k ~ U{4,...,12} even, p=0.1, "
+                  "seed=20230610, one ef_compute_batched call (replayed CUDA graph)"),
 }
+BATCHED = {"ws4096"}
 PASSES = ("prep_ms", "orient_ms", "wedge_small_ms", "wedge_big_ms", "tri_hash_ms", "tri_pairs_ms", "finalize_ms")
 PASS_KERNEL = {"prep_ms": "k_degrees+k_row_stats+k_row_stats_hub+k_ftab",
                "orient_ms": "scan+k_orient+k_orient_hub", "wedge_small_ms": "k_wedge_small<4,8,16,32>",
@@ -102,6 +105,7 @@ def parse():
     p.add_argument("--scale", type=float, default=1.0,
                    help="shrink the workload's node count (small cases for profiling; not a bench line)")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    p.add_argument("--autotune", action="store_true", help="run ef_autotune on the workload before timing")
     return p.parse_args()
 
 
@@ -257,9 +261,22 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     ctx = ef.Context(local, stream)
     out = torch.empty(n, dtype=torch.float64, device=dev)
+    batched = args.workload in BATCHED
+    if args.autotune:
+        tuned = ef.ef_autotune(ctx.handle, rp, ci, precision=args.precision, reps=2)
 
-    def step(profile=False):
-        ef.ef_compute_ex(ctx.handle, rp, ci, precision=args.precision, ef=out, profile=profile)
+    def step(profile=False, io=None):
+        kw = dict(precision=args.precision, profile=profile)
+        if io is None:
+            kw.update(ef=out)
+            a, b = rp, ci
+        else:
+            kw.update(ef=io[2], host_io=True)
+            a, b = io[0], io[1]
+        if batched:
+            ef.ef_compute_batched(ctx.handle, a, b, g.graph_off, graph=not profile, **kw)
+        else:
+            ef.ef_compute_ex(ctx.handle, a, b, **kw)
 
     def barrier():
         if world > 1:
@@ -271,22 +288,34 @@ def run_ours(args):
     ctx.stats(reset=True)
 
     # ---- device-resident timing (inputs in HBM; > L2, no flush) ----
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    # Single graphs: the timed steps also carry the library's per-pass events.
+    # Batches: the timed steps replay the captured CUDA graph (no events
+    # inside); a second region of as many eager, profiled steps gives the
+    # per-pass breakdown.
+    def timed(profile):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize(dev)
         ev0.record(stream)
         for _ in range(args.steps):
-            step(profile=True)
+            step(profile=profile)
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms_ = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms_], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_ = float(t.item())
+        return ms_
+
+    with ClockSampler(local) as clk:
+        ms = timed(profile=not batched)
+    replays = ctx.stats()["graph_replays"]
+    if batched:
+        ctx.stats(reset=True)
+        timed(profile=True)
     passes = ctx.stats(reset=True)
     ms_step = ms / args.steps
     value = st["W"] * args.steps * world / (ms / 1e3)
@@ -299,13 +328,14 @@ def run_ours(args):
         h_rp = torch.from_numpy(g.row_ptr).pin_memory()
         h_ci = torch.from_numpy(g.col_idx).pin_memory()
         h_out = torch.empty(n, dtype=torch.float64).pin_memory()
+        io = (h_rp, h_ci, h_out)
         for _ in range(2):
-            ef.ef_compute_ex(ctx.handle, h_rp, h_ci, precision=args.precision, ef=h_out, host_io=True)
+            step(io=io)
         barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            ef.ef_compute_ex(ctx.handle, h_rp, h_ci, precision=args.precision, ef=h_out, host_io=True)
+            step(io=io)
         torch.cuda.synchronize(dev)
         e2e_s = time.perf_counter() - t0
         if world > 1:
@@ -341,10 +371,13 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32c" else "f64", "data": "synthetic",
         "config": {"workload": desc, "nodes": n, "nnz": g.nnz, "edges": g.nnz // 2, "clusters": st["W"],
+                   "graphs": len(g.graph_off) - 1 if batched else 1,
+                   "tuning": ef.ef_get_tuning(ctx.handle), "autotuned": bool(args.autotune),
                    "max_degree": st["maxdeg"], "precision": args.precision,
                    "l2": f"inputs larger than L2 (CSR {(4 * (n + 1) + 4 * g.nnz) / 2**20:.0f} MiB), no flush",
                    "parallelism": f"replicas x{world}"},
-        "ef_wall_ms_per_graph": ms_step,
+        "ef_wall_ms_per_graph": ms_step / (len(g.graph_off) - 1 if batched else 1),
+        "graph_replays_in_timed_region": replays,
         "passes_ms": per,
         "roofline": roofline,
         "roofline_path": roofline_path,

@@ -80,7 +80,11 @@ typedef struct {
                               wedge kernel for every middle node of degree
                               > 32 (reference kernel for benchmarking); other
                               values: EF_ERR_UNSUPPORTED */
-    int32_t reserved[2];
+    int32_t graph;         /* 1: run the passes that need no host decision as
+                              one CUDA graph, captured on the first call and
+                              replayed while pointers, sizes, options and
+                              tuning stay the same (ignored with profile) */
+    int32_t reserved;
 } ef_options;
 
 /* Optional per-node outputs (any may be NULL); length n each. */
@@ -106,7 +110,20 @@ typedef struct {
     double finalize_ms;    /* per-node sums, S, N, EF */
     double total_ms;
     int64_t kernels;       /* kernels launched by profiled calls */
+    int64_t graph_replays; /* calls served by replaying a cached CUDA graph */
 } ef_stats;
+
+/* Launch parameters (every choice gives the same results; see ef_autotune). */
+typedef struct {
+    int32_t row_thread_max; /* row passes: rows of degree <= this are walked by
+                               one thread, longer ones by a warp (1..32; 32) */
+    int32_t hub_min;        /* rows and middle nodes of degree >= this take a
+                               whole CTA (33..513; 513) */
+    int32_t tri_variant;    /* pair-test kernel: 0 two candidates per lane
+                               step, 1 four (0) */
+    int32_t grid_per_sm;    /* blocks per SM of the grid-stride row passes
+                               (1..256; 64) */
+} ef_tuning;
 
 /* Create a context on CUDA device `device` issuing work on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  0 on success. */
@@ -138,6 +155,42 @@ int ef_compute_ex(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
                   const ef_options *opt, ef_outputs *out);
 
 /*
+ * Batched EF (many graphs in one call).  The batch is one CSR over the
+ * disjoint union of its graphs with global node ids: graph k owns nodes
+ * [graph_off[k], graph_off[k+1]) and every entry of those rows lies in the
+ * same range.  EF of a node depends only on nodes within two hops of it
+ * (Algorithm 1 credits a node only for clusters that contain it), so EF over
+ * the union equals EF of each graph computed alone.
+ *   g: union CSR (device unless host_io), m: its nnz (< 2^31);
+ *   graph_off: int64[num_graphs+1], HOST memory, graph_off[0] = 0,
+ *   non-decreasing, n = graph_off[num_graphs] < 2^31;
+ *   out: per-node outputs over the union (length n).
+ * Validation (unless trust_input) is ef_compute_ex's plus the check that no
+ * entry leaves its graph (EF_ERR_GRAPH "edge-between-graphs").  With
+ * opt->graph = 1 the passes run as one replayed CUDA graph (with
+ * trust_input, the whole call is one graph launch).
+ */
+int ef_compute_batched(ef_ctx *ctx, const ef_csr *g, int64_t m,
+                       const int64_t *graph_off, int32_t num_graphs,
+                       const ef_options *opt, ef_outputs *out);
+
+/* Read or set the context's launch parameters (t = NULL restores the
+ * defaults; out-of-range values give EF_ERR_ARG and change nothing). */
+int ef_get_tuning(const ef_ctx *ctx, ef_tuning *out);
+int ef_set_tuning(ef_ctx *ctx, const ef_tuning *t);
+
+/*
+ * Autotuner: validates the graph once (unless trust_input), then times
+ * candidate launch parameters on it (coordinate descent over the four
+ * ef_tuning fields, two sweeps; each candidate one warm-up and `reps` timed
+ * runs as a replayed CUDA graph, CUDA events on the context stream), keeps
+ * the fastest on the context and returns it in *best.  A batch is tuned by
+ * passing its union CSR.  Device pointers only.
+ */
+int ef_autotune(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
+                const ef_options *opt, int32_t reps, ef_tuning *best);
+
+/*
  * ef_compute_static: EF of every node with no memory allocation at all.
  * The paper has no counterpart; this is for callers that cannot allocate
  * device memory when they need EF (code inside a memory pool that owns the
@@ -149,7 +202,7 @@ int ef_compute_ex(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
  *   stream has finished this call's work.  Input is validated.
  * Scratch lives in a fixed 32 MiB device array inside the library, held by
  * every GPU that loads it until the process exits.  Graphs whose scratch
- * would exceed it (about 164 n + 36 m + 48 min(n, m) bytes) are rejected with
+ * would exceed it (about 180 n + 44 m + 48 min(n, m) bytes) are rejected with
  * EF_ERR_ARG and a message naming the limit; nothing runs on the GPU then.
  * The first call on a device looks up the array's address (make it before
  * any stream capture).  All calls share the array: calls that overlap on the

@@ -25,7 +25,8 @@ PRECISIONS = {"fp64": EF_PREC_FP64, "fp32c": EF_PREC_FP32C}
 
 # Every symbol include/ef.h declares (checked by the CPU test of the ABI).
 EXPORTED = ("ef_ctx_create", "ef_ctx_destroy", "ef_last_error", "ef_sync", "ef_get_stats",
-            "ef_compute", "ef_compute_ex", "ef_compute_static")
+            "ef_compute", "ef_compute_ex", "ef_compute_batched", "ef_get_tuning", "ef_set_tuning", "ef_autotune",
+            "ef_compute_static")
 
 
 class EfError(RuntimeError):
@@ -41,7 +42,7 @@ class ef_csr(ctypes.Structure):
 class ef_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("trust_input", ctypes.c_int32), ("host_io", ctypes.c_int32),
                 ("async_", ctypes.c_int32), ("profile", ctypes.c_int32), ("wedge_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ef_outputs(ctypes.Structure):
@@ -53,7 +54,16 @@ class ef_stats(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("prep_ms", ctypes.c_double), ("orient_ms", ctypes.c_double),
                 ("wedge_small_ms", ctypes.c_double), ("wedge_big_ms", ctypes.c_double),
                 ("tri_hash_ms", ctypes.c_double), ("tri_pairs_ms", ctypes.c_double),
-                ("finalize_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("kernels", ctypes.c_int64)]
+                ("finalize_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("kernels", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ef_tuning(ctypes.Structure):
+    _fields_ = [("row_thread_max", ctypes.c_int32), ("hub_min", ctypes.c_int32), ("tri_variant", ctypes.c_int32),
+                ("grid_per_sm", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -80,6 +90,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ef_compute.argtypes = [ctypes.POINTER(ef_csr), i32, i64, vp]
     lib.ef_compute_ex.argtypes = [vp, ctypes.POINTER(ef_csr), i32, i64, ctypes.POINTER(ef_options),
                                   ctypes.POINTER(ef_outputs)]
+    lib.ef_compute_batched.argtypes = [vp, ctypes.POINTER(ef_csr), i64, ctypes.POINTER(ctypes.c_int64), i32,
+                                       ctypes.POINTER(ef_options), ctypes.POINTER(ef_outputs)]
+    lib.ef_get_tuning.argtypes = [vp, ctypes.POINTER(ef_tuning)]
+    lib.ef_set_tuning.argtypes = [vp, ctypes.POINTER(ef_tuning)]
+    lib.ef_autotune.argtypes = [vp, ctypes.POINTER(ef_csr), i32, i64, ctypes.POINTER(ef_options), i32,
+                                ctypes.POINTER(ef_tuning)]
     lib.ef_compute_static.argtypes = [ctypes.POINTER(ef_csr), i32, i64, i32, vp, vp]
     for name in EXPORTED:
         if name != "ef_last_error":
@@ -136,17 +152,63 @@ def ef_compute(row_ptr, col_idx, out_ef) -> None:
     _check(load_library().ef_compute(ctypes.byref(g), n, int(col_idx.shape[0]), _ptr(out_ef)))
 
 
+def _options(precision, trust_input, host_io, async_, profile, wedge_mode, graph) -> ef_options:
+    return ef_options(PRECISIONS[precision], int(trust_input), int(host_io), int(async_), int(profile),
+                      int(wedge_mode), int(graph))
+
+
 def ef_compute_ex(ctx: int, row_ptr, col_idx, *, precision: str = "fp64", ef=None, n_clusters=None, s=None,
                   t=None, triangles=None, flag=None, trust_input: bool = False, host_io: bool = False,
-                  async_: bool = False, profile: bool = False, wedge_mode: int = 0) -> None:
+                  async_: bool = False, profile: bool = False, wedge_mode: int = 0, graph: bool = False) -> None:
     """Full-control EF: writes whichever output buffers are given (device, or host with host_io)."""
     n = int(row_ptr.shape[0]) - 1
     g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
-    o = ef_options(PRECISIONS[precision], int(trust_input), int(host_io), int(async_), int(profile),
-                   int(wedge_mode))
+    o = _options(precision, trust_input, host_io, async_, profile, wedge_mode, graph)
     out = ef_outputs(_ptr(ef), _ptr(n_clusters), _ptr(s), _ptr(t), _ptr(triangles), _ptr(flag))
     _check(load_library().ef_compute_ex(ctx, ctypes.byref(g), n, int(col_idx.shape[0]), ctypes.byref(o),
                                         ctypes.byref(out)), ctx)
+
+
+def ef_compute_batched(ctx: int, row_ptr, col_idx, graph_off, *, precision: str = "fp64", ef=None,
+                       n_clusters=None, s=None, t=None, triangles=None, flag=None, trust_input: bool = False,
+                       host_io: bool = False, async_: bool = False, profile: bool = False, wedge_mode: int = 0,
+                       graph: bool = True) -> None:
+    """EF of every node of a batch of graphs given as one disjoint-union CSR; graph_off is a host int64
+    array of num_graphs + 1 node offsets."""
+    off = np.ascontiguousarray(np.asarray(graph_off, dtype=np.int64))
+    g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
+    o = _options(precision, trust_input, host_io, async_, profile, wedge_mode, graph)
+    out = ef_outputs(_ptr(ef), _ptr(n_clusters), _ptr(s), _ptr(t), _ptr(triangles), _ptr(flag))
+    _check(load_library().ef_compute_batched(ctx, ctypes.byref(g), int(col_idx.shape[0]),
+                                             off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1,
+                                             ctypes.byref(o), ctypes.byref(out)), ctx)
+
+
+def ef_get_tuning(ctx: int) -> dict:
+    t = ef_tuning()
+    _check(load_library().ef_get_tuning(ctx, ctypes.byref(t)), ctx)
+    return t.as_dict()
+
+
+def ef_set_tuning(ctx: int, tuning: dict | None = None) -> None:
+    """Set the context's launch parameters (None restores the defaults)."""
+    if tuning is None:
+        _check(load_library().ef_set_tuning(ctx, None), ctx)
+        return
+    t = ef_tuning(**tuning)
+    _check(load_library().ef_set_tuning(ctx, ctypes.byref(t)), ctx)
+
+
+def ef_autotune(ctx: int, row_ptr, col_idx, *, precision: str = "fp32c", reps: int = 3,
+                trust_input: bool = False, wedge_mode: int = 0) -> dict:
+    """Time candidate launch parameters on this graph; keeps the fastest on the context and returns it."""
+    n = int(row_ptr.shape[0]) - 1
+    g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
+    o = _options(precision, trust_input, False, False, False, wedge_mode, False)
+    t = ef_tuning()
+    _check(load_library().ef_autotune(ctx, ctypes.byref(g), n, int(col_idx.shape[0]), ctypes.byref(o), int(reps),
+                                      ctypes.byref(t)), ctx)
+    return t.as_dict()
 
 
 def ef_compute_static(row_ptr, col_idx, out_ef, precision: str = "fp64", stream: int | None = None) -> None:

@@ -81,8 +81,9 @@ __global__ void __launch_bounds__(256) k_finalize(int32_t n, FinalArgs f) {
     if ((threadIdx.x & 31) == 0 && err) atomicOr(f.cnt + CNT_ERR, err);
 }
 
-int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs &out, int num_sms,
+int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs &out, const Tune &t,
                     cudaStream_t st) {
+    const int num_sms = t.num_sms;
     const FinalArgs f{s.D,    s.sig1,    s.sig2, s.omega, s.fp_row,   s.fp_push,
                       s.Tacc, s.Ccenter, s.qacc, s.tcnt,  s.counters, out};
     int64_t g = ((int64_t)n + 255) / 256;

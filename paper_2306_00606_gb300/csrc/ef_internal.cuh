@@ -42,6 +42,7 @@ enum : int {
     ERRB_SELFLOOP = 4,  // v in N(v)
     ERRB_UNSORTED = 8,  // a row not strictly ascending (includes duplicates)
     ERRB_ASYM = 16,     // x in N(u) but u not in N(x)
+    ERRB_CROSS = 32,    // batched input: an entry outside its row's graph
 };
 
 // Work bins (each a list of node ids of capacity n), filled from the degrees.
@@ -51,8 +52,8 @@ enum : int {
     BIN_S16,       // 9..16         2 per warp
     BIN_S32,       // 17..32        1 per warp
     BIN_BIG,       // D > 32        (direct wedge kernel)
-    BIN_MID,       // 32 < D <= MID_MAX   degree-class wedge kernel, one warp each
-    BIN_HUB0,      // D > MID_MAX, bucket floor(log2 D) - 9, capped at NUM_HUB_BUCKETS-1
+    BIN_MID,       // 32 < D < hub_min (<= MID_MAX)   degree-class wedge kernel, one warp each
+    BIN_HUB0,      // D >= hub_min, bucket floor(log2 D) - 9 clamped to [0, NUM_HUB_BUCKETS-1]
     BIN_HUB_LAST = BIN_HUB0 + 6,
     NUM_BINS
 };
@@ -80,6 +81,21 @@ constexpr int TRI_FRAC_MAX = 52;
 template <bool F64>
 using AccT = typename std::conditional<F64, double, float>::type;
 
+// Launch parameters an autotuner may change (ef_tuning in ef.h); every
+// choice gives the same results.
+struct Tune {
+    int row_thread_max = SMALL_MAX;   // row passes: rows of degree <= this take one thread each
+    int hub_min = MID_MAX + 1;        // rows / middle nodes of degree >= this take a CTA (33..MID_MAX+1)
+    int tri_variant = 0;              // pair-test kernel: 0 two candidates per lane step, 1 four
+    int grid_per_sm = 64;             // blocks per SM of the grid-stride row passes
+    int num_sms = 0;
+    unsigned grid(int64_t work, int per_block) const {
+        int64_t g = (work + per_block - 1) / per_block;
+        const int64_t cap = (int64_t)num_sms * grid_per_sm;
+        return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+    }
+};
+
 // Scratch carved from one device allocation per call (sizes depend on n, m).
 struct Scratch {
     int32_t *D;          // n      degrees
@@ -90,6 +106,7 @@ struct Scratch {
     uint64_t *fp_row;    // n      fingerprint of the lower-ranked neighbours, from the node's own row
     uint64_t *fp_push;   // n      the same, pushed by those neighbours (symmetry check)
     int32_t *out_ptr;    // n+1    oriented CSR offsets
+    int4    *info;       // n      {D, sigma1, out_ptr, out_ptr next} per node, for the orientation
     int32_t *out_col;    // m+8    oriented neighbour ids (ascending id within a row)
     int32_t *out_D;      // m+1    their degrees
     int2    *out_rng;    // m+1    their own out-list ranges [out_ptr[x], out_ptr[x+1])
@@ -209,17 +226,22 @@ constexpr double LN2 = 0.69314718055994530942;
 
 // ------------------------------------------------------------ launchers
 namespace ef {
-int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st);
-int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st);
+int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
+                  cudaStream_t st);
+int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
+                  cudaStream_t st);
 int launch_big_items(const Scratch &s, int32_t n, cudaStream_t st);
+int launch_batch_check(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const int64_t *goff, int32_t G,
+                       const Scratch &s, const Tune &t, cudaStream_t st);
+int prepare_kernels();
 int launch_scan(const int32_t *in, int32_t *out, int32_t n, int32_t *tmp, cudaStream_t st);
 int launch_ftab(double *ftab, int64_t *tq, int32_t *cnt, int64_t cap, cudaStream_t st);
 int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
-                       cudaStream_t st);
+                       const Tune &t, cudaStream_t st);
 int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int wedge_mode,
-                     int32_t n, int64_t m, int num_sms, cudaStream_t st);
-int launch_out_hash(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st);
-int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st);
-int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs &out, int num_sms,
+                     int32_t n, int64_t m, const Tune &t, cudaStream_t st);
+int launch_out_hash(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st);
+int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st);
+int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs &out, const Tune &t,
                     cudaStream_t st);
 }  // namespace ef

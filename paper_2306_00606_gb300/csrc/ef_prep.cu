@@ -7,9 +7,10 @@
 // array D is the only per-node quantity the wedge pass reads besides the CSR.
 //
 // Row passes use three granularities so that no row's latency chain becomes
-// the tail of the pass: a thread per row of degree <= 32 (serial loop), a
-// warp per row of degree 33..MID_MAX, and a CTA per hub row (degree >
-// MID_MAX, listed by the degree kernel, largest first).
+// the tail of the pass: a thread per row of degree <= row_thread_max (32 by
+// default; loop unrolled by four), a warp per row up to hub_min - 1 (512 by
+// default), and a CTA per hub row (listed by the degree kernel, largest
+// first).  Both limits are launch parameters (Tune).
 #include "ef_internal.cuh"
 
 namespace ef {
@@ -68,8 +69,8 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int *total = nullptr)
 // depend on D only): small sub-warp bins, or "big" plus the mid list or a
 // hub bucket.  Block-level counting in shared memory, one global atomic per
 // bin per block.
-__global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, int32_t *__restrict__ D,
-                          int32_t *__restrict__ bins, int32_t *__restrict__ cnt) {
+__global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, int hub_min,
+                          int32_t *__restrict__ D, int32_t *__restrict__ bins, int32_t *__restrict__ cnt) {
     __shared__ int s_cnt[NUM_BINS], s_base[NUM_BINS];
     __shared__ int s_mx[32], s_err[32];
     if (threadIdx.x < NUM_BINS) s_cnt[threadIdx.x] = 0;
@@ -87,11 +88,11 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
             b0 = d <= 4 ? BIN_S4 : d <= 8 ? BIN_S8 : d <= 16 ? BIN_S16 : BIN_S32;
         } else if (d > SMALL_MAX) {
             b0 = BIN_BIG;
-            if (d <= MID_MAX) {
+            if (d < hub_min) {
                 b1 = BIN_MID;
             } else {
-                const int lg = 31 - __clz(d);   // floor(log2 d) >= 9
-                b1 = BIN_HUB0 + min(lg - 9, NUM_HUB_BUCKETS - 1);
+                const int lg = 31 - __clz(d);   // floor(log2 d)
+                b1 = BIN_HUB0 + max(0, min(lg - 9, NUM_HUB_BUCKETS - 1));
             }
         }
     }
@@ -160,6 +161,42 @@ struct RowStats {
             fpr += node_print(x);
         }
     }
+    // A whole short row by one thread, four entries at a time: their loads
+    // are issued together, so four dependent chains are in flight.
+    __device__ __forceinline__ void row(const int32_t *__restrict__ ci, const int32_t *__restrict__ D, int32_t n,
+                                        int v, int Dv, int a, int b, uint64_t pv, uint64_t *__restrict__ fp_push) {
+        int prev = 0;
+        for (int e0 = a; e0 < b; e0 += 4) {
+            int x[4], Dx[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = e0 + q < b ? ci[e0 + q] : 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) Dx[q] = e0 + q < b && x[q] >= 0 && x[q] < n ? D[x[q]] : 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (e0 + q < b) {
+                    const int xq = x[q];
+                    const bool later = e0 + q > a;
+                    const int before = prev;
+                    prev = xq;
+                    if (xq < 0 || xq >= n) {
+                        err |= ERRB_RANGE;
+                        continue;
+                    }
+                    if (xq == v) err |= ERRB_SELFLOOP;
+                    if (later && before >= xq) err |= ERRB_UNSORTED;
+                    s1 += Dx[q];
+                    s2 += (int64_t)Dx[q] * Dx[q];
+                    if (rank_less(Dv, v, Dx[q], xq)) {
+                        ++od;
+                        atomicAdd((unsigned long long *)(fp_push + xq), (unsigned long long)pv);
+                    } else {
+                        fpr += node_print(xq);
+                    }
+                }
+            }
+        }
+    }
 };
 
 struct RowOut {
@@ -169,7 +206,8 @@ struct RowOut {
 };
 
 __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
-                            const int32_t *__restrict__ D, RowOut ro, int32_t *__restrict__ cnt) {
+                            int tmax, int hub_min, const int32_t *__restrict__ D, RowOut ro,
+                            int32_t *__restrict__ cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
@@ -179,18 +217,17 @@ __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__res
         const int a = in ? rp[v] : 0, b = in ? rp[v + 1] : 0;
         const bool ok = in && a >= 0 && a <= b && (int64_t)b <= m;
         const int Dv = ok ? b - a : 0;
-        if (in && Dv <= SMALL_MAX) {
+        if (in && Dv <= tmax) {
             RowStats r;
             const uint64_t pv = node_print(v);
-            if (ok)
-                for (int e = a; e < b; ++e) r.entry(ci, D, n, v, Dv, a, e, pv, ro.fp_push);
+            if (ok) r.row(ci, D, n, v, Dv, a, b, pv, ro.fp_push);
             ro.sig1[v] = r.s1;
             ro.sig2[v] = r.s2;
             ro.outdeg[v] = r.od;
             ro.fp_row[v] = r.fpr;
             if (r.err) atomicOr(cnt + CNT_ERR, r.err);
         }
-        unsigned mid = __ballot_sync(FULL, Dv > SMALL_MAX && Dv <= MID_MAX);
+        unsigned mid = __ballot_sync(FULL, Dv > tmax && Dv < hub_min);
         while (mid) {
             const int j = __ffs(mid) - 1;
             mid &= mid - 1;
@@ -248,28 +285,56 @@ __global__ void __launch_bounds__(ROW_CTA) k_row_stats_hub(const int32_t *__rest
 // u; and gathers omega_u = sum over N(u) of sigma1(x), the last per-node sum
 // the closed form of S needs.
 struct Orient {
-    const int32_t *ci, *D;
-    const int64_t *sig1;
-    const int32_t *out_ptr;
+    const int32_t *ci;
+    const int4 *info;   // per node {D, sigma1, out_ptr, out_ptr next}
     int32_t *out_col, *out_D, *out_src;
     int2 *out_rng;
     int32_t n;
-    __device__ __forceinline__ bool probe(int u, int Du, int e, int &x, int &Dx, int64_t &om) const {
-        x = ci[e];
-        const bool xin = x >= 0 && x < n;
-        Dx = xin ? D[x] : 0;
-        om += xin ? sig1[x] : 0;
-        return xin && rank_less(Du, u, Dx, x);
+    __device__ __forceinline__ int4 node(int x) const {
+        return x >= 0 && x < n ? __ldg(info + x) : make_int4(0, 0, 0, 0);
     }
-    __device__ __forceinline__ void put(int k, int u, int x, int Dx) const {
+    __device__ __forceinline__ bool probe(int u, int Du, int e, int &x, int4 &nf, int64_t &om) const {
+        x = ci[e];
+        nf = node(x);
+        om += nf.y;
+        return x >= 0 && x < n && rank_less(Du, u, nf.x, x);
+    }
+    __device__ __forceinline__ void put(int k, int u, int x, int4 nf) const {
         out_col[k] = x;
-        out_D[k] = Dx;
+        out_D[k] = nf.x;
         out_src[k] = u;
-        out_rng[k] = make_int2(out_ptr[x], out_ptr[x + 1]);
+        out_rng[k] = make_int2(nf.z, nf.w);
+    }
+    // A whole short row by one thread, four entries at a time (loads issued
+    // together); returns omega_v.
+    __device__ __forceinline__ int64_t row(int v, int Dv, int a, int b, int k) const {
+        int64_t om = 0;
+        for (int e0 = a; e0 < b; e0 += 4) {
+            int x[4];
+            int4 nf[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) x[q] = e0 + q < b ? ci[e0 + q] : -1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nf[q] = node(x[q]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                om += nf[q].y;
+                if (x[q] >= 0 && x[q] < n && rank_less(Dv, v, nf[q].x, x[q])) put(k++, v, x[q], nf[q]);
+            }
+        }
+        return om;
     }
 };
 
-__global__ void k_orient(const int32_t *__restrict__ rp, int32_t n, int64_t m, Orient o,
+// info[v] = {D_v, sigma1(v), out_ptr[v], out_ptr[v+1]}: what the orientation
+// needs of a neighbour, in one 16-byte gather (sigma1 <= m < 2^31).
+__global__ void k_node_info(const int32_t *__restrict__ D, const int64_t *__restrict__ sig1,
+                            const int32_t *__restrict__ out_ptr, int32_t n, int4 *__restrict__ info) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        info[v] = make_int4(D[v], (int)sig1[v], out_ptr[v], out_ptr[v + 1]);
+}
+
+__global__ void k_orient(const int32_t *__restrict__ rp, int32_t n, int64_t m, int tmax, int hub_min, Orient o,
                          const int32_t *__restrict__ out_ptr, int64_t *__restrict__ omega) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -280,16 +345,8 @@ __global__ void k_orient(const int32_t *__restrict__ rp, int32_t n, int64_t m, O
         const int a = in ? rp[v] : 0, b = in ? rp[v + 1] : 0;
         const bool ok = in && a >= 0 && a <= b && (int64_t)b <= m;
         const int Dv = ok ? b - a : 0;
-        if (ok && Dv <= SMALL_MAX) {
-            int k = out_ptr[v];
-            int64_t om = 0;
-            for (int e = a; e < b; ++e) {
-                int x, Dx;
-                if (o.probe(v, Dv, e, x, Dx, om)) o.put(k++, v, x, Dx);
-            }
-            omega[v] = om;
-        }
-        unsigned mid = __ballot_sync(FULL, Dv > SMALL_MAX && Dv <= MID_MAX);
+        if (ok && Dv <= tmax) omega[v] = o.row(v, Dv, a, b, out_ptr[v]);
+        unsigned mid = __ballot_sync(FULL, Dv > tmax && Dv < hub_min);
         while (mid) {
             const int j = __ffs(mid) - 1;
             mid &= mid - 1;
@@ -299,10 +356,11 @@ __global__ void k_orient(const int32_t *__restrict__ rp, int32_t n, int64_t m, O
             int64_t om = 0;
             for (int e0 = ua; e0 < ub; e0 += 32) {
                 const int e = e0 + lane;
-                int x = 0, Dx = 0;
-                const bool isout = e < ub && o.probe(u, ub - ua, e, x, Dx, om);
+                int x = 0;
+                int4 nf = make_int4(0, 0, 0, 0);
+                const bool isout = e < ub && o.probe(u, ub - ua, e, x, nf, om);
                 const unsigned bal = __ballot_sync(FULL, isout);
-                if (isout) o.put(k0 + __popc(bal & ((1u << lane) - 1u)), u, x, Dx);
+                if (isout) o.put(k0 + __popc(bal & ((1u << lane) - 1u)), u, x, nf);
                 k0 += __popc(bal);
             }
             om = warp_sum(om);
@@ -325,11 +383,12 @@ __global__ void __launch_bounds__(ROW_CTA) k_orient_hub(const int32_t *__restric
         int64_t om = 0;
         for (int e0 = a; e0 < b; e0 += ROW_CTA) {
             const int e = e0 + threadIdx.x;
-            int x = 0, Dx = 0;
-            const bool isout = e < b && o.probe(u, b - a, e, x, Dx, om);
+            int x = 0;
+            int4 nf = make_int4(0, 0, 0, 0);
+            const bool isout = e < b && o.probe(u, b - a, e, x, nf, om);
             int tot;
             const int off = block_exclusive_scan(isout ? 1 : 0, &tot);
-            if (isout) o.put(k0 + off, u, x, Dx);
+            if (isout) o.put(k0 + off, u, x, nf);
             k0 += tot;
         }
         om = block_sum<int64_t>(om, s_buf);
@@ -453,20 +512,49 @@ static inline unsigned grid_for(int64_t work, int per_block, int64_t cap) {
 }
 
 // Degrees + wedge bins, per-row checks and neighbour sums.
-int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
-    k_degrees<<<grid_for(n, 1024, 1 << 30), 1024, 0, st>>>(rp, n, m, s.D, s.bins, s.counters);
+int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
+                  cudaStream_t st) {
+    k_degrees<<<grid_for(n, 1024, 1 << 30), 1024, 0, st>>>(rp, n, m, t.hub_min, s.D, s.bins, s.counters);
     const RowOut ro{s.sig1, s.sig2, s.outdeg, s.fp_row, s.fp_push};
-    k_row_stats<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, ci, n, m, s.D, ro, s.counters);
-    k_row_stats_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, ci, n, s.D, s.bins, ro, s.counters);
+    k_row_stats<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, ci, n, m, t.row_thread_max, t.hub_min, s.D, ro,
+                                                         s.counters);
+    k_row_stats_hub<<<t.num_sms * 4, ROW_CTA, 0, st>>>(rp, ci, n, s.D, s.bins, ro, s.counters);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // Oriented CSR and omega.
-int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, cudaStream_t st) {
+int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
+                  cudaStream_t st) {
     if (launch_scan(s.outdeg, s.out_ptr, n, s.scan_tmp, st)) return -1;
-    const Orient o{ci, s.D, s.sig1, s.out_ptr, s.out_col, s.out_D, s.out_src, s.out_rng, n};
-    k_orient<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(rp, n, m, o, s.out_ptr, s.omega);
-    k_orient_hub<<<152 * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters, s.omega);
+    k_node_info<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.D, s.sig1, s.out_ptr, n, s.info);
+    const Orient o{ci, s.info, s.out_col, s.out_D, s.out_src, s.out_rng, n};
+    k_orient<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, n, m, t.row_thread_max, t.hub_min, o, s.out_ptr, s.omega);
+    k_orient_hub<<<t.num_sms * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters, s.omega);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Batched input: every entry of row v must lie in v's own graph
+// [goff[g], goff[g+1]).  Rows are checked to be strictly ascending by the row
+// pass, so the first and last entries decide.
+__global__ void k_batch_check(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
+                              const int64_t *__restrict__ goff, int32_t G, int32_t *__restrict__ cnt) {
+    int err = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int lo = 0, hi = G - 1;   // last g with goff[g] <= v
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (goff[mid] <= v) lo = mid; else hi = mid - 1;
+        }
+        const int a = rp[v], b = rp[v + 1];   // bad row pointers are reported by k_degrees
+        if (a >= 0 && a < b && (int64_t)b <= m && (ci[a] < goff[lo] || ci[b - 1] >= goff[lo + 1])) err |= ERRB_CROSS;
+    }
+    err = __reduce_or_sync(FULL, err);
+    if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
+}
+
+int launch_batch_check(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const int64_t *goff, int32_t G,
+                       const Scratch &s, const Tune &t, cudaStream_t st) {
+    k_batch_check<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, ci, n, m, goff, G, s.counters);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

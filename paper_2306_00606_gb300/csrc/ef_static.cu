@@ -66,7 +66,7 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
         char msg[200];
         snprintf(msg, sizeof msg,
                  "ef_compute_static: graph needs %zu bytes of scratch, above the fixed %zu-byte maximum "
-                 "(about 164 n + 36 m + 48 min(n, m) bytes); use ef_compute_ex",
+                 "(about 180 n + 44 m + 48 min(n, m) bytes); use ef_compute_ex",
                  need, EF_STATIC_SCRATCH_BYTES);
         return fail(EF_ERR_ARG, msg);
     }
@@ -88,15 +88,16 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     }
     s.ftab = (double *)((char *)base + carve_scratch((char *)base, n, m, s));
     s.tq = reinterpret_cast<int64_t *>(s.ftab + fcap);
-    int num_sms = 0;
-    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    Tune t;
+    if (cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        prepare_kernels())
         return fail(EF_ERR_CUDA, "ef_compute_static: device query failed");
 
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t *rp = g->row_ptr, *ci = g->col_idx;
     if (cudaMemsetAsync(s.Tacc, 0, accumulator_bytes(s), st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: memset failed");
-    if (launch_prep_a(rp, ci, n, m, s, st))
+    if (launch_prep_a(rp, ci, n, m, s, t, st))
         return fail(EF_ERR_CUDA, "ef_compute_static: prep launch failed");
     int32_t h_cnt[NUM_COUNTERS];
     if (cudaMemcpyAsync(h_cnt, s.counters, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -105,11 +106,10 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     if (h_cnt[CNT_ERR]) return fail(EF_ERR_GRAPH, "ef_compute_static: input is not a symmetric simple sorted CSR");
     ef_outputs out = {};
     out.ef = out_ef;
-    if (launch_ftab(s.ftab, s.tq, s.counters, fcap, st) || launch_orient(rp, ci, n, m, s, st) ||
-        launch_wedge_small(rp, ci, s, precision, n, st) ||
-        launch_wedge_big(rp, ci, s, precision, 0, n, m, num_sms, st) ||
-        launch_out_hash(s, n, m, num_sms, st) || launch_tri_pairs(s, n, m, num_sms, st) ||
-        launch_finalize(s, precision, n, out, num_sms, st) ||
+    if (launch_ftab(s.ftab, s.tq, s.counters, fcap, st) || launch_orient(rp, ci, n, m, s, t, st) ||
+        launch_wedge_small(rp, ci, s, precision, n, t, st) || launch_wedge_big(rp, ci, s, precision, 0, n, m, t, st) ||
+        launch_out_hash(s, n, m, t, st) || launch_tri_pairs(s, n, m, t, st) ||
+        launch_finalize(s, precision, n, out, t, st) ||
         cudaMemcpyAsync(h_cnt, s.counters, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: launch failed");
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)

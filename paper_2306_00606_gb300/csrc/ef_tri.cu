@@ -25,6 +25,13 @@
 // the test but for rare long probe runs.  The oriented CSR carries each
 // out-neighbour's own list range, so no test waits for an out_ptr load.
 //
+// Measured and left out (4M-node power-law graph): L2 eviction hints
+// (evict_last on probes, evict_first on the candidate stream) changed
+// nothing; staging each tile's candidates in shared memory was slower
+// (2.00 against 1.84 ms).  The pass reads about 1.8 GB from DRAM per launch,
+// mostly misses of the long tail of membership probes (10% of the tests spread
+// over about 100 MB of tables and lists).
+//
 // The pass is integer-only: g comes from a table in fixed point (units of
 // 2^-F, F chosen per call from the maximum degree), so the sums are exact and
 // independent of the order of the atomics, and no FP64 instruction (one lane
@@ -37,11 +44,10 @@
 namespace ef {
 
 constexpr int TRI_WARPS = 8;
-// Candidate pairs per lane step and resident blocks per SM the registers are
-// sized for: measured on the 4M-node power-law graph, (2, 4) 1.80 ms,
-// (2, 3) 1.98, (2, 5) 2.06, (4, 3) 2.28, (4, 4) 2.51 (register spills).
-constexpr int TRI_UNIT = 2;
-constexpr int TRI_BLOCKS = 4;
+// Kernel variants: candidate pairs per lane step (TRI_UNIT) and resident
+// blocks per SM the registers are sized for.  Measured on the 4M-node
+// power-law graph: (2, 4) 1.80 ms, (2, 3) 1.98, (2, 5) 2.06, (4, 3) 2.28,
+// (4, 4) 2.51 (register spills).  Variant 0 = (2, 4), 1 = (4, 3).
 
 // Table of the out-list [ls, le) of one node: slots [base, base + 4 nb) of
 // out_hash, base = 2 ls rounded up to a multiple of 4 and 4 nb = 2 (le - ls)
@@ -160,14 +166,15 @@ __device__ __forceinline__ void credit_tri(int64_t *qacc, int64_t *tcnt, int v, 
     atomicAdd((unsigned long long *)(tcnt + v), (unsigned long long)cnt);
 }
 
+template <int TRI_UNIT, int TRI_BLOCKS>
 __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
     const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_D,
     const int2 *__restrict__ out_rng, const int32_t *__restrict__ out_src, const int32_t *__restrict__ out_hash,
     int64_t hash_cap, const int32_t *__restrict__ D, int32_t n, const int64_t *__restrict__ tq,
     int64_t *__restrict__ qacc, int64_t *__restrict__ tcnt) {
     __shared__ int s_ex[TRI_WARPS][32];   // exclusive prefix of unit counts
-    __shared__ int s_k[TRI_WARPS][32], s_kend[TRI_WARPS][32], s_b[TRI_WARPS][32], s_Db[TRI_WARPS][32];
-    __shared__ int s_bs[TRI_WARPS][32], s_be[TRI_WARPS][32], s_Dab[TRI_WARPS][32], s_a[TRI_WARPS][32];
+    __shared__ int s_kend[TRI_WARPS][32], s_b[TRI_WARPS][32], s_Db[TRI_WARPS][32], s_bs[TRI_WARPS][32];
+    __shared__ int s_be[TRI_WARPS][32], s_Dab[TRI_WARPS][32], s_a[TRI_WARPS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t total = out_ptr[n];
     const int64_t stride = (int64_t)gridDim.x * TRI_WARPS * 32;
@@ -182,7 +189,6 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
                 const int b = out_col[k];
                 const int Db = out_D[k];
                 const int2 rb = out_rng[k];
-                s_k[w][lane] = (int)k;
                 s_kend[w][lane] = kend;
                 s_b[w][lane] = b;
                 s_Db[w][lane] = Db;
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
         __syncwarp();
         int cur_a = -1, hit_a = 0;
         int64_t acc_a = 0;
-        int i = -1, ki = 0, kend = 0, exi = 0, b = 0, Db = 0, bs = 0, be = 0, Dab = 0, ai = 0;
+        int i = -1, kend = 0, exi = 0, b = 0, Db = 0, bs = 0, be = 0, Dab = 0, ai = 0;
         for (int t = lane; t < U; t += 32) {
             // the warp edge owning unit t: the last i with s_ex[i] <= t (s_ex is
             // non-decreasing; i + step <= 31 at every step)
@@ -214,7 +220,6 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
                 if (s_ex[w][ni + step] <= t) ni += step;
             if (ni != i) {
                 i = ni;
-                ki = s_k[w][i];
                 kend = s_kend[w][i];
                 exi = s_ex[w][i];
                 b = s_b[w][i];
@@ -224,18 +229,24 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
                 Dab = s_Dab[w][i];
                 ai = s_a[w][i];
             }
-            const int j0 = ki + 1 + TRI_UNIT * (t - exi);
-            const int jn = min(TRI_UNIT, kend - j0);
-            // issue every test's two quad loads first (bit 10 of info: b is the lower-ranked end)
-            Probe pr[TRI_UNIT];
-            int4 x[TRI_UNIT], y[TRI_UNIT];
+            const int64_t j0 = K0 + i + 1 + TRI_UNIT * (t - exi);
+            const int jn = (int)min((int64_t)TRI_UNIT, kend - j0);
             int c[TRI_UNIT], Dc[TRI_UNIT];
+            int2 rc[TRI_UNIT];
 #pragma unroll
             for (int q = 0; q < TRI_UNIT; ++q) {
                 if (q < jn) {
-                    c[q] = out_col[j0 + q];
-                    Dc[q] = out_D[j0 + q];
-                    const int2 r = out_rng[j0 + q];
+                    c[q] = __ldg(out_col + j0 + q);
+                    Dc[q] = __ldg(out_D + j0 + q);
+                    rc[q] = __ldg(out_rng + j0 + q);
+                }
+            }
+            Probe pr[TRI_UNIT];
+            int4 x[TRI_UNIT], y[TRI_UNIT];
+#pragma unroll
+            for (int q = 0; q < TRI_UNIT; ++q) {
+                if (q < jn) {
+                    const int2 r = rc[q];
                     const bool b_low = rank_less(Db, b, Dc[q], c[q]);
                     pr[q] = probe_of(out_col, out_hash, hash_cap, b_low ? bs : r.x, b_low ? be : r.y,
                                      b_low ? c[q] : b);
@@ -251,10 +262,9 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
                 if (q < jn) {
                     const bool b_low = (pr[q].info >> 10) & 1u;
                     int ls = bs, le = be;
-                    if (!b_low && (pr[q].info >> 8) & 3u) {   // rare ends only: c's own range
-                        const int2 r = out_rng[j0 + q];
-                        ls = r.x;
-                        le = r.y;
+                    if (!b_low) {
+                        ls = rc[q].x;
+                        le = rc[q].y;
                     }
                     if (probe_done(pr[q], x[q], y[q], out_col, out_hash, hash_cap, ls, le, b_low ? c[q] : b)) {
                         const int64_t g = __ldg(tq + Dab + Dc[q]);
@@ -288,17 +298,22 @@ static inline unsigned grid_of(int64_t work, int per_block, int64_t cap) {
     return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-int launch_out_hash(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st) {
+int launch_out_hash(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st) {
+    const int num_sms = t.num_sms;
     if (cudaMemsetAsync(s.out_hash, 0xff, (size_t)hash_slots(m) * sizeof(int32_t), st) != cudaSuccess) return -1;
     k_out_hash<<<grid_of(m / 2, 256, (int64_t)num_sms * 32), 256, 0, st>>>(s.out_ptr, s.out_col, s.out_src, n,
                                                                           hash_slots(m), s.out_hash);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, int num_sms, cudaStream_t st) {
-    k_tri_pairs<<<grid_of(m / 2, TRI_WARPS * 32, (int64_t)num_sms * 16), TRI_WARPS * 32, 0, st>>>(
-        s.out_ptr, s.out_col, s.out_D, s.out_rng, s.out_src, s.out_hash, hash_slots(m), s.D, n, s.tq, s.qacc,
-        s.tcnt);
+int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st) {
+    const unsigned grid = grid_of(m / 2, TRI_WARPS * 32, (int64_t)t.num_sms * 16);
+    if (t.tri_variant == 1)
+        k_tri_pairs<4, 3><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_rng, s.out_src,
+                                                            s.out_hash, hash_slots(m), s.D, n, s.tq, s.qacc, s.tcnt);
+    else
+        k_tri_pairs<2, 4><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_rng, s.out_src,
+                                                            s.out_hash, hash_slots(m), s.D, n, s.tq, s.qacc, s.tcnt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

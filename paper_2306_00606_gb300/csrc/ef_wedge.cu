@@ -441,7 +441,6 @@ __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
     }
 }
 
-int hub_grid(int num_sms) { return num_sms * 2; }
 
 template <bool F64>
 static void small_all(const int32_t *rp, const int32_t *ci, const Scratch &s, int32_t n, cudaStream_t st,
@@ -458,33 +457,48 @@ static void small_all(const int32_t *rp, const int32_t *ci, const Scratch &s, in
 }
 
 int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
-                       cudaStream_t st) {
+                       const Tune &t, cudaStream_t st) {
     int64_t g = ((int64_t)n + 63) / 64;
-    unsigned grid = (unsigned)(g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g));
+    const int64_t cap = (int64_t)t.num_sms * 16;
+    unsigned grid = (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
     if (precision == EF_PREC_FP64) small_all<true>(rp, ci, s, n, st, grid);
     else small_all<false>(rp, ci, s, n, st, grid);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <bool F64>
+static size_t hub_smem_bytes() {
+    using E = ClassEval<F64>;
+    return HUB_HIST * sizeof(int32_t) + HUB_SMEM_K * (sizeof(typename E::Cls) + sizeof(typename E::R));
+}
+
+// Opt the hub kernels in to their dynamic shared memory on the current device
+// (once per context, before any launch or stream capture).
+int prepare_kernels() {
+    if (cudaFuncSetAttribute(k_wedge_hub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)hub_smem_bytes<true>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_wedge_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)hub_smem_bytes<false>()) != cudaSuccess)
+        return -1;
+    return 0;
+}
+
+template <bool F64>
 static int big_classes(const int32_t *rp, const int32_t *ci, const Scratch &s, int32_t n, int num_sms,
                        cudaStream_t st) {
-    using E = ClassEval<F64>;
     const int32_t *mid = s.bins + (size_t)BIN_MID * n;
     k_wedge_mid<F64><<<(unsigned)(num_sms * 8), MID_WARPS * 32, 0, st>>>(rp, ci, s.D, mid, s.counters, s.ftab, s.Tacc,
                                                                          s.Ccenter);
-    const size_t smem = HUB_HIST * sizeof(int32_t) + HUB_SMEM_K * (sizeof(typename E::Cls) + sizeof(typename E::R));
-    if (cudaFuncSetAttribute(k_wedge_hub<F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return -1;
-    k_wedge_hub<F64><<<(unsigned)hub_grid(num_sms), HUB_THREADS, smem, st>>>(
+    const size_t smem = hub_smem_bytes<F64>();
+    k_wedge_hub<F64><<<(unsigned)(num_sms * 2), HUB_THREADS, smem, st>>>(
         rp, ci, s.D, s.bins, n, s.counters, s.ftab, s.Tacc, s.Ccenter, s.hub_cidx, s.hub_cls, s.hub_q);
     return 0;
 }
 
 int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int wedge_mode,
-                     int32_t n, int64_t m, int num_sms, cudaStream_t st) {
+                     int32_t n, int64_t m, const Tune &t, cudaStream_t st) {
     (void)m;
+    const int num_sms = t.num_sms;
     const int32_t *big = s.bins + (size_t)BIN_BIG * n;
     if (wedge_mode == 1) {
         if (launch_big_items(s, n, st)) return -1;
