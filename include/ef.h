@@ -191,6 +191,116 @@ int ef_autotune(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
                 const ef_options *opt, int32_t reps, ef_tuning *best);
 
 /*
+ * Exact EF of chosen nodes only (vertex-centric form of Algorithm 1: every
+ * cluster containing a chosen node, with its 2/1/1 credits).
+ *   g: CSR (device); nodes: int32[k] device node ids (duplicates allowed;
+ *   an id outside [0, n) gives EF_ERR_ARG); out: device arrays of length k
+ *   (out->ef[i] belongs to nodes[i]; any member may be NULL).
+ * Validation and precision as ef_compute_ex (host_io and async are not
+ * accepted: EF_ERR_ARG).
+ */
+int ef_compute_nodes(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
+                     const int32_t *nodes, int32_t k, const ef_options *opt,
+                     ef_outputs *out);
+
+/* ------------------------------------------------------------------------
+ * Learned ranking path.  A regression network 16-64-64-1 (ReLU, BF16
+ * tensor-core products with FP32 accumulation) maps 16 cheap per-node
+ * features to a predicted EF.  It is trained on exact EF produced by this
+ * library, ranks all nodes of a graph, and exact EF is then recomputed on
+ * the best-ranked candidates and on a random audit sample.
+ *
+ * Features (row-major float32 [n][16], natural logarithms):
+ *   0 ln(1+D)  1 ln(1+sigma1)  2 ln(1+sigma2)  3 ln(1+omega)
+ *   4 ln(1+mean neighbour degree)  5 ln(1+its standard deviation)
+ *   6 ln(1+min neighbour degree)   7 ln(1+max neighbour degree)
+ *   8 ln(1+N)   9 ln(1+S_open)   10 = 9 - 8   11 ln(1+t)
+ *   12 clustering t / C(D,2)   13 ln(1+S)   14 = 2 - 1   15 = 3 - 1
+ * with sigma1, sigma2 the sums of neighbour degrees and of their squares,
+ * omega the sum of the neighbours' sigma1, N the credited cluster count,
+ * S_open the credited degree sum at open degrees, t the triangles and
+ * S = S_open - 8t.  Feature mode 0 takes t = 0 (no triangle pass);
+ * mode 1 runs the triangle pass.
+ * ---------------------------------------------------------------------- */
+typedef struct ef_model ef_model;
+
+#define EF_MODEL_PARAMS 5313   /* W1[16][64], b1[64], W2[64][64], b2[64], w3[64], b3 */
+#define EF_MODEL_FLOATS (EF_MODEL_PARAMS + 32)   /* followed by mean[16], std[16] */
+
+/* Features of every node into x (device float32 [n*16]). */
+int ef_features(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
+                int32_t mode, const ef_options *opt, float *x);
+
+/* A model on the context's device: weights uniform in
+ * +-1/sqrt(fan in) from a counter-based generator (splitmix64 of seed),
+ * zero biases, standardisation unset (fitted from the first training data). */
+int ef_model_create(ef_ctx *ctx, uint64_t seed, int32_t feature_mode, ef_model **out);
+int ef_model_destroy(ef_model *model);
+/* Copy all EF_MODEL_FLOATS floats out of / into host memory (set marks the
+ * standardisation as fitted). */
+int ef_model_get(const ef_model *model, float *host);
+int ef_model_set(ef_model *model, const float *host);
+int ef_model_feature_mode(const ef_model *model);
+/* Binary file: 8-byte magic "EFMLP001", int32 feature mode, int32 fitted,
+ * EF_MODEL_FLOATS little-endian float32. */
+int ef_model_save(const ef_model *model, const char *path);
+int ef_model_load(ef_ctx *ctx, const char *path, ef_model **out);
+
+/* Predictions for n feature rows (device x float32 [n*16], out float32 [n]). */
+int ef_mlp_forward(ef_ctx *ctx, const ef_model *model, const float *x, int32_t n, float *out);
+/* Mean-squared-error loss over all n rows and its gradient with respect to
+ * the EF_MODEL_PARAMS parameters (device x, y; host loss and grad). */
+int ef_mlp_grad(ef_ctx *ctx, ef_model *model, const float *x, const float *y, int32_t n,
+                float *loss, float *grad);
+
+typedef struct {
+    int32_t steps;      /* Adam steps */
+    int32_t batch;      /* rows per step, sampled uniformly with replacement
+                           by a counter-based generator */
+    float lr;           /* Adam step size (beta1 0.9, beta2 0.999, eps 1e-8) */
+    int32_t pad;
+    uint64_t seed;
+} ef_train_options;
+
+typedef struct {
+    float first_loss, last_loss;   /* batch losses of the first and last step */
+    double ms;                     /* device time of the whole training */
+} ef_train_stats;
+
+/* Train on n rows (device x float32 [n*16], y float32 [n] = exact EF).
+ * The steps after the first replay one captured CUDA graph. */
+int ef_surrogate_train(ef_ctx *ctx, ef_model *model, const float *x, const float *y, int32_t n,
+                       const ef_train_options *opt, ef_train_stats *stats);
+
+typedef struct {
+    int32_t n_candidates;   /* nodes whose exact EF was recomputed as candidates */
+    int32_t n_audit;        /* audit sample size */
+    int32_t n_top;          /* size of the reported top set */
+    int32_t pad;
+    double spearman_audit;  /* Spearman rho of prediction vs exact EF on the audit sample */
+    double max_abs_err_audit;
+    double features_ms, infer_ms, select_ms, exact_ms, total_ms;
+} ef_rank_stats;
+
+/*
+ * Rank the nodes of g with the model:
+ * - features, then predictions of every node;
+ * - the ceil(cand_frac n) best-predicted nodes are the candidates;
+ * - an audit sample takes each node with probability audit_frac (splitmix64
+ *   of seed and node id);
+ * - exact EF (ef_compute_nodes) of candidates and audit nodes;
+ * - out_idx / out_ef (device, capacity ceil(top_frac n)) receive the
+ *   ceil(top_frac n) candidates of largest exact EF, in node-id order.
+ * The plain exact pass stays the reference: recall against it is
+ * measured by the caller.  out_score (device float32 [n], may be NULL)
+ * receives every prediction.  Requires 0 < top_frac <= cand_frac <= 1.
+ */
+int ef_surrogate_rank(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_model *model,
+                      float top_frac, float cand_frac, float audit_frac, uint64_t seed,
+                      const ef_options *opt, int32_t *out_idx, double *out_ef, float *out_score,
+                      ef_rank_stats *stats);
+
+/*
  * ef_compute_static: EF of every node with no memory allocation at all.
  * The paper has no counterpart; this is for callers that cannot allocate
  * device memory when they need EF (code inside a memory pool that owns the

@@ -26,7 +26,11 @@ PRECISIONS = {"fp64": EF_PREC_FP64, "fp32c": EF_PREC_FP32C}
 # Every symbol include/ef.h declares (checked by the CPU test of the ABI).
 EXPORTED = ("ef_ctx_create", "ef_ctx_destroy", "ef_last_error", "ef_sync", "ef_get_stats",
             "ef_compute", "ef_compute_ex", "ef_compute_batched", "ef_get_tuning", "ef_set_tuning", "ef_autotune",
-            "ef_compute_static")
+            "ef_compute_nodes", "ef_features", "ef_model_create", "ef_model_destroy", "ef_model_get", "ef_model_set",
+            "ef_model_feature_mode", "ef_model_save", "ef_model_load", "ef_mlp_forward", "ef_mlp_grad",
+            "ef_surrogate_train", "ef_surrogate_rank", "ef_compute_static")
+MODEL_PARAMS = 5313
+MODEL_FLOATS = MODEL_PARAMS + 32
 
 
 class EfError(RuntimeError):
@@ -59,6 +63,28 @@ class ef_stats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ef_train_options(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float), ("pad", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class ef_train_stats(ctypes.Structure):
+    _fields_ = [("first_loss", ctypes.c_float), ("last_loss", ctypes.c_float), ("ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ef_rank_stats(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int32), ("n_audit", ctypes.c_int32), ("n_top", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("spearman_audit", ctypes.c_double), ("max_abs_err_audit", ctypes.c_double),
+                ("features_ms", ctypes.c_double), ("infer_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
+                ("exact_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 class ef_tuning(ctypes.Structure):
@@ -96,6 +122,23 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ef_set_tuning.argtypes = [vp, ctypes.POINTER(ef_tuning)]
     lib.ef_autotune.argtypes = [vp, ctypes.POINTER(ef_csr), i32, i64, ctypes.POINTER(ef_options), i32,
                                 ctypes.POINTER(ef_tuning)]
+    lib.ef_compute_nodes.argtypes = [vp, ctypes.POINTER(ef_csr), i32, i64, vp, i32, ctypes.POINTER(ef_options),
+                                     ctypes.POINTER(ef_outputs)]
+    lib.ef_features.argtypes = [vp, ctypes.POINTER(ef_csr), i32, i64, i32, ctypes.POINTER(ef_options), vp]
+    lib.ef_model_create.argtypes = [vp, ctypes.c_uint64, i32, ctypes.POINTER(vp)]
+    lib.ef_model_destroy.argtypes = [vp]
+    lib.ef_model_get.argtypes = [vp, vp]
+    lib.ef_model_set.argtypes = [vp, vp]
+    lib.ef_model_feature_mode.argtypes = [vp]
+    lib.ef_model_save.argtypes = [vp, ctypes.c_char_p]
+    lib.ef_model_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(vp)]
+    lib.ef_mlp_forward.argtypes = [vp, vp, vp, i32, vp]
+    lib.ef_mlp_grad.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(ctypes.c_float), vp]
+    lib.ef_surrogate_train.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(ef_train_options),
+                                       ctypes.POINTER(ef_train_stats)]
+    lib.ef_surrogate_rank.argtypes = [vp, ctypes.POINTER(ef_csr), i32, i64, vp, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(ef_options), vp, vp, vp,
+                                      ctypes.POINTER(ef_rank_stats)]
     lib.ef_compute_static.argtypes = [ctypes.POINTER(ef_csr), i32, i64, i32, vp, vp]
     for name in EXPORTED:
         if name != "ef_last_error":
@@ -217,6 +260,145 @@ def ef_compute_static(row_ptr, col_idx, out_ef, precision: str = "fp64", stream:
     g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
     _check(load_library().ef_compute_static(ctypes.byref(g), n, int(col_idx.shape[0]), PRECISIONS[precision],
                                             _ptr(out_ef), stream or None))
+
+
+def ef_compute_nodes(ctx: int, row_ptr, col_idx, nodes, *, precision: str = "fp64", ef=None, n_clusters=None,
+                     s=None, t=None, triangles=None, flag=None, trust_input: bool = False) -> None:
+    """Exact EF of the listed nodes only (device tensors; outputs of length len(nodes))."""
+    n = int(row_ptr.shape[0]) - 1
+    g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
+    o = _options(precision, trust_input, False, False, False, 0, False)
+    out = ef_outputs(_ptr(ef), _ptr(n_clusters), _ptr(s), _ptr(t), _ptr(triangles), _ptr(flag))
+    _check(load_library().ef_compute_nodes(ctx, ctypes.byref(g), n, int(col_idx.shape[0]), _ptr(nodes),
+                                           int(nodes.shape[0]), ctypes.byref(o), ctypes.byref(out)), ctx)
+
+
+def ef_features(ctx: int, row_ptr, col_idx, x, *, mode: int = 0, trust_input: bool = False) -> None:
+    """The 16 learned-path features of every node into x (device float32 [n, 16])."""
+    n = int(row_ptr.shape[0]) - 1
+    g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
+    o = _options("fp64", trust_input, False, False, False, 0, False)
+    _check(load_library().ef_features(ctx, ctypes.byref(g), n, int(col_idx.shape[0]), int(mode), ctypes.byref(o),
+                                      _ptr(x)), ctx)
+
+
+def ef_model_create(ctx: int, seed: int = 0, feature_mode: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().ef_model_create(ctx, int(seed), int(feature_mode), ctypes.byref(h)), ctx)
+    return h.value
+
+
+def ef_model_destroy(model: int) -> None:
+    _check(load_library().ef_model_destroy(model))
+
+
+def ef_model_get(model: int) -> np.ndarray:
+    h = np.zeros(MODEL_FLOATS, dtype=np.float32)
+    _check(load_library().ef_model_get(model, h.ctypes.data))
+    return h
+
+
+def ef_model_set(model: int, flat) -> None:
+    h = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
+    if h.shape != (MODEL_FLOATS,):
+        raise EfError(EF_ERR_ARG, f"expected {MODEL_FLOATS} floats")
+    _check(load_library().ef_model_set(model, h.ctypes.data))
+
+
+def ef_model_feature_mode(model: int) -> int:
+    return load_library().ef_model_feature_mode(model)
+
+
+def ef_model_save(model: int, path: str) -> None:
+    _check(load_library().ef_model_save(model, str(path).encode()))
+
+
+def ef_model_load(ctx: int, path: str) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().ef_model_load(ctx, str(path).encode(), ctypes.byref(h)), ctx)
+    return h.value
+
+
+def ef_mlp_forward(ctx: int, model: int, x, out) -> None:
+    _check(load_library().ef_mlp_forward(ctx, model, _ptr(x), int(x.shape[0]), _ptr(out)), ctx)
+
+
+def ef_mlp_grad(ctx: int, model: int, x, y) -> tuple[float, np.ndarray]:
+    g = np.zeros(MODEL_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(load_library().ef_mlp_grad(ctx, model, _ptr(x), _ptr(y), int(x.shape[0]), ctypes.byref(loss),
+                                      g.ctypes.data), ctx)
+    return float(loss.value), g
+
+
+def ef_surrogate_train(ctx: int, model: int, x, y, *, steps: int, batch: int = 4096, lr: float = 1e-3,
+                       seed: int = 1) -> dict:
+    o = ef_train_options(int(steps), int(batch), float(lr), 0, int(seed))
+    st = ef_train_stats()
+    _check(load_library().ef_surrogate_train(ctx, model, _ptr(x), _ptr(y), int(x.shape[0]), ctypes.byref(o),
+                                             ctypes.byref(st)), ctx)
+    return st.as_dict()
+
+
+def ef_surrogate_rank(ctx: int, model: int, row_ptr, col_idx, out_idx, out_ef, *, top_frac: float = 0.01,
+                      cand_frac: float = 0.02, audit_frac: float = 0.001, seed: int = 7, precision: str = "fp32c",
+                      out_score=None, trust_input: bool = False) -> dict:
+    n = int(row_ptr.shape[0]) - 1
+    g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
+    o = _options(precision, trust_input, False, False, False, 0, False)
+    st = ef_rank_stats()
+    _check(load_library().ef_surrogate_rank(ctx, ctypes.byref(g), n, int(col_idx.shape[0]), model, float(top_frac),
+                                            float(cand_frac), float(audit_frac), int(seed), ctypes.byref(o),
+                                            _ptr(out_idx), _ptr(out_ef), _ptr(out_score), ctypes.byref(st)), ctx)
+    return st.as_dict()
+
+
+class Model:
+    """A surrogate network on the device of a context (wraps ef_model_*)."""
+
+    def __init__(self, ctx: int, seed: int = 0, feature_mode: int = 0, handle: int | None = None):
+        self.ctx = ctx
+        self.handle = ef_model_create(ctx, seed, feature_mode) if handle is None else handle
+
+    @classmethod
+    def load(cls, ctx: int, path: str) -> "Model":
+        return cls(ctx, handle=ef_model_load(ctx, path))
+
+    def close(self):
+        if self.handle:
+            ef_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def feature_mode(self) -> int:
+        return ef_model_feature_mode(self.handle)
+
+    def get(self) -> np.ndarray:
+        return ef_model_get(self.handle)
+
+    def set(self, flat) -> None:
+        ef_model_set(self.handle, flat)
+
+    def save(self, path: str) -> None:
+        ef_model_save(self.handle, path)
+
+    def forward(self, x, out) -> None:
+        ef_mlp_forward(self.ctx, self.handle, x, out)
+
+    def grad(self, x, y) -> tuple[float, np.ndarray]:
+        return ef_mlp_grad(self.ctx, self.handle, x, y)
+
+    def train(self, x, y, **kw) -> dict:
+        return ef_surrogate_train(self.ctx, self.handle, x, y, **kw)
+
+    def rank(self, row_ptr, col_idx, out_idx, out_ef, **kw) -> dict:
+        return ef_surrogate_rank(self.ctx, self.handle, row_ptr, col_idx, out_idx, out_ef, **kw)
 
 
 # ---------------------------------------------------------------- convenience

@@ -25,11 +25,15 @@
 // sizes, options and tuning stay the same (one cached graph per context).
 #include "ef_internal.cuh"
 
+#include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <stdarg.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <string.h>
+#include <vector>
 
 namespace {
 
@@ -68,6 +72,18 @@ struct ef_ctx {
     ef::Tune tune;
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey;   // zero-filled in ef_ctx_create
+    void *rank = nullptr;            // learned-path buffers (RankScratch)
+    size_t rank_bytes = 0;
+    void *acts = nullptr;            // training activations
+    size_t acts_bytes = 0;
+    double *dtmp = nullptr;          // small device scratch (feature sums)
+};
+
+struct ef_model {
+    int device = 0;
+    ef::ModelDev *d = nullptr;
+    int32_t feature_mode = 0;
+    int32_t fitted = 0;
 };
 
 namespace {
@@ -414,6 +430,164 @@ void from_abi(ef::Tune &t, const ef_tuning &a) {
 std::mutex g_default_mu;
 ef_ctx *g_default[64];
 
+// ----------------------------------------------------------- learned path
+size_t carve_rank(char *base, int32_t n, ef::RankScratch &r) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void * {
+        void *p = base ? base + off : nullptr;
+        off += al(bytes);
+        return p;
+    };
+    const size_t N = (size_t)n;
+    r.x = (float *)take(4 * N * ef::MLP_F);
+    r.score = (float *)take(4 * N);
+    r.nbr_min = (int32_t *)take(4 * N);
+    r.nbr_max = (int32_t *)take(4 * N);
+    r.key = (uint64_t *)take(8 * N);
+    r.flag = (int32_t *)take(4 * N);
+    r.pos = (int32_t *)take(4 * (N + 1));
+    r.list = (int32_t *)take(4 * N);
+    r.listL = (int32_t *)take(4 * N);
+    r.lista = (int32_t *)take(4 * N);
+    r.role = (int32_t *)take(4 * N);
+    r.hist = (int32_t *)take(4 * 65536);
+    r.sel = (uint64_t *)take(8 * 4);
+    r.scan_tmp = (int32_t *)take(4 * (N / 4096 + 4));
+    r.exact = (double *)take(8 * N);
+    r.exact_node = (double *)take(8 * N);
+    r.a_score = (float *)take(4 * N);
+    r.a_exact = (double *)take(8 * N);
+    return off;
+}
+
+// Scratch, part A with the validation readback, and the f tables: what every
+// learned-path entry needs before its own passes.
+int prepare_graph(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const ef_options &o,
+                  ef::Scratch &s, int64_t &fcap) {
+    using namespace ef;
+    const size_t need = carve_scratch(nullptr, n, m, s);
+    int rc = ensure_buffer(ctx, &ctx->scratch, &ctx->scratch_bytes, need, need / 8);
+    if (rc) return rc;
+    carve_scratch((char *)ctx->scratch, n, m, s);
+    Job j{rp, ci, n, m, nullptr, 0, o, ef_outputs{}};
+    rc = part_a(ctx, j, s, ctx->stream);
+    if (rc) return rc;
+    if (o.trust_input) {
+        const int64_t bound = (int64_t)n - 1 < m ? (int64_t)n - 1 : m;
+        fcap = 3 * (bound > 0 ? bound : 0) + 1;
+    } else {
+        CU(cudaMemcpyAsync(ctx->h_counters, s.counters, NUM_COUNTERS * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        if (ctx->h_counters[CNT_ERR]) return graph_error(ctx, ctx->h_counters[CNT_ERR]);
+        fcap = 3 * (int64_t)ctx->h_counters[CNT_MAXDEG] + 1;
+    }
+    size_t have = (size_t)ctx->ftab_cap * 2 * sizeof(double);
+    rc = ensure_buffer(ctx, (void **)&ctx->ftab, &have, (size_t)fcap * 2 * sizeof(double), 0);
+    if (rc) return rc;
+    ctx->ftab_cap = (int64_t)(have / (2 * sizeof(double)));
+    s.ftab = ctx->ftab;
+    s.tq = reinterpret_cast<int64_t *>(ctx->ftab + fcap);
+    LAUNCH(launch_ftab(s.ftab, s.tq, s.counters, fcap, ctx->stream), "f table");
+    return EF_OK;
+}
+
+int rank_buffers(ef_ctx *ctx, int32_t n, ef::RankScratch &r) {
+    const size_t need = carve_rank(nullptr, n, r);
+    int rc = ensure_buffer(ctx, &ctx->rank, &ctx->rank_bytes, need, 0);
+    if (rc) return rc;
+    carve_rank((char *)ctx->rank, n, r);
+    return EF_OK;
+}
+
+// Features of every node into x (after prepare_graph).
+int features_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, int mode,
+                    const ef::Scratch &s, ef::RankScratch r, float *x) {
+    using namespace ef;
+    cudaStream_t st = ctx->stream;
+    LAUNCH(launch_omega_mm(rp, ci, n, m, s, r, ctx->tune, st), "omega");
+    if (mode == 1) {
+        LAUNCH(launch_orient(rp, ci, n, m, s, ctx->tune, st), "orientation");
+        LAUNCH(launch_out_hash(s, n, m, ctx->tune, st), "out-list hash");
+        LAUNCH(launch_tri_pairs(s, n, m, ctx->tune, st), "triangle");
+    }
+    r.x = x;
+    LAUNCH(launch_features(s, r, n, mode, ctx->tune, st), "features");
+    return EF_OK;
+}
+
+// Exact EF of list[0..k) (k on the device when kptr is given): the wedge
+// kernels over bins of the listed nodes, then a CTA per listed node.
+int nodes_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const ef::Scratch &s,
+                 const int32_t *list, int32_t kmax, const int32_t *kptr, int precision, const ef_outputs &out) {
+    using namespace ef;
+    cudaStream_t st = ctx->stream;
+    LAUNCH(launch_bin_nodes(list, kmax, kptr, s, n, ctx->tune.hub_min, st), "node bins");
+    LAUNCH(launch_wedge_small(rp, ci, s, precision, n, ctx->tune, st), "small wedge");
+    LAUNCH(launch_wedge_big(rp, ci, s, precision, 0, n, m, ctx->tune, st), "big wedge");
+    LAUNCH(launch_nodes_exact(rp, ci, s, list, kmax, kptr, n, precision, out, ctx->tune, st), "node exact");
+    return EF_OK;
+}
+
+int final_check(ef_ctx *ctx, const ef::Scratch &s, bool validate) {
+    CU(cudaMemcpyAsync(ctx->h_counters + ef::CNT_ERR, s.counters + ef::CNT_ERR, sizeof(int32_t),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const int bits = ctx->h_counters[ef::CNT_ERR];
+    if (bits & ef::ERRB_NODE) {
+        set_err(ctx, "a requested node id is outside [0, n)");
+        return EF_ERR_ARG;
+    }
+    if (validate && bits) return graph_error(ctx, bits);
+    CU(cudaGetLastError());
+    return EF_OK;
+}
+
+int check_learned_opts(ef_ctx *ctx, const ef_options &o) {
+    int rc = check_opts(ctx, o);
+    if (rc) return rc;
+    if (o.host_io || o.async) { set_err(ctx, "host_io and async are not available on this entry point"); return EF_ERR_ARG; }
+    return EF_OK;
+}
+
+uint64_t splitmix64(uint64_t &x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Spearman rho with average ranks for ties (host, audit sample only).
+double spearman(const std::vector<double> &a, const std::vector<double> &b) {
+    const size_t n = a.size();
+    if (n < 2) return 0.0;
+    auto ranks = [&](const std::vector<double> &x) {
+        std::vector<size_t> o(n);
+        for (size_t i = 0; i < n; ++i) o[i] = i;
+        std::stable_sort(o.begin(), o.end(), [&](size_t i, size_t j) { return x[i] < x[j]; });
+        std::vector<double> r(n);
+        for (size_t i = 0; i < n;) {
+            size_t j = i;
+            while (j + 1 < n && x[o[j + 1]] == x[o[i]]) ++j;
+            for (size_t q = i; q <= j; ++q) r[o[q]] = (double)(i + j) / 2.0 + 1.0;
+            i = j + 1;
+        }
+        return r;
+    };
+    std::vector<double> ra = ranks(a), rb = ranks(b);
+    double ma = 0, mb = 0;
+    for (size_t i = 0; i < n; ++i) { ma += ra[i]; mb += rb[i]; }
+    ma /= n;
+    mb /= n;
+    double sab = 0, saa = 0, sbb = 0;
+    for (size_t i = 0; i < n; ++i) {
+        sab += (ra[i] - ma) * (rb[i] - mb);
+        saa += (ra[i] - ma) * (ra[i] - ma);
+        sbb += (rb[i] - mb) * (rb[i] - mb);
+    }
+    return saa > 0 && sbb > 0 ? sab / std::sqrt(saa * sbb) : 0.0;
+}
+
 }  // namespace
 
 namespace ef {
@@ -508,6 +682,9 @@ int ef_ctx_destroy(ef_ctx *ctx) {
     cudaFree(ctx->ftab);
     cudaFree(ctx->io);
     cudaFree(ctx->goff);
+    cudaFree(ctx->rank);
+    cudaFree(ctx->acts);
+    cudaFree(ctx->dtmp);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     for (int i = 0; i < 8; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
@@ -653,6 +830,350 @@ int ef_autotune(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_opt
     }
     ctx->tune = cur;
     *best = to_abi(cur);
+    return EF_OK;
+}
+
+int ef_compute_nodes(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const int32_t *nodes, int32_t k,
+                     const ef_options *opt, ef_outputs *out) {
+    if (!ctx) { set_err(nullptr, "null context"); return EF_ERR_ARG; }
+    ef_options o = {};
+    if (opt) o = *opt;
+    int rc = check_args(ctx, g, n, m, o, out);
+    if (rc) return rc;
+    rc = check_learned_opts(ctx, o);
+    if (rc) return rc;
+    if (k < 0 || (k > 0 && !nodes)) { set_err(ctx, "bad node list"); return EF_ERR_ARG; }
+    ctx->err[0] = 0;
+    if (k == 0) return EF_OK;
+    if (n == 0) { set_err(ctx, "node ids given for an empty graph"); return EF_ERR_ARG; }
+    DeviceGuard dg(ctx->device);
+    ef::Scratch s;
+    int64_t fcap;
+    rc = prepare_graph(ctx, g->row_ptr, g->col_idx, n, m, o, s, fcap);
+    if (rc) return rc;
+    ef::RankScratch r = {};
+    LAUNCH(ef::launch_omega_mm(g->row_ptr, g->col_idx, n, m, s, r, ctx->tune, ctx->stream), "omega");
+    rc = nodes_device(ctx, g->row_ptr, g->col_idx, n, m, s, nodes, k, nullptr, o.precision, *out);
+    if (rc) return rc;
+    return final_check(ctx, s, !o.trust_input);
+}
+
+int ef_features(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, int32_t mode, const ef_options *opt, float *x) {
+    if (!ctx) { set_err(nullptr, "null context"); return EF_ERR_ARG; }
+    ef_options o = {};
+    if (opt) o = *opt;
+    ef_outputs none = {};
+    int rc = check_args(ctx, g, n, m, o, &none);
+    if (rc) return rc;
+    rc = check_learned_opts(ctx, o);
+    if (rc) return rc;
+    if (mode < 0 || mode > 1 || (n > 0 && !x)) { set_err(ctx, "bad feature mode or null output"); return EF_ERR_ARG; }
+    ctx->err[0] = 0;
+    if (n == 0) return EF_OK;
+    DeviceGuard dg(ctx->device);
+    ef::Scratch s;
+    int64_t fcap;
+    rc = prepare_graph(ctx, g->row_ptr, g->col_idx, n, m, o, s, fcap);
+    if (rc) return rc;
+    ef::RankScratch r;
+    rc = rank_buffers(ctx, n, r);
+    if (rc) return rc;
+    rc = features_device(ctx, g->row_ptr, g->col_idx, n, m, mode, s, r, x);
+    if (rc) return rc;
+    return final_check(ctx, s, !o.trust_input);
+}
+
+int ef_model_create(ef_ctx *ctx, uint64_t seed, int32_t feature_mode, ef_model **out) {
+    if (!ctx || !out || feature_mode < 0 || feature_mode > 1) { set_err(ctx, "bad model arguments"); return EF_ERR_ARG; }
+    *out = nullptr;
+    DeviceGuard dg(ctx->device);
+    std::vector<float> h(EF_MODEL_FLOATS, 0.f);
+    uint64_t x = seed;
+    auto init = [&](int off, int count, int fan_in) {
+        for (int i = 0; i < count; ++i) {
+            const double u = (double)(splitmix64(x) >> 11) * (1.0 / 9007199254740992.0);
+            h[off + i] = (float)((2.0 * u - 1.0) / std::sqrt((double)fan_in));
+        }
+    };
+    init(ef::P_W1, ef::MLP_F * ef::MLP_H, ef::MLP_F);
+    init(ef::P_W2, ef::MLP_H * ef::MLP_H, ef::MLP_H);
+    init(ef::P_W3, ef::MLP_H, ef::MLP_H);
+    for (int f = 0; f < ef::MLP_F; ++f) h[ef::P_N + ef::MLP_F + f] = 1.f;   // std
+    ef_model *mdl = new (std::nothrow) ef_model();
+    if (!mdl) { set_err(ctx, "host allocation failed"); return EF_ERR_OOM; }
+    mdl->device = ctx->device;
+    mdl->feature_mode = feature_mode;
+    cudaError_t e = cudaMalloc(&mdl->d, sizeof(ef::ModelDev));
+    if (e == cudaSuccess) e = cudaMemset(mdl->d, 0, sizeof(ef::ModelDev));
+    if (e == cudaSuccess) e = cudaMemcpy(mdl->d->p, h.data(), sizeof(float) * ef::P_N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(mdl->d->mean, h.data() + ef::P_N, sizeof(float) * 2 * ef::MLP_F, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&mdl->d->feature_mode, &feature_mode, sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && ef::launch_model_pack(mdl->d, nullptr)) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        set_err(ctx, "model set-up failed: %s", cudaGetErrorString(e));
+        cudaFree(mdl->d);
+        delete mdl;
+        return e == cudaErrorMemoryAllocation ? EF_ERR_OOM : EF_ERR_CUDA;
+    }
+    *out = mdl;
+    return EF_OK;
+}
+
+int ef_model_destroy(ef_model *model) {
+    if (!model) return EF_OK;
+    DeviceGuard dg(model->device);
+    cudaFree(model->d);
+    delete model;
+    return EF_OK;
+}
+
+int ef_model_feature_mode(const ef_model *model) { return model ? model->feature_mode : -1; }
+
+int ef_model_get(const ef_model *model, float *host) {
+    if (!model || !host) return EF_ERR_ARG;
+    DeviceGuard dg(model->device);
+    if (cudaMemcpy(host, model->d->p, sizeof(float) * ef::P_N, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(host + ef::P_N, model->d->mean, sizeof(float) * 2 * ef::MLP_F, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return EF_ERR_CUDA;
+    return EF_OK;
+}
+
+int ef_model_set(ef_model *model, const float *host) {
+    if (!model || !host) return EF_ERR_ARG;
+    for (int f = 0; f < ef::MLP_F; ++f)
+        if (!(host[ef::P_N + ef::MLP_F + f] > 0.f)) return EF_ERR_MODEL;   // std must be positive
+    DeviceGuard dg(model->device);
+    if (cudaMemcpy(model->d->p, host, sizeof(float) * ef::P_N, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(model->d->mean, host + ef::P_N, sizeof(float) * 2 * ef::MLP_F, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        ef::launch_model_pack(model->d, nullptr) || cudaDeviceSynchronize() != cudaSuccess)
+        return EF_ERR_CUDA;
+    model->fitted = 1;
+    return EF_OK;
+}
+
+int ef_model_save(const ef_model *model, const char *path) {
+    if (!model || !path) return EF_ERR_ARG;
+    std::vector<float> h(EF_MODEL_FLOATS);
+    int rc = ef_model_get(model, h.data());
+    if (rc) return rc;
+    FILE *f = fopen(path, "wb");
+    if (!f) return EF_ERR_ARG;
+    const char magic[8] = {'E', 'F', 'M', 'L', 'P', '0', '0', '1'};
+    const int32_t hdr[2] = {model->feature_mode, model->fitted};
+    const bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(int32_t), 2, f) == 2 &&
+                    fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
+    return fclose(f) == 0 && ok ? EF_OK : EF_ERR_ARG;
+}
+
+int ef_model_load(ef_ctx *ctx, const char *path, ef_model **out) {
+    if (!ctx || !path || !out) { set_err(ctx, "bad arguments"); return EF_ERR_ARG; }
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) { set_err(ctx, "cannot open %s", path); return EF_ERR_ARG; }
+    char magic[8];
+    int32_t hdr[2];
+    std::vector<float> h(EF_MODEL_FLOATS);
+    const bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "EFMLP001", 8) == 0 &&
+                    fread(hdr, sizeof(int32_t), 2, f) == 2 && fread(h.data(), sizeof(float), h.size(), f) == h.size();
+    fclose(f);
+    if (!ok || hdr[0] < 0 || hdr[0] > 1) { set_err(ctx, "%s is not a model file", path); return EF_ERR_MODEL; }
+    int rc = ef_model_create(ctx, 0, hdr[0], out);
+    if (rc) return rc;
+    rc = ef_model_set(*out, h.data());
+    if (rc) {
+        ef_model_destroy(*out);
+        *out = nullptr;
+        set_err(ctx, "%s holds an invalid model", path);
+        return rc;
+    }
+    (*out)->fitted = hdr[1];
+    return EF_OK;
+}
+
+int ef_mlp_forward(ef_ctx *ctx, const ef_model *model, const float *x, int32_t n, float *out) {
+    if (!ctx || !model || n < 0 || (n > 0 && (!x || !out))) { set_err(ctx, "bad arguments"); return EF_ERR_ARG; }
+    if (model->device != ctx->device) { set_err(ctx, "model and context on different devices"); return EF_ERR_MODEL; }
+    if (n == 0) return EF_OK;
+    DeviceGuard dg(ctx->device);
+    LAUNCH(ef::launch_mlp_infer(model->d, x, n, out, ctx->num_sms, ctx->stream), "network");
+    CU(cudaStreamSynchronize(ctx->stream));
+    return EF_OK;
+}
+
+int ef_mlp_grad(ef_ctx *ctx, ef_model *model, const float *x, const float *y, int32_t n, float *loss, float *grad) {
+    if (!ctx || !model || n < 1 || !x || !y || !loss || !grad) { set_err(ctx, "bad arguments"); return EF_ERR_ARG; }
+    if (model->device != ctx->device) { set_err(ctx, "model and context on different devices"); return EF_ERR_MODEL; }
+    DeviceGuard dg(ctx->device);
+    int rc = ensure_buffer(ctx, &ctx->acts, &ctx->acts_bytes, ef::mlp_act_bytes(n), 0);
+    if (rc) return rc;
+    LAUNCH(ef::launch_mlp_step(model->d, x, y, n, n, 0, false, false, false, 0.f, (uint16_t *)ctx->acts,
+                               ctx->num_sms, ctx->stream),
+           "network gradient");
+    float ls = 0.f;
+    CU(cudaMemcpyAsync(grad, model->d->grad, sizeof(float) * ef::P_N, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(&ls, &model->d->loss_sum, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *loss = ls / (float)n;
+    return EF_OK;
+}
+
+int ef_surrogate_train(ef_ctx *ctx, ef_model *model, const float *x, const float *y, int32_t n,
+                       const ef_train_options *opt, ef_train_stats *stats) {
+    if (!ctx || !model || !opt || n < 1 || !x || !y || opt->steps < 1 || opt->batch < 1 || !(opt->lr > 0.f)) {
+        set_err(ctx, "bad training arguments");
+        return EF_ERR_ARG;
+    }
+    if (model->device != ctx->device) { set_err(ctx, "model and context on different devices"); return EF_ERR_MODEL; }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = ctx->stream;
+    int rc = ensure_buffer(ctx, &ctx->acts, &ctx->acts_bytes, ef::mlp_act_bytes(opt->batch), 0);
+    if (rc) return rc;
+    if (!ctx->dtmp) CU(cudaMalloc(&ctx->dtmp, 64 * sizeof(double)));
+    if (!model->fitted) {
+        LAUNCH(ef::launch_feature_stats(x, n, model->d, ctx->dtmp, st), "feature statistics");
+        LAUNCH(ef::launch_model_pack(model->d, st), "model pack");
+        model->fitted = 1;
+    }
+    uint16_t *acts = (uint16_t *)ctx->acts;
+    auto step = [&](cudaStream_t s) {
+        return ef::launch_mlp_step(model->d, x, y, n, opt->batch, opt->seed, true, true, true, opt->lr, acts,
+                                   ctx->num_sms, s);
+    };
+    float first = 0.f, last = 0.f;
+    CU(cudaEventRecord(ctx->ev[0], st));
+    LAUNCH(step(st), "training step");
+    CU(cudaMemcpyAsync(&first, &model->d->loss_sum, sizeof(float), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (opt->steps > 1) {
+        // the remaining steps replay one captured step (a private graph)
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        CU(cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
+        const int lrc = step(ctx->capture);
+        const cudaError_t ec = cudaStreamEndCapture(ctx->capture, &g);
+        if (lrc || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            set_err(ctx, "training step capture failed");
+            return EF_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        CU(ei);
+        cudaError_t el = cudaSuccess;
+        for (int i = 1; i < opt->steps && el == cudaSuccess; ++i) el = cudaGraphLaunch(ge, st);
+        if (el == cudaSuccess) el = cudaStreamSynchronize(st);
+        cudaGraphExecDestroy(ge);
+        CU(el);
+    }
+    CU(cudaEventRecord(ctx->ev[7], st));
+    CU(cudaMemcpyAsync(&last, &model->d->loss_sum, sizeof(float), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (stats) {
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[7]));
+        stats->first_loss = first / (float)opt->batch;
+        stats->last_loss = last / (float)opt->batch;
+        stats->ms = ms;
+    }
+    return EF_OK;
+}
+
+int ef_surrogate_rank(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_model *model, float top_frac,
+                      float cand_frac, float audit_frac, uint64_t seed, const ef_options *opt, int32_t *out_idx,
+                      double *out_ef, float *out_score, ef_rank_stats *stats) {
+    using namespace ef;
+    if (!ctx) { set_err(nullptr, "null context"); return EF_ERR_ARG; }
+    ef_options o = {};
+    if (opt) o = *opt;
+    ef_outputs none = {};
+    int rc = check_args(ctx, g, n, m, o, &none);
+    if (rc) return rc;
+    rc = check_learned_opts(ctx, o);
+    if (rc) return rc;
+    if (!model || !(top_frac > 0.f) || !(cand_frac >= top_frac) || cand_frac > 1.f || audit_frac < 0.f ||
+        audit_frac > 1.f || n < 1) {
+        set_err(ctx, "need a model, 0 < top_frac <= cand_frac <= 1, 0 <= audit_frac <= 1 and n >= 1");
+        return EF_ERR_ARG;
+    }
+    if (model->device != ctx->device) { set_err(ctx, "model and context on different devices"); return EF_ERR_MODEL; }
+    if (!model->fitted) { set_err(ctx, "the model is not trained"); return EF_ERR_MODEL; }
+    ctx->err[0] = 0;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int32_t kc = (int32_t)std::min<int64_t>(n, (int64_t)std::ceil((double)cand_frac * n));
+    const int32_t kt = (int32_t)std::min<int64_t>(kc, (int64_t)std::ceil((double)top_frac * n));
+    CU(cudaEventRecord(ctx->ev[0], st));
+    Scratch s;
+    int64_t fcap;
+    rc = prepare_graph(ctx, g->row_ptr, g->col_idx, n, m, o, s, fcap);
+    if (rc) return rc;
+    RankScratch r;
+    rc = rank_buffers(ctx, n, r);
+    if (rc) return rc;
+    rc = features_device(ctx, g->row_ptr, g->col_idx, n, m, model->feature_mode, s, r, r.x);
+    if (rc) return rc;
+    CU(cudaEventRecord(ctx->ev[1], st));
+    LAUNCH(launch_mlp_infer(model->d, r.x, n, r.score, ctx->num_sms, st), "network");
+    if (out_score) CU(cudaMemcpyAsync(out_score, r.score, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    CU(cudaEventRecord(ctx->ev[2], st));
+    // candidates, audit sample, their union
+    LAUNCH(launch_keys_score(r.score, n, r.key, st), "keys");
+    LAUNCH(launch_select_top(r, n, kc, ctx->tune, st), "candidate selection");
+    const double thr = std::ldexp((double)audit_frac, 64);
+    const uint64_t threshold = audit_frac >= 1.f ? ~0ull : (uint64_t)thr;
+    LAUNCH(launch_roles(r.list, kc, n, seed, threshold, r.role, st), "roles");
+    LAUNCH(launch_compact_role(r.role, n, 3, r.flag, r.pos, r.scan_tmp, r.listL, st), "listing");
+    const int32_t *kL = r.pos + n;   // count of listed nodes, on the device
+    CU(cudaEventRecord(ctx->ev[3], st));
+    ef_outputs eo = {};
+    eo.ef = r.exact;
+    rc = nodes_device(ctx, g->row_ptr, g->col_idx, n, m, s, r.listL, n, kL, o.precision, eo);
+    if (rc) return rc;
+    CU(cudaEventRecord(ctx->ev[4], st));
+    // the reported top set: largest exact EF among the candidates
+    CU(cudaMemsetAsync(r.key, 0, sizeof(uint64_t) * n, st));
+    LAUNCH(launch_exact_keys(r.listL, kL, n, r.exact, r.role, r.exact_node, r.key, st), "exact keys");
+    LAUNCH(launch_select_top(r, n, kt, ctx->tune, st), "top selection");
+    LAUNCH(launch_gather_top(r.list, kt, r.exact_node, out_idx, out_ef, st), "top set");
+    // audit sample: predictions against exact EF
+    LAUNCH(launch_compact_role(r.role, n, 2, r.flag, r.pos, r.scan_tmp, r.lista, st), "audit listing");
+    LAUNCH(launch_gather_audit(r.lista, r.pos + n, n, r.score, r.exact_node, r.a_score, r.a_exact, st), "audit");
+    CU(cudaEventRecord(ctx->ev[5], st));
+    int32_t na = 0;
+    CU(cudaMemcpyAsync(&na, r.pos + n, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    rc = final_check(ctx, s, !o.trust_input);
+    if (rc) return rc;
+    if (stats) {
+        std::vector<float> as(na);
+        std::vector<double> ae(na), ps(na);
+        if (na > 0) {
+            CU(cudaMemcpy(as.data(), r.a_score, sizeof(float) * na, cudaMemcpyDeviceToHost));
+            CU(cudaMemcpy(ae.data(), r.a_exact, sizeof(double) * na, cudaMemcpyDeviceToHost));
+        }
+        double mx = 0.0;
+        for (int32_t i = 0; i < na; ++i) {
+            ps[i] = as[i];
+            mx = std::max(mx, std::fabs(ps[i] - ae[i]));
+        }
+        stats->n_candidates = kc;
+        stats->n_audit = na;
+        stats->n_top = kt;
+        stats->spearman_audit = spearman(ps, ae);
+        stats->max_abs_err_audit = mx;
+        float t[5];
+        for (int i = 0; i < 4; ++i) CU(cudaEventElapsedTime(&t[i], ctx->ev[i], ctx->ev[i + 1]));
+        CU(cudaEventElapsedTime(&t[4], ctx->ev[0], ctx->ev[5]));
+        stats->features_ms = t[0];
+        stats->infer_ms = t[1];
+        stats->select_ms = t[2];
+        stats->exact_ms = t[3];
+        stats->total_ms = t[4];
+    }
     return EF_OK;
 }
 

@@ -43,6 +43,7 @@ enum : int {
     ERRB_UNSORTED = 8,  // a row not strictly ascending (includes duplicates)
     ERRB_ASYM = 16,     // x in N(u) but u not in N(x)
     ERRB_CROSS = 32,    // batched input: an entry outside its row's graph
+    ERRB_NODE = 64,     // a requested node id outside [0, n)
 };
 
 // Work bins (each a list of node ids of capacity n), filled from the degrees.
@@ -224,6 +225,55 @@ constexpr double LN2 = 0.69314718055994530942;
 
 }  // namespace ef
 
+namespace ef {
+
+// ---------------------------------------------------- learned ranking path
+// The regression network 16-64-64-1 (ReLU) on standardised node features.
+// Parameters in flattened order: W1 [16][64] row-major, b1[64], W2 [64][64]
+// row-major (W2[i][j] joins unit i of layer 1 to unit j of layer 2), b2[64],
+// w3[64], b3.
+constexpr int MLP_F = 16, MLP_H = 64;
+constexpr int P_W1 = 0, P_B1 = 1024, P_W2 = 1088, P_B2 = 5184, P_W3 = 5248, P_B3 = 5312, P_N = 5313;
+
+// A model on the device (one allocation): FP32 master parameters, the
+// standardisation, Adam moments, the gradient buffer and BF16 copies of the
+// weights laid out for the tensor-core fragments (w1t[j][f] = W1[f][j],
+// w2t[j][i] = W2[i][j], w2r = W2 row-major).
+struct ModelDev {
+    float p[P_N];
+    float mean[MLP_F], stdv[MLP_F];
+    float m[P_N], v[P_N], grad[P_N];
+    float loss_sum;
+    int32_t step;
+    int32_t feature_mode;   // 0: features without triangles, 1: with
+    int32_t pad;
+    __align__(16) uint16_t w1t[MLP_H * MLP_F];
+    __align__(16) uint16_t w2t[MLP_H * MLP_H];
+    __align__(16) uint16_t w2r[MLP_H * MLP_H];
+};
+
+// Working buffers of the learned path (carved from one allocation).
+struct RankScratch {
+    float *x;            // n x 16 features
+    float *score;        // n predictions
+    int32_t *nbr_min, *nbr_max;   // n
+    uint64_t *key;       // n selection keys
+    int32_t *flag, *pos; // n and n+1: compaction flags and their scan
+    int32_t *list;       // n: selected node ids
+    int32_t *listL;      // n: candidates and audit nodes
+    int32_t *lista;      // n: audit nodes
+    int32_t *role;       // n: bit 1 candidate, bit 2 audit
+    int32_t *hist;       // 65536 digit counts
+    uint64_t *sel;       // selection state: prefix, need, k
+    int32_t *scan_tmp;
+    double *exact;       // n: exact EF of listL by position
+    double *exact_node;  // n: exact EF by node (listed nodes only)
+    float *a_score;      // n: audit predictions
+    double *a_exact;     // n: audit exact EF
+};
+
+}  // namespace ef
+
 // ------------------------------------------------------------ launchers
 namespace ef {
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
@@ -244,4 +294,31 @@ int launch_out_hash(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaS
 int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st);
 int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs &out, const Tune &t,
                     cudaStream_t st);
+// learned path (ef_mlp.cu, ef_rank.cu)
+int launch_mlp_infer(const ModelDev *M, const float *x, int32_t n, float *out, int num_sms, cudaStream_t st);
+int launch_mlp_step(ModelDev *M, const float *x, const float *y, int32_t n, int32_t batch, uint64_t seed, bool sample,
+                    bool count_step, bool adam, float lr, uint16_t *acts, int num_sms, cudaStream_t st);
+size_t mlp_act_bytes(int32_t batch);
+int launch_model_pack(ModelDev *M, cudaStream_t st);
+int launch_feature_stats(const float *x, int32_t n, ModelDev *M, double *tmp, cudaStream_t st);
+int launch_omega_mm(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s,
+                    const RankScratch &r, const Tune &t, cudaStream_t st);
+int launch_features(const Scratch &s, const RankScratch &r, int32_t n, int mode, const Tune &t, cudaStream_t st);
+int launch_select_top(const RankScratch &r, int32_t n, int64_t k, const Tune &t, cudaStream_t st);
+int launch_bin_nodes(const int32_t *list, int32_t k, const int32_t *kptr, const Scratch &s, int32_t n, int hub_min,
+                     cudaStream_t st);
+int launch_nodes_exact(const int32_t *rp, const int32_t *ci, const Scratch &s, const int32_t *list, int32_t k,
+                       const int32_t *kptr, int32_t n, int precision, const ef_outputs &out, const Tune &t,
+                       cudaStream_t st);
+int launch_keys_score(const float *score, int32_t n, uint64_t *key, cudaStream_t st);
+int launch_roles(const int32_t *cand, int32_t kc, int32_t n, uint64_t seed, uint64_t threshold, int32_t *role,
+                 cudaStream_t st);
+int launch_compact_role(const int32_t *role, int32_t n, int mask, int32_t *flag, int32_t *pos, int32_t *tmp,
+                        int32_t *list, cudaStream_t st);
+int launch_exact_keys(const int32_t *L, const int32_t *kL, int32_t kmax, const double *exact, const int32_t *role,
+                      double *exact_node, uint64_t *key, cudaStream_t st);
+int launch_gather_top(const int32_t *list, int32_t k, const double *exact_node, int32_t *out_idx, double *out_ef,
+                      cudaStream_t st);
+int launch_gather_audit(const int32_t *list, const int32_t *ka, int32_t kmax, const float *score,
+                        const double *exact_node, float *a_score, double *a_exact, cudaStream_t st);
 }  // namespace ef

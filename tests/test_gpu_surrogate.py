@@ -1,0 +1,214 @@
+"""The learned ranking path on the GPU, through the C ABI, against the CPU oracle.
+
+- features: every one of the 16 against oracle/surrogate.py (FP32 logs,
+  so 1e-5 relative);
+- exact EF of chosen nodes: N, S and t exactly, EF within the parity bars,
+  against the vertex-centric oracle;
+- the network: forward pass and gradients (BF16 operands, FP32
+  accumulation) against the FP64 oracle.  The bars come from BF16's 8-bit
+  significand: relative error per product about 2^-9, so a few 1e-3 on a
+  64-term sum, and 3e-2 relative on the gradient of each weight block,
+  far below the O(1) error of a transposed or misplaced operand;
+- training lowers the loss, and save/load round-trips;
+- ranking: the trained network's top set reaches 0.95 recall of the exact
+  top 1% while computing exact EF for a few percent of the nodes, and it
+  beats the same network untrained and the ranking by degree.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import surrogate as sg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2306_00606_gb300 as ef
+    c = ef.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _features(ctx, g, mode):
+    import torch
+    import paper_2306_00606_gb300 as ef
+    x = torch.empty((g.n, 16), dtype=torch.float32, device="cuda")
+    ef.ef_features(ctx.handle, _dev(g.row_ptr), _dev(g.col_idx), x, mode=mode)
+    torch.cuda.synchronize()
+    return x
+
+
+def _exact_all(ctx, g, precision="fp32c"):
+    import torch
+    out = ctx.compute(_dev(g.row_ptr), _dev(g.col_idx), precision=precision, outputs=("ef",))
+    torch.cuda.synchronize()
+    return out["ef"].cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_features_match_oracle(ctx, mode):
+    g = synth.disjoint_union([synth.barabasi_albert(3000, 4, 41), synth.powerlaw_cm(4000, 2.2, 2, 900, 42),
+                              synth.complete(12), synth.star(50), synth.path(2)])
+    got = _features(ctx, g, mode).cpu().numpy()
+    ref = sg.features(g, triangles=oracle.triangles(g) if mode == 1 else None)
+    np.testing.assert_allclose(got, ref, rtol=1e-5, atol=2e-5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_nodes_exact_matches_oracle(ctx, precision):
+    import torch
+    import paper_2306_00606_gb300 as ef
+    g = synth.powerlaw_cm(30000, 2.1, 2, 6000, 43)
+    deg = np.diff(g.row_ptr)
+    rng = np.random.default_rng(1)
+    nodes = np.concatenate([np.argsort(-deg)[:40], rng.choice(g.n, 300, replace=False), [0, 0]]).astype(np.int32)
+    out = {k: torch.empty(len(nodes), dtype=dt, device="cuda") for k, dt in
+           (("ef", torch.float64), ("n_clusters", torch.int64), ("s", torch.int64), ("triangles", torch.int64))}
+    ef.ef_compute_nodes(ctx.handle, _dev(g.row_ptr), _dev(g.col_idx), _dev(nodes), precision=precision, **out)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    ref = oracle.vertex(g, nodes)
+    np.testing.assert_array_equal(got["n_clusters"], ref["N"])
+    np.testing.assert_array_equal(got["s"], ref["S"])
+    np.testing.assert_array_equal(got["triangles"], ref["t"])
+    if precision == "fp64":
+        np.testing.assert_allclose(got["ef"], ref["EF"], rtol=1e-9, atol=1e-12)
+    else:
+        np.testing.assert_allclose(got["ef"], ref["EF"], rtol=0, atol=2e-5)
+    with pytest.raises(ef.EfError) as ei:
+        ef.ef_compute_nodes(ctx.handle, _dev(g.row_ptr), _dev(g.col_idx), _dev(np.array([5, g.n], np.int32)),
+                            ef=torch.empty(2, dtype=torch.float64, device="cuda"))
+    assert ei.value.code == ef.EF_ERR_ARG
+
+
+def _random_model(ctx, seed, X):
+    import paper_2306_00606_gb300 as ef
+    rng = np.random.default_rng(seed)
+    p = sg.init_params(seed, mean=X.mean(axis=0), std=X.std(axis=0) + 0.5)
+    p["b1"] = rng.normal(size=64) * 0.2
+    p["b2"] = rng.normal(size=64) * 0.2
+    p["b3"] = 0.4
+    m = ef.Model(ctx.handle)
+    m.set(np.concatenate([sg.flatten(p), p["mean"], p["std"]]).astype(np.float32))
+    # the oracle takes the parameters the device holds (rounded to float32)
+    flat = m.get().astype(np.float64)
+    return m, sg.unflatten(flat[:sg.N_PARAMS], flat[sg.N_PARAMS:sg.N_PARAMS + 16], flat[sg.N_PARAMS + 16:])
+
+
+def test_network_forward_matches_oracle(ctx):
+    import torch
+    g = synth.barabasi_albert(5000, 5, 44)
+    x = _features(ctx, g, 0)
+    X = x.cpu().numpy().astype(np.float64)
+    m, p = _random_model(ctx, 3, X)
+    out = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    m.forward(x, out)
+    got = out.cpu().numpy()
+    ref, _ = sg.forward(p, X)
+    scale = np.abs(ref).mean() + np.abs(ref).std()
+    assert np.abs(got - ref).max() <= 2e-2 * scale, (np.abs(got - ref).max(), scale)
+
+
+def test_network_gradients_match_oracle(ctx):
+    g = synth.barabasi_albert(3000, 5, 45)
+    x = _features(ctx, g, 0)
+    X = x.cpu().numpy().astype(np.float64)
+    y = oracle.alg1(g)["EF"]
+    m, p = _random_model(ctx, 4, X)
+    loss, grad = m.grad(x, _dev(y.astype(np.float32)))
+    ref_loss, ref_g = sg.loss_and_grads(p, X, y)
+    assert abs(loss - ref_loss) <= 1e-2 * ref_loss
+    gf = sg.flatten(ref_g)
+    o = 0
+    for k in sg.TRAINED:
+        size = int(np.prod(sg.SHAPES[k]))
+        a, b = grad[o:o + size].astype(np.float64), gf[o:o + size]
+        err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+        assert err <= 3e-2, (k, err)
+        o += size
+
+
+def _training_set(ctx):
+    """Exact EF on graphs shaped like the small workloads (ER 2000, BA), as labels."""
+    import torch
+    gs = [synth.workload(1), synth.barabasi_albert(60000, 5, 46), synth.barabasi_albert(30000, 4, 47)]
+    xs, ys = [], []
+    for g in gs:
+        xs.append(_features(ctx, g, 0))
+        ys.append(_dev(_exact_all(ctx, g).astype(np.float32)))
+    return torch.cat(xs), torch.cat(ys)
+
+
+@pytest.fixture(scope="module")
+def trained(ctx):
+    import paper_2306_00606_gb300 as ef
+    x, y = _training_set(ctx)
+    m = ef.Model(ctx.handle, seed=5)
+    st = m.train(x, y, steps=1500, batch=4096, lr=2e-3, seed=9)
+    return m, st, x, y
+
+
+def test_training_lowers_the_loss(trained):
+    m, st, x, y = trained
+    assert st["last_loss"] < 0.05 * st["first_loss"], st
+
+
+def test_model_save_load_roundtrip(ctx, trained, tmp_path):
+    import torch
+    import paper_2306_00606_gb300 as ef
+    m, _, x, _ = trained
+    path = tmp_path / "model.bin"
+    m.save(str(path))
+    m2 = ef.Model.load(ctx.handle, str(path))
+    a = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    m.forward(x, a)
+    m2.forward(x, b)
+    assert torch.equal(a, b) and np.array_equal(m.get(), m2.get())
+
+
+def _rank(ctx, model, g, cand_frac):
+    import torch
+    kt = math.ceil(0.01 * g.n)
+    idx = torch.empty(kt, dtype=torch.int32, device="cuda")
+    efv = torch.empty(kt, dtype=torch.float64, device="cuda")
+    score = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    st = model.rank(_dev(g.row_ptr), _dev(g.col_idx), idx, efv, top_frac=0.01, cand_frac=cand_frac,
+                    audit_frac=0.01, seed=3, out_score=score)
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), efv.cpu().numpy(), score.cpu().numpy(), st
+
+
+def test_ranking_recall_and_what_the_network_gains(ctx, trained):
+    import paper_2306_00606_gb300 as ef
+    model = trained[0]
+    g = synth.barabasi_albert(200000, 4, 48)   # not seen in training
+    exact = _exact_all(ctx, g)
+    truth = set(sg.top_set(exact, 0.01).tolist())
+    idx, efv, score, st = _rank(ctx, model, g, cand_frac=0.03)
+    # the reported EF values are the exact ones, and the set is the top of the candidates
+    np.testing.assert_allclose(efv, exact[idx], rtol=0, atol=2e-5)
+    recall = len(truth & set(idx.tolist())) / len(truth)
+    assert recall >= 0.95, (recall, st)
+    assert st["n_candidates"] == math.ceil(0.03 * g.n) and st["spearman_audit"] > 0.9
+    # without the trained network: the same network untrained, and ranking by degree
+    raw = ef.Model(ctx.handle, seed=5)
+    raw.set(np.concatenate([sg.flatten(sg.init_params(5)), model.get()[sg.N_PARAMS:]]).astype(np.float32))
+    idx_raw, _, _, _ = _rank(ctx, raw, g, cand_frac=0.03)
+    recall_raw = len(truth & set(idx_raw.tolist())) / len(truth)
+    deg = np.diff(g.row_ptr).astype(np.float64)
+    cand_deg = sg.top_set(deg, 0.03)
+    top_deg = cand_deg[np.lexsort((cand_deg, -exact[cand_deg]))][:len(truth)]
+    recall_deg = len(truth & set(top_deg.tolist())) / len(truth)
+    print(f"top-1% recall: trained {recall:.4f}, untrained {recall_raw:.4f}, degree {recall_deg:.4f}")
+    assert recall > recall_raw and recall >= recall_deg - 0.01, (recall, recall_raw, recall_deg)
