@@ -280,6 +280,8 @@ typedef struct {
     double spearman_audit;  /* Spearman rho of prediction vs exact EF on the audit sample */
     double max_abs_err_audit;
     double features_ms, infer_ms, select_ms, exact_ms, total_ms;
+    double exact_tri_ms;    /* of exact_ms: the triangle pass */
+    double exact_wedge_ms;  /* of exact_ms: marking, bins and the wedge pass */
 } ef_rank_stats;
 
 /*

@@ -81,7 +81,8 @@ class ef_rank_stats(ctypes.Structure):
     _fields_ = [("n_candidates", ctypes.c_int32), ("n_audit", ctypes.c_int32), ("n_top", ctypes.c_int32),
                 ("pad", ctypes.c_int32), ("spearman_audit", ctypes.c_double), ("max_abs_err_audit", ctypes.c_double),
                 ("features_ms", ctypes.c_double), ("infer_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
-                ("exact_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+                ("exact_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("exact_tri_ms", ctypes.c_double),
+                ("exact_wedge_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}

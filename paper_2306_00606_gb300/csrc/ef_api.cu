@@ -67,7 +67,7 @@ struct ef_ctx {
     size_t io_bytes = 0;
     int64_t *goff = nullptr;         // device copy of the batch offsets
     size_t goff_bytes = 0;
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[10] = {};   // 0-7 pass timings; 8, 9 the exact part of a ranking
     ef_stats stats = {};
     ef::Tune tune;
     cudaGraphExec_t gexec = nullptr;
@@ -500,14 +500,18 @@ int rank_buffers(ef_ctx *ctx, int32_t n, ef::RankScratch &r) {
     return EF_OK;
 }
 
-// Features of every node into x (after prepare_graph).
+// Features of every node into x (after prepare_graph).  with_orient: take
+// omega and the neighbour degree range from the orientation pass (which a
+// ranking needs anyway for its triangles) instead of the lighter omega pass.
 int features_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, int mode,
-                    const ef::Scratch &s, ef::RankScratch r, float *x) {
+                    const ef::Scratch &s, ef::RankScratch r, float *x, bool with_orient = false) {
     using namespace ef;
     cudaStream_t st = ctx->stream;
-    LAUNCH(launch_omega_mm(rp, ci, n, m, s, r, ctx->tune, st), "omega");
+    if (with_orient || mode == 1)
+        LAUNCH(launch_orient(rp, ci, n, m, s, ctx->tune, st, r.nbr_min, r.nbr_max), "orientation");
+    else
+        LAUNCH(launch_omega_mm(rp, ci, n, m, s, r, ctx->tune, st), "omega");
     if (mode == 1) {
-        LAUNCH(launch_orient(rp, ci, n, m, s, ctx->tune, st), "orientation");
         LAUNCH(launch_out_hash(s, n, m, ctx->tune, st), "out-list hash");
         LAUNCH(launch_tri_pairs(s, n, m, ctx->tune, st), "triangle");
     }
@@ -517,15 +521,29 @@ int features_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n
 }
 
 // Exact EF of list[0..k) (k on the device when kptr is given): the wedge
-// kernels over bins of the listed nodes, then a CTA per listed node.
+// kernels over bins of the listed nodes and their neighbours, then a CTA per
+// listed node.  Triangles: per listed node (few nodes), or (global_tri) the
+// full oriented triangle pass, which costs less once the list holds the
+// high-EF nodes next to the hubs; orient_done / tri_done: the features
+// already ran the orientation / the whole triangle pass.
 int nodes_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const ef::Scratch &s,
-                 const int32_t *list, int32_t kmax, const int32_t *kptr, int precision, const ef_outputs &out) {
+                 const int32_t *list, int32_t kmax, const int32_t *kptr, int precision, bool global_tri,
+                 bool orient_done, bool tri_done, const ef_outputs &out, bool timed = false) {
     using namespace ef;
     cudaStream_t st = ctx->stream;
-    LAUNCH(launch_bin_nodes(list, kmax, kptr, s, n, ctx->tune.hub_min, st), "node bins");
+    if (global_tri && !tri_done) {
+        if (!orient_done) LAUNCH(launch_orient(rp, ci, n, m, s, ctx->tune, st), "orientation");
+        LAUNCH(launch_out_hash(s, n, m, ctx->tune, st), "out-list hash");
+        LAUNCH(launch_tri_pairs(s, n, m, ctx->tune, st), "triangle");
+    }
+    if (timed) CU(cudaEventRecord(ctx->ev[8], st));
+    // the row passes' out-degrees are not needed any more: they hold the marks
+    LAUNCH(launch_bin_nodes(list, kmax, kptr, rp, ci, s, s.outdeg, n, ctx->tune, st), "node bins");
     LAUNCH(launch_wedge_small(rp, ci, s, precision, n, ctx->tune, st), "small wedge");
     LAUNCH(launch_wedge_big(rp, ci, s, precision, 0, n, m, ctx->tune, st), "big wedge");
-    LAUNCH(launch_nodes_exact(rp, ci, s, list, kmax, kptr, n, precision, out, ctx->tune, st), "node exact");
+    if (timed) CU(cudaEventRecord(ctx->ev[9], st));
+    LAUNCH(launch_nodes_exact(rp, ci, s, list, kmax, kptr, n, precision, global_tri, out, ctx->tune, st),
+           "node exact");
     return EF_OK;
 }
 
@@ -662,7 +680,7 @@ int ef_ctx_create(int device, void *stream, ef_ctx **out) {
     ctx->tune.num_sms = ctx->num_sms;
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counters, ef::NUM_COUNTERS * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
-    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+    for (int i = 0; i < 10 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
     if (e == cudaSuccess && ef::prepare_kernels()) e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_err(nullptr, "context set-up failed: %s", cudaGetErrorString(e));
@@ -686,7 +704,7 @@ int ef_ctx_destroy(ef_ctx *ctx) {
     cudaFree(ctx->acts);
     cudaFree(ctx->dtmp);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 10; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     if (ctx->capture) cudaStreamDestroy(ctx->capture);
     delete ctx;
@@ -853,7 +871,8 @@ int ef_compute_nodes(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const i
     if (rc) return rc;
     ef::RankScratch r = {};
     LAUNCH(ef::launch_omega_mm(g->row_ptr, g->col_idx, n, m, s, r, ctx->tune, ctx->stream), "omega");
-    rc = nodes_device(ctx, g->row_ptr, g->col_idx, n, m, s, nodes, k, nullptr, o.precision, *out);
+    rc = nodes_device(ctx, g->row_ptr, g->col_idx, n, m, s, nodes, k, nullptr, o.precision, false, false, false,
+                      *out);
     if (rc) return rc;
     return final_check(ctx, s, !o.trust_input);
 }
@@ -1115,7 +1134,7 @@ int ef_surrogate_rank(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const 
     RankScratch r;
     rc = rank_buffers(ctx, n, r);
     if (rc) return rc;
-    rc = features_device(ctx, g->row_ptr, g->col_idx, n, m, model->feature_mode, s, r, r.x);
+    rc = features_device(ctx, g->row_ptr, g->col_idx, n, m, model->feature_mode, s, r, r.x, true);
     if (rc) return rc;
     CU(cudaEventRecord(ctx->ev[1], st));
     LAUNCH(launch_mlp_infer(model->d, r.x, n, r.score, ctx->num_sms, st), "network");
@@ -1123,7 +1142,7 @@ int ef_surrogate_rank(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const 
     CU(cudaEventRecord(ctx->ev[2], st));
     // candidates, audit sample, their union
     LAUNCH(launch_keys_score(r.score, n, r.key, st), "keys");
-    LAUNCH(launch_select_top(r, n, kc, ctx->tune, st), "candidate selection");
+    LAUNCH(launch_select_top(r, n, kc, 32, ctx->tune, st), "candidate selection");
     const double thr = std::ldexp((double)audit_frac, 64);
     const uint64_t threshold = audit_frac >= 1.f ? ~0ull : (uint64_t)thr;
     LAUNCH(launch_roles(r.list, kc, n, seed, threshold, r.role, st), "roles");
@@ -1132,13 +1151,14 @@ int ef_surrogate_rank(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const 
     CU(cudaEventRecord(ctx->ev[3], st));
     ef_outputs eo = {};
     eo.ef = r.exact;
-    rc = nodes_device(ctx, g->row_ptr, g->col_idx, n, m, s, r.listL, n, kL, o.precision, eo);
+    rc = nodes_device(ctx, g->row_ptr, g->col_idx, n, m, s, r.listL, n, kL, o.precision, true, true,
+                      model->feature_mode == 1, eo, stats != nullptr);
     if (rc) return rc;
     CU(cudaEventRecord(ctx->ev[4], st));
     // the reported top set: largest exact EF among the candidates
     CU(cudaMemsetAsync(r.key, 0, sizeof(uint64_t) * n, st));
     LAUNCH(launch_exact_keys(r.listL, kL, n, r.exact, r.role, r.exact_node, r.key, st), "exact keys");
-    LAUNCH(launch_select_top(r, n, kt, ctx->tune, st), "top selection");
+    LAUNCH(launch_select_top(r, n, kt, 64, ctx->tune, st), "top selection");
     LAUNCH(launch_gather_top(r.list, kt, r.exact_node, out_idx, out_ef, st), "top set");
     // audit sample: predictions against exact EF
     LAUNCH(launch_compact_role(r.role, n, 2, r.flag, r.pos, r.scan_tmp, r.lista, st), "audit listing");
@@ -1173,6 +1193,11 @@ int ef_surrogate_rank(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const 
         stats->select_ms = t[2];
         stats->exact_ms = t[3];
         stats->total_ms = t[4];
+        float a = 0.f, b = 0.f;
+        CU(cudaEventElapsedTime(&a, ctx->ev[3], ctx->ev[8]));
+        CU(cudaEventElapsedTime(&b, ctx->ev[8], ctx->ev[9]));
+        stats->exact_tri_ms = a;
+        stats->exact_wedge_ms = b;
     }
     return EF_OK;
 }

@@ -279,7 +279,7 @@ namespace ef {
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
                   cudaStream_t st);
 int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
-                  cudaStream_t st);
+                  cudaStream_t st, int32_t *nmin = nullptr, int32_t *nmax = nullptr);
 int launch_big_items(const Scratch &s, int32_t n, cudaStream_t st);
 int launch_batch_check(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const int64_t *goff, int32_t G,
                        const Scratch &s, const Tune &t, cudaStream_t st);
@@ -304,12 +304,12 @@ int launch_feature_stats(const float *x, int32_t n, ModelDev *M, double *tmp, cu
 int launch_omega_mm(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s,
                     const RankScratch &r, const Tune &t, cudaStream_t st);
 int launch_features(const Scratch &s, const RankScratch &r, int32_t n, int mode, const Tune &t, cudaStream_t st);
-int launch_select_top(const RankScratch &r, int32_t n, int64_t k, const Tune &t, cudaStream_t st);
-int launch_bin_nodes(const int32_t *list, int32_t k, const int32_t *kptr, const Scratch &s, int32_t n, int hub_min,
-                     cudaStream_t st);
+int launch_select_top(const RankScratch &r, int32_t n, int64_t k, int bits, const Tune &t, cudaStream_t st);
+int launch_bin_nodes(const int32_t *list, int32_t k, const int32_t *kptr, const int32_t *rp, const int32_t *ci,
+                     const Scratch &s, int32_t *mark, int32_t n, const Tune &t, cudaStream_t st);
 int launch_nodes_exact(const int32_t *rp, const int32_t *ci, const Scratch &s, const int32_t *list, int32_t k,
-                       const int32_t *kptr, int32_t n, int precision, const ef_outputs &out, const Tune &t,
-                       cudaStream_t st);
+                       const int32_t *kptr, int32_t n, int precision, bool global_tri, const ef_outputs &out,
+                       const Tune &t, cudaStream_t st);
 int launch_keys_score(const float *score, int32_t n, uint64_t *key, cudaStream_t st);
 int launch_roles(const int32_t *cand, int32_t kc, int32_t n, uint64_t seed, uint64_t threshold, int32_t *role,
                  cudaStream_t st);

@@ -43,23 +43,31 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// The model as one CTA holds it in shared memory.
+// The model as one CTA holds it in shared memory.  Weight rows are padded
+// (16 -> 24 and 64 -> 72 elements) so that the eight row groups of a
+// fragment load fall in different banks (unpadded, 64-element rows put them
+// all in one bank: an 8-way conflict that made inference bound by shared
+// memory).
+constexpr int W1S = 24, W2S = 72;
+
 struct MlpSmem {
-    __align__(16) uint16_t w1t[MLP_H * MLP_F];
-    __align__(16) uint16_t w2t[MLP_H * MLP_H];
-    __align__(16) uint16_t w2r[MLP_H * MLP_H];
+    __align__(16) uint16_t w1t[MLP_H * W1S];
+    __align__(16) uint16_t w2t[MLP_H * W2S];
+    __align__(16) uint16_t w2r[MLP_H * W2S];
     float b1[MLP_H], b2[MLP_H], w3[MLP_H], mean[MLP_F], istd[MLP_F];
     float b3;
 };
 
 __device__ void load_model(const ModelDev *M, MlpSmem &s, bool with_w2r) {
+    // 16-byte chunks: 2 per W1 row, 8 per W2 row
     const uint4 *src1 = reinterpret_cast<const uint4 *>(M->w1t);
     const uint4 *src2 = reinterpret_cast<const uint4 *>(M->w2t);
     const uint4 *src3 = reinterpret_cast<const uint4 *>(M->w2r);
-    for (int i = threadIdx.x; i < MLP_H * MLP_F / 8; i += blockDim.x) reinterpret_cast<uint4 *>(s.w1t)[i] = src1[i];
-    for (int i = threadIdx.x; i < MLP_H * MLP_H / 8; i += blockDim.x) {
-        reinterpret_cast<uint4 *>(s.w2t)[i] = src2[i];
-        if (with_w2r) reinterpret_cast<uint4 *>(s.w2r)[i] = src3[i];
+    for (int i = threadIdx.x; i < MLP_H * 2; i += blockDim.x)
+        reinterpret_cast<uint4 *>(s.w1t + (i >> 1) * W1S)[i & 1] = src1[i];
+    for (int i = threadIdx.x; i < MLP_H * 8; i += blockDim.x) {
+        reinterpret_cast<uint4 *>(s.w2t + (i >> 3) * W2S)[i & 7] = src2[i];
+        if (with_w2r) reinterpret_cast<uint4 *>(s.w2r + (i >> 3) * W2S)[i & 7] = src3[i];
     }
     for (int i = threadIdx.x; i < MLP_H; i += blockDim.x) {
         s.b1[i] = M->p[P_B1 + i];
@@ -82,15 +90,36 @@ struct Tile {
     float p0, p1;         // predictions of rows g and g+8 (all four lanes of a group)
 };
 
+// The four features a thread needs of one row (2t, 2t+1, 2t+8, 2t+9).
+struct RowPart {
+    float2 lo, hi;
+};
+
+__device__ __forceinline__ RowPart load_row(const float *x) {
+    const int t = threadIdx.x & 3;
+    if (!x) return RowPart{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    return RowPart{__ldg(reinterpret_cast<const float2 *>(x + 2 * t)),
+                   __ldg(reinterpret_cast<const float2 *>(x + 2 * t + 8))};
+}
+
+__device__ __forceinline__ void tile_forward(const MlpSmem &s, RowPart rg, RowPart rg8, bool vg, bool vg8, Tile &T);
+
 __device__ __forceinline__ void tile_forward(const MlpSmem &s, const float *xg, const float *xg8, Tile &T) {
+    tile_forward(s, load_row(xg), load_row(xg8), xg != nullptr, xg8 != nullptr, T);
+}
+
+__device__ __forceinline__ void tile_forward(const MlpSmem &s, RowPart rg, RowPart rg8, bool vg, bool vg8, Tile &T) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int f0 = 2 * t, f1 = 2 * t + 8;
     float z[2][4];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
-        const float *x = rr ? xg8 : xg;
-        const int f[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) z[rr][q] = x ? (x[f[q]] - s.mean[f[q]]) * s.istd[f[q]] : 0.0f;
+        const RowPart &p = rr ? rg8 : rg;
+        const bool v = rr ? vg8 : vg;
+        z[rr][0] = v ? (p.lo.x - s.mean[f0]) * s.istd[f0] : 0.f;
+        z[rr][1] = v ? (p.lo.y - s.mean[f0 + 1]) * s.istd[f0 + 1] : 0.f;
+        z[rr][2] = v ? (p.hi.x - s.mean[f1]) * s.istd[f1] : 0.f;
+        z[rr][3] = v ? (p.hi.y - s.mean[f1 + 1]) * s.istd[f1 + 1] : 0.f;
     }
     T.a1[0] = pack_bf16(z[0][0], z[0][1]);
     T.a1[1] = pack_bf16(z[1][0], z[1][1]);
@@ -100,8 +129,8 @@ __device__ __forceinline__ void tile_forward(const MlpSmem &s, const float *xg, 
     for (int j = 0; j < 8; ++j) {
         const int n = 8 * j + g;
         float c[4] = {0.f, 0.f, 0.f, 0.f};
-        mma16816(c, T.a1, *reinterpret_cast<const uint32_t *>(&s.w1t[n * MLP_F + 2 * t]),
-                 *reinterpret_cast<const uint32_t *>(&s.w1t[n * MLP_F + 2 * t + 8]));
+        mma16816(c, T.a1, *reinterpret_cast<const uint32_t *>(&s.w1t[n * W1S + 2 * t]),
+                 *reinterpret_cast<const uint32_t *>(&s.w1t[n * W1S + 2 * t + 8]));
         const float bb0 = s.b1[8 * j + 2 * t], bb1 = s.b1[8 * j + 2 * t + 1];
         T.h1[j][0] = fmaxf(c[0] + bb0, 0.f);
         T.h1[j][1] = fmaxf(c[1] + bb1, 0.f);
@@ -118,8 +147,8 @@ __device__ __forceinline__ void tile_forward(const MlpSmem &s, const float *xg, 
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int n = 8 * j + g;
-            mma16816(T.h2[j], a, *reinterpret_cast<const uint32_t *>(&s.w2t[n * MLP_H + 16 * kc + 2 * t]),
-                     *reinterpret_cast<const uint32_t *>(&s.w2t[n * MLP_H + 16 * kc + 2 * t + 8]));
+            mma16816(T.h2[j], a, *reinterpret_cast<const uint32_t *>(&s.w2t[n * W2S + 16 * kc + 2 * t]),
+                     *reinterpret_cast<const uint32_t *>(&s.w2t[n * W2S + 16 * kc + 2 * t + 8]));
         }
     }
     float p0 = 0.f, p1 = 0.f;
@@ -144,7 +173,7 @@ __device__ __forceinline__ void tile_forward(const MlpSmem &s, const float *xg, 
 
 constexpr int MLP_WARPS = 8;
 
-__global__ void __launch_bounds__(MLP_WARPS * 32) k_mlp_infer(const ModelDev *__restrict__ M,
+__global__ void __launch_bounds__(MLP_WARPS * 32, 4) k_mlp_infer(const ModelDev *__restrict__ M,
                                                               const float *__restrict__ X, int32_t n,
                                                               float *__restrict__ out) {
     __shared__ MlpSmem s;
@@ -152,10 +181,21 @@ __global__ void __launch_bounds__(MLP_WARPS * 32) k_mlp_infer(const ModelDev *__
     __syncthreads();
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
     const int64_t tiles = ((int64_t)n + 15) / 16;
-    for (int64_t tile = (int64_t)blockIdx.x * MLP_WARPS + w; tile < tiles; tile += (int64_t)gridDim.x * MLP_WARPS) {
+    const int64_t step = (int64_t)gridDim.x * MLP_WARPS;
+    auto row = [&](int64_t r) { return r < n ? X + r * MLP_F : nullptr; };
+    int64_t tile = (int64_t)blockIdx.x * MLP_WARPS + w;
+    // the next tile's rows are loaded before the current tile is computed
+    RowPart a = load_row(row(tile * 16 + g)), b = load_row(row(tile * 16 + g + 8));
+    for (; tile < tiles; tile += step) {
         const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        const RowPart ca = a, cb = b;
+        const int64_t nx = tile + step;
+        if (nx < tiles) {
+            a = load_row(row(nx * 16 + g));
+            b = load_row(row(nx * 16 + g + 8));
+        }
         Tile T;
-        tile_forward(s, r0 < n ? X + r0 * MLP_F : nullptr, r1 < n ? X + r1 * MLP_F : nullptr, T);
+        tile_forward(s, ca, cb, r0 < n, r1 < n, T);
         if (t == 0) {
             if (r0 < n) out[r0] = T.p0;
             if (r1 < n) out[r1] = T.p1;
@@ -251,8 +291,8 @@ __global__ void __launch_bounds__(MLP_WARPS * 32) k_mlp_fwd_bwd(ModelDev *M, con
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int nn = 8 * j + g;
-                mma16816(e1v[j], a, *reinterpret_cast<const uint32_t *>(&s.w2r[nn * MLP_H + 16 * kc + 2 * t]),
-                         *reinterpret_cast<const uint32_t *>(&s.w2r[nn * MLP_H + 16 * kc + 2 * t + 8]));
+                mma16816(e1v[j], a, *reinterpret_cast<const uint32_t *>(&s.w2r[nn * W2S + 16 * kc + 2 * t]),
+                         *reinterpret_cast<const uint32_t *>(&s.w2r[nn * W2S + 16 * kc + 2 * t + 8]));
             }
         }
 #pragma unroll

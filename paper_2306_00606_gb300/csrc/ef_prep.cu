@@ -33,6 +33,24 @@ __device__ __forceinline__ T block_sum(T v, T *s_buf) {
     return r;
 }
 
+__device__ __forceinline__ int64_t block_max_i64(int64_t v, int64_t *s_buf) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, (int64_t)__shfl_xor_sync(FULL, (long long)v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) s_buf[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int64_t t = lane < (int)(blockDim.x >> 5) ? s_buf[lane] : INT64_MIN;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = max(t, (int64_t)__shfl_xor_sync(FULL, (long long)t, o));
+        if (lane == 0) s_buf[0] = t;
+    }
+    __syncthreads();
+    const int64_t r = s_buf[0];
+    __syncthreads();
+    return r;
+}
+
 // Block-wide exclusive scan of one int per thread (all threads must call).
 __device__ __forceinline__ int block_exclusive_scan(int x, int *total = nullptr) {
     __shared__ int s_w[33];
@@ -289,6 +307,7 @@ struct Orient {
     const int4 *info;   // per node {D, sigma1, out_ptr, out_ptr next}
     int32_t *out_col, *out_D, *out_src;
     int2 *out_rng;
+    int32_t *nmin, *nmax;   // optional: smallest / largest neighbour degree (node features)
     int32_t n;
     __device__ __forceinline__ int4 node(int x) const {
         return x >= 0 && x < n ? __ldg(info + x) : make_int4(0, 0, 0, 0);
@@ -309,6 +328,7 @@ struct Orient {
     // together); returns omega_v.
     __device__ __forceinline__ int64_t row(int v, int Dv, int a, int b, int k) const {
         int64_t om = 0;
+        int mn = 0x7fffffff, mx = 0;
         for (int e0 = a; e0 < b; e0 += 4) {
             int x[4];
             int4 nf[4];
@@ -319,8 +339,16 @@ struct Orient {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 om += nf[q].y;
-                if (x[q] >= 0 && x[q] < n && rank_less(Dv, v, nf[q].x, x[q])) put(k++, v, x[q], nf[q]);
+                if (x[q] >= 0 && x[q] < n) {
+                    mn = min(mn, nf[q].x);
+                    mx = max(mx, nf[q].x);
+                    if (rank_less(Dv, v, nf[q].x, x[q])) put(k++, v, x[q], nf[q]);
+                }
             }
+        }
+        if (nmin) {
+            nmin[v] = mx ? mn : 0;
+            nmax[v] = mx;
         }
         return om;
     }
@@ -354,17 +382,30 @@ __global__ void k_orient(const int32_t *__restrict__ rp, int32_t n, int64_t m, i
             const int ua = __shfl_sync(FULL, a, j), ub = __shfl_sync(FULL, b, j);
             int k0 = out_ptr[u];
             int64_t om = 0;
+            int mn = 0x7fffffff, mx = 0;
             for (int e0 = ua; e0 < ub; e0 += 32) {
                 const int e = e0 + lane;
                 int x = 0;
                 int4 nf = make_int4(0, 0, 0, 0);
                 const bool isout = e < ub && o.probe(u, ub - ua, e, x, nf, om);
+                if (e < ub && x >= 0 && x < n) {
+                    mn = min(mn, nf.x);
+                    mx = max(mx, nf.x);
+                }
                 const unsigned bal = __ballot_sync(FULL, isout);
                 if (isout) o.put(k0 + __popc(bal & ((1u << lane) - 1u)), u, x, nf);
                 k0 += __popc(bal);
             }
             om = warp_sum(om);
-            if (lane == 0) omega[u] = om;
+            mn = __reduce_min_sync(FULL, mn);
+            mx = __reduce_max_sync(FULL, mx);
+            if (lane == 0) {
+                omega[u] = om;
+                if (o.nmin) {
+                    o.nmin[u] = mx ? mn : 0;
+                    o.nmax[u] = mx;
+                }
+            }
         }
     }
 }
@@ -381,18 +422,34 @@ __global__ void __launch_bounds__(ROW_CTA) k_orient_hub(const int32_t *__restric
         const int a = rp[u], b = rp[u + 1];
         int k0 = out_ptr[u];
         int64_t om = 0;
+        int64_t mn = 0x7fffffff, mx = 0;
         for (int e0 = a; e0 < b; e0 += ROW_CTA) {
             const int e = e0 + threadIdx.x;
             int x = 0;
             int4 nf = make_int4(0, 0, 0, 0);
             const bool isout = e < b && o.probe(u, b - a, e, x, nf, om);
+            if (e < b && x >= 0 && x < n) {
+                mn = min(mn, (int64_t)nf.x);
+                mx = max(mx, (int64_t)nf.x);
+            }
             int tot;
             const int off = block_exclusive_scan(isout ? 1 : 0, &tot);
             if (isout) o.put(k0 + off, u, x, nf);
             k0 += tot;
         }
         om = block_sum<int64_t>(om, s_buf);
-        if (threadIdx.x == 0) omega[u] = om;
+        if (o.nmin) {
+            // min and max through the sum reduction: -max(-x), max(x)
+            mx = block_max_i64(mx, s_buf);
+            mn = -block_max_i64(-mn, s_buf);
+        }
+        if (threadIdx.x == 0) {
+            omega[u] = om;
+            if (o.nmin) {
+                o.nmin[u] = mx ? (int32_t)mn : 0;
+                o.nmax[u] = (int32_t)mx;
+            }
+        }
     }
 }
 
@@ -524,10 +581,10 @@ int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
 
 // Oriented CSR and omega.
 int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
-                  cudaStream_t st) {
+                  cudaStream_t st, int32_t *nmin, int32_t *nmax) {
     if (launch_scan(s.outdeg, s.out_ptr, n, s.scan_tmp, st)) return -1;
     k_node_info<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.D, s.sig1, s.out_ptr, n, s.info);
-    const Orient o{ci, s.info, s.out_col, s.out_D, s.out_src, s.out_rng, n};
+    const Orient o{ci, s.info, s.out_col, s.out_D, s.out_src, s.out_rng, nmin, nmax, n};
     k_orient<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, n, m, t.row_thread_max, t.hub_min, o, s.out_ptr, s.omega);
     k_orient_hub<<<t.num_sms * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters, s.omega);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -6,13 +6,15 @@
 //
 // Exact EF of a chosen node v (T_v = middle + end + triangle parts, S_v and
 // N_v in closed form as in the full pass):
-// - middle: the wedge kernels run with work bins that hold only the chosen
-//   nodes, which gives Ccenter[v] (the degree-class kernels for large D_v);
-// - end: for every neighbour u and every j in N(u) other than v, one credit
-//   of open degree D_u + D_v + D_j - 4; a CTA per chosen node streams N(u);
-// - triangles: j in N(u) that is also in N(v) closes a triangle {v, u, j},
-//   found twice (through u and through j); each triangle brings the same
+// - middle and end: the wedge kernels of the full pass run with work bins
+//   that hold only the chosen nodes and their neighbours (every middle node
+//   whose clusters contain a chosen node), which gives Ccenter[v] and
+//   Tacc[v] exactly, at the degree-class cost of those middle nodes;
+// - triangles at v: per chosen node (k_nodes_final), each bringing the same
 //   fixed-point correction 4 (f(s-6) - f(s-4)) as in the full pass.
+// The chosen nodes of a ranking have the largest EF, which sit next to the
+// hubs: their neighbourhoods cover most middle nodes (60-67% of the nodes of
+// a BA graph for the top 1-2%), so this costs most of a wedge pass.
 #include "ef_internal.cuh"
 
 namespace ef {
@@ -188,10 +190,11 @@ int launch_features(const Scratch &s, const RankScratch &r, int32_t n, int mode,
 }
 
 // ------------------------------------------------------------- top-k select
-// The k largest of n 64-bit keys (key 0 = not eligible), found digit by
-// digit (four 16-bit passes), then compacted in index order; among keys
-// equal to the k-th largest the smallest indices are taken.  State in
-// sel[]: 0 prefix, 1 still needed, 2 k.
+// The k largest of n keys (key 0 = not eligible), found digit by digit from
+// the top (8-bit digits, histograms in shared memory, then one atomic per
+// bin per block), then compacted in index order; among keys equal to the
+// k-th largest the smallest indices are taken.  State in sel[]: 0 prefix,
+// 1 still needed, 2 k.
 __global__ void k_sel_init(uint64_t *sel, int64_t k) {
     sel[0] = 0;
     sel[1] = (uint64_t)k;
@@ -200,24 +203,29 @@ __global__ void k_sel_init(uint64_t *sel, int64_t k) {
 
 __global__ void k_sel_hist(const uint64_t *__restrict__ key, int32_t n, const uint64_t *__restrict__ sel, int shift,
                            int32_t *__restrict__ hist) {
+    __shared__ int32_t h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
     const uint64_t prefix = sel[0];
-    const int hs = shift + 16;
+    const int hs = shift + 8;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const uint64_t kk = key[v];
         if (kk == 0) continue;
         if (hs < 64 && (kk >> hs) != (prefix >> hs)) continue;
-        atomicAdd(hist + ((kk >> shift) & 0xffff), 1);
+        atomicAdd(&h[(kk >> shift) & 255], 1);
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(hist + i, h[i]);
 }
 
-// One CTA of 1024 threads: the digit d with (keys above d) < need <= (keys at
-// or above d); thread 0 covers the highest 64 digits.
-__global__ void __launch_bounds__(1024) k_sel_pick(const int32_t *__restrict__ hist, uint64_t *sel, int shift) {
-    __shared__ int64_t s_w[33];
+// 256 threads, thread i holding digit 255 - i: the digit d with (keys above
+// d) < need <= (keys at or above d).
+__global__ void __launch_bounds__(256) k_sel_pick(const int32_t *__restrict__ hist, uint64_t *sel, int shift) {
+    __shared__ int64_t s_w[8];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int hi = 65535 - 64 * tid;   // this thread's digits hi, hi-1, ..., hi-63
-    int64_t mine = 0;
-    for (int q = 0; q < 64; ++q) mine += hist[hi - q];
+    const int digit = 255 - tid;
+    const int64_t mine = hist[digit];
     int64_t inc = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -226,29 +234,14 @@ __global__ void __launch_bounds__(1024) k_sel_pick(const int32_t *__restrict__ h
     }
     if (lane == 31) s_w[w] = inc;
     __syncthreads();
-    if (w == 0) {
-        int64_t x = s_w[lane], xi = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(FULL, xi, o);
-            if (lane >= o) xi += y;
-        }
-        s_w[lane] = xi - x;
-    }
-    __syncthreads();
-    const int64_t above = s_w[w] + inc - mine;   // keys in higher digits than this thread's
+    int64_t before = 0;
+    for (int i = 0; i < w; ++i) before += s_w[i];
+    const int64_t above = before + inc - mine;   // keys in higher digits
     const int64_t need = (int64_t)sel[1];
+    __syncthreads();
     if (above < need && above + mine >= need) {
-        int64_t acc = above;
-        for (int q = 0; q < 64; ++q) {
-            const int64_t h = hist[hi - q];
-            if (acc + h >= need) {
-                sel[0] |= (uint64_t)(hi - q) << shift;
-                sel[1] = (uint64_t)(need - acc);
-                break;
-            }
-            acc += h;
-        }
+        sel[0] |= (uint64_t)digit << shift;
+        sel[1] = (uint64_t)(need - above);
     }
 }
 
@@ -277,15 +270,16 @@ __global__ void k_scatter(const int32_t *__restrict__ flag, const int32_t *__res
         if (flag[v]) list[pos[v]] = v;
 }
 
-// Selects the k largest keys of r.key into r.list[0..k) (index order).  The
-// caller guarantees 1 <= k <= number of nonzero keys.
-int launch_select_top(const RankScratch &r, int32_t n, int64_t k, const Tune &t, cudaStream_t st) {
+// Selects the k largest keys of r.key (keys `bits` wide: 32 or 64) into
+// r.list[0..k) (index order).  The caller guarantees 1 <= k <= number of
+// nonzero keys.
+int launch_select_top(const RankScratch &r, int32_t n, int64_t k, int bits, const Tune &t, cudaStream_t st) {
     const unsigned grid = t.grid((int64_t)n, 256);
     k_sel_init<<<1, 1, 0, st>>>(r.sel, k);
-    for (int shift = 48; shift >= 0; shift -= 16) {
-        if (cudaMemsetAsync(r.hist, 0, 65536 * sizeof(int32_t), st) != cudaSuccess) return -1;
+    for (int shift = bits - 8; shift >= 0; shift -= 8) {
+        if (cudaMemsetAsync(r.hist, 0, 256 * sizeof(int32_t), st) != cudaSuccess) return -1;
         k_sel_hist<<<grid, 256, 0, st>>>(r.key, n, r.sel, shift, r.hist);
-        k_sel_pick<<<1, 1024, 0, st>>>(r.hist, r.sel, shift);
+        k_sel_pick<<<1, 256, 0, st>>>(r.hist, r.sel, shift);
     }
     k_sel_ties<<<grid, 256, 0, st>>>(r.key, n, r.sel, r.flag);
     if (launch_scan(r.flag, r.pos, n, r.scan_tmp, st)) return -1;
@@ -296,112 +290,172 @@ int launch_select_top(const RankScratch &r, int32_t n, int64_t k, const Tune &t,
 }
 
 // ------------------------------------------------------ exact EF of nodes
-// Work bins holding only the listed nodes (as middle nodes of the wedge
-// kernels); node ids outside [0, n) set an error bit.
-__global__ void k_bin_nodes(const int32_t *__restrict__ list, int32_t k_max, const int32_t *__restrict__ kptr,
-                            const int32_t *__restrict__ D, int32_t n, int hub_min, int32_t *__restrict__ bins,
-                            int32_t *__restrict__ cnt) {
+// mark[x] = 1 for every listed node and every neighbour of one: the middle
+// nodes whose wedge credits reach a listed node.  Ids outside [0, n) set an
+// error bit.
+__global__ void k_mark_nbhd(const int32_t *__restrict__ list, int32_t k_max, const int32_t *__restrict__ kptr,
+                            const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n,
+                            int32_t *__restrict__ mark, int32_t *__restrict__ cnt) {
     const int k = kptr ? *kptr : k_max;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < k; i += nw) {   // a warp per listed node
         const int v = list[i];
         if (v < 0 || v >= n) {
-            atomicOr(cnt + CNT_ERR, ERRB_NODE);
+            if (lane == 0) atomicOr(cnt + CNT_ERR, ERRB_NODE);
             continue;
         }
-        const int d = D[v];
-        int b0 = -1, b1 = -1;
-        if (d >= 1 && d <= SMALL_MAX) {
-            b0 = d <= 4 ? BIN_S4 : d <= 8 ? BIN_S8 : d <= 16 ? BIN_S16 : BIN_S32;
-        } else if (d > SMALL_MAX) {
-            b0 = BIN_BIG;
-            b1 = d < hub_min ? BIN_MID : BIN_HUB0 + max(0, min(31 - __clz(d) - 9, NUM_HUB_BUCKETS - 1));
-        }
-        if (b0 >= 0) bins[(size_t)b0 * n + atomicAdd(cnt + b0, 1)] = v;
-        if (b1 >= 0) bins[(size_t)b1 * n + atomicAdd(cnt + b1, 1)] = v;
+        if (lane == 0) mark[v] = 1;
+        for (int e = rp[v] + lane; e < rp[v + 1]; e += 32) mark[ci[e]] = 1;
     }
 }
 
-int launch_bin_nodes(const int32_t *list, int32_t k, const int32_t *kptr, const Scratch &s, int32_t n, int hub_min,
-                     cudaStream_t st) {
+// Work bins holding only the marked nodes (as middle nodes of the wedge
+// kernels).  Counting per block in shared memory, one global atomic per bin
+// per block, so the bins keep the node order within a block.
+__global__ void k_bin_marked(const int32_t *__restrict__ mark, const int32_t *__restrict__ D, int32_t n, int hub_min,
+                             int32_t *__restrict__ bins, int32_t *__restrict__ cnt) {
+    __shared__ int s_cnt[NUM_BINS], s_base[NUM_BINS];
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        if (threadIdx.x < NUM_BINS) s_cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const int v = (int)(base + threadIdx.x);
+        int b0 = -1, b1 = -1, p0 = 0, p1 = 0;
+        if (v < n && mark[v]) {
+            const int d = D[v];
+            if (d >= 1 && d <= SMALL_MAX) {
+                b0 = d <= 4 ? BIN_S4 : d <= 8 ? BIN_S8 : d <= 16 ? BIN_S16 : BIN_S32;
+            } else if (d > SMALL_MAX) {
+                b0 = BIN_BIG;
+                b1 = d < hub_min ? BIN_MID : BIN_HUB0 + max(0, min(31 - __clz(d) - 9, NUM_HUB_BUCKETS - 1));
+            }
+        }
+        if (b0 >= 0) p0 = atomicAdd(&s_cnt[b0], 1);
+        if (b1 >= 0) p1 = atomicAdd(&s_cnt[b1], 1);
+        __syncthreads();
+        if (threadIdx.x < NUM_BINS)
+            s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(cnt + threadIdx.x, s_cnt[threadIdx.x]) : 0;
+        __syncthreads();
+        if (b0 >= 0) bins[(size_t)b0 * n + s_base[b0] + p0] = v;
+        if (b1 >= 0) bins[(size_t)b1 * n + s_base[b1] + p1] = v;
+        __syncthreads();
+    }
+}
+
+// mark: an n-int array free for this call (the row passes' out-degrees).
+int launch_bin_nodes(const int32_t *list, int32_t k, const int32_t *kptr, const int32_t *rp, const int32_t *ci,
+                     const Scratch &s, int32_t *mark, int32_t n, const Tune &t, cudaStream_t st) {
+    if (cudaMemsetAsync(mark, 0, (size_t)n * sizeof(int32_t), st) != cudaSuccess) return -1;
     if (cudaMemsetAsync(s.counters, 0, NUM_BINS * sizeof(int32_t), st) != cudaSuccess) return -1;
     // the work counters of the big-node kernels (CNT_BIGITEM .. CNT_HUB; CNT_TRIFRAC stays)
     if (cudaMemsetAsync(s.counters + CNT_BIGITEM, 0, (CNT_HUB - CNT_BIGITEM + 1) * sizeof(int32_t), st) !=
         cudaSuccess)
         return -1;
-    int64_t g = ((int64_t)k + 255) / 256;
-    k_bin_nodes<<<(unsigned)(g < 1 ? 1 : (g > 4096 ? 4096 : g)), 256, 0, st>>>(list, k, kptr, s.D, n, hub_min,
-                                                                              s.bins, s.counters);
+    int64_t g = ((int64_t)k * 32 + 255) / 256;
+    k_mark_nbhd<<<(unsigned)(g < 1 ? 1 : (g > 8192 ? 8192 : g)), 256, 0, st>>>(list, k, kptr, rp, ci, n, mark,
+                                                                              s.counters);
+    k_bin_marked<<<t.grid((int64_t)n, 256), 256, 0, st>>>(mark, s.D, n, t.hub_min, s.bins, s.counters);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 constexpr int NODE_THREADS = 256;
 constexpr int NODE_ROW_SMEM = 4096;   // rows up to this length are staged for the triangle tests
 
+// Is x adjacent to y?  Binary search in the shorter of the two sorted rows.
+__device__ __forceinline__ bool adjacent(const int32_t *rp, const int32_t *ci, int x, int Dx, int y, int Dy) {
+    const int a = Dx <= Dy ? x : y, b = Dx <= Dy ? y : x;
+    const int s = rp[a], len = rp[a + 1] - s;
+    const int p = lower_bound_i32(ci + s, len, b);
+    return p < len && ci[s + p] == b;
+}
+
+// A CTA per listed node v: triangles at v and their corrections, then EF.
+// T_v = Ccenter[v] (middle, open degrees) + Tacc[v] (end, open degrees, from
+// the wedge pass over the marked middle nodes) + corrections.  Triangles are
+// found either as adjacent pairs of N(v) (C(D_v, 2) tests in the shorter
+// rows, each triangle once) or by streaming every neighbour's row against
+// N(v) (sigma1(v) tests in a row held in shared memory, each triangle twice),
+// whichever costs less.
 template <bool F64>
-__global__ void __launch_bounds__(NODE_THREADS) k_nodes_exact(
+__global__ void __launch_bounds__(NODE_THREADS) k_nodes_final(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
     const int64_t *__restrict__ sig1, const int64_t *__restrict__ sig2, const int64_t *__restrict__ omega,
-    const void *__restrict__ Ccenter, const double *__restrict__ ftab, const int64_t *__restrict__ tq,
+    const void *__restrict__ Ccenter, const double *__restrict__ Tacc, const int64_t *__restrict__ tq,
     const int32_t *__restrict__ cnt, const int32_t *__restrict__ list, int32_t k_max,
-    const int32_t *__restrict__ kptr, int32_t n, ef_outputs out) {
+    const int32_t *__restrict__ kptr, int32_t n, const int64_t *__restrict__ qacc, const int64_t *__restrict__ tcnt,
+    ef_outputs out) {
     __shared__ int32_t s_row[NODE_ROW_SMEM];
-    __shared__ double s_acc[NODE_THREADS / 32];
     __shared__ long long s_q[NODE_THREADS / 32], s_t[NODE_THREADS / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int F = cnt[CNT_TRIFRAC];
     const int k = kptr ? *kptr : k_max;
     for (int i = blockIdx.x; i < k; i += gridDim.x) {
         const int v = list[i];
-        if (v < 0 || v >= n) continue;   // reported by k_bin_nodes (the whole CTA skips alike)
+        if (v < 0 || v >= n) continue;   // reported by k_mark_nbhd (the whole CTA skips alike)
         const int a = rp[v], Dv = rp[v + 1] - a;
-        const bool staged = Dv <= NODE_ROW_SMEM;
+        const int64_t s1v = sig1[v];
+        const bool global = qacc != nullptr;   // triangles already counted by the full pass
+        const bool by_pairs = !global && (int64_t)Dv * (Dv - 1) / 2 * 16 <= s1v;
+        const bool staged = !global && !by_pairs && Dv <= NODE_ROW_SMEM;
         if (staged)
             for (int e = threadIdx.x; e < Dv; e += NODE_THREADS) s_row[e] = ci[a + e];
         __syncthreads();
-        const int32_t *row = staged ? s_row : ci + a;
-        SumAcc<AccT<F64>> acc;
-        int64_t q2 = 0, t2 = 0;
-        for (int e = w; e < Dv; e += NODE_THREADS / 32) {
-            const int u = row[e];
-            const int ua = rp[u], Du = rp[u + 1] - ua;
-            const int base = Du + Dv - 4;
-            for (int jj = lane; jj < Du; jj += 32) {
-                const int x = ci[ua + jj];
-                if (x == v) continue;
-                const int Dx = D[x];
-                if constexpr (F64) acc.add(__ldg(ftab + base + Dx));
-                else acc.add(dlog2d((float)(base + Dx)));
-                const int p = lower_bound_i32(row, Dv, x);
-                if (p < Dv && row[p] == x) {
-                    q2 += __ldg(tq + Dv + Du + Dx);
-                    ++t2;
+        int64_t q = 0, t = 0;   // by pairs: each triangle once; by streaming: twice
+        if (global) {
+        } else if (by_pairs) {
+            for (int x = w; x < Dv; x += NODE_THREADS / 32) {
+                const int bx = ci[a + x], Dx = D[bx];
+                for (int y = x + 1 + lane; y < Dv; y += 32) {
+                    const int by = ci[a + y], Dy = D[by];
+                    if (adjacent(rp, ci, bx, Dx, by, Dy)) {
+                        q += __ldg(tq + Dv + Dx + Dy);
+                        ++t;
+                    }
+                }
+            }
+        } else {
+            const int32_t *row = staged ? s_row : ci + a;
+            for (int e = w; e < Dv; e += NODE_THREADS / 32) {
+                const int u = row[e];
+                const int ua = rp[u], Du = rp[u + 1] - ua;
+                for (int jj = lane; jj < Du; jj += 32) {
+                    const int x = ci[ua + jj];
+                    if (x == v) continue;
+                    const int p = lower_bound_i32(row, Dv, x);
+                    if (p < Dv && row[p] == x) {
+                        q += __ldg(tq + Dv + Du + D[x]);
+                        ++t;
+                    }
                 }
             }
         }
-        double end = F64 ? (double)acc.get() : (double)acc.get() * LN2;
-        end = warp_sum(end);
-        q2 = warp_sum(q2);
-        t2 = warp_sum(t2);
+        q = warp_sum(q);
+        t = warp_sum(t);
         if (lane == 0) {
-            s_acc[w] = end;
-            s_q[w] = q2;
-            s_t[w] = t2;
+            s_q[w] = q;
+            s_t[w] = t;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double e_sum = 0.0;
             int64_t qs = 0, ts = 0;
-            for (int q = 0; q < NODE_THREADS / 32; ++q) {
-                e_sum += s_acc[q];
-                qs += s_q[q];
-                ts += s_t[q];
+            for (int j = 0; j < NODE_THREADS / 32; ++j) {
+                qs += s_q[j];
+                ts += s_t[j];
             }
-            const int64_t d = Dv, t = ts / 2, s1 = sig1[v], s2 = sig2[v], om = omega[v];
-            const int64_t N = d * (d - 2) + s1;
+            if (global) {
+                qs = qacc[v];
+                ts = tcnt[v];
+            } else if (!by_pairs) {
+                qs /= 2;   // each triangle was found through both of its other nodes
+                ts /= 2;
+            }
+            const int64_t d = Dv, s2 = sig2[v], om = omega[v];
+            const int64_t N = d * (d - 2) + s1v;
             const int64_t S =
-                d * (d - 1) * (d - 4) + 2 * (d - 1) * s1 + s2 - s1 + (d - 4) * (s1 - d) + om - d * d - 8 * t;
+                d * (d - 1) * (d - 4) + 2 * (d - 1) * s1v + s2 - s1v + (d - 4) * (s1v - d) + om - d * d - 8 * ts;
             const double cc = d >= 2 ? (double)reinterpret_cast<const AccT<F64> *>(Ccenter)[v] : 0.0;
-            const double T = cc + e_sum + ldexp((double)(qs / 2), -F);
+            const double T = cc + Tacc[v] + ldexp((double)qs, -F);
             double ef = 0.0;
             uint8_t fl = 1;
             if (S > 0) {
@@ -412,24 +466,72 @@ __global__ void __launch_bounds__(NODE_THREADS) k_nodes_exact(
             if (out.n_clusters) out.n_clusters[i] = N;
             if (out.s) out.s[i] = S;
             if (out.t) out.t[i] = T;
-            if (out.triangles) out.triangles[i] = t;
+            if (out.triangles) out.triangles[i] = ts;
             if (out.flag) out.flag[i] = fl;
         }
         __syncthreads();
     }
 }
 
+// With the full triangle pass done: a thread per listed node assembles T, S,
+// N and EF from the accumulators (as the finalize pass does for all nodes).
+template <bool F64>
+__global__ void k_nodes_assemble(const int32_t *__restrict__ D, const int64_t *__restrict__ sig1,
+                                 const int64_t *__restrict__ sig2, const int64_t *__restrict__ omega,
+                                 const void *__restrict__ Ccenter, const double *__restrict__ Tacc,
+                                 const int64_t *__restrict__ qacc, const int64_t *__restrict__ tcnt,
+                                 const int32_t *__restrict__ cnt, const int32_t *__restrict__ list, int32_t k_max,
+                                 const int32_t *__restrict__ kptr, int32_t n, ef_outputs out) {
+    const int F = cnt[CNT_TRIFRAC];
+    const int k = kptr ? *kptr : k_max;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+        const int v = list[i];
+        if (v < 0 || v >= n) continue;   // reported by k_mark_nbhd
+        const int64_t d = D[v], s1 = sig1[v], s2 = sig2[v], om = omega[v], t = tcnt[v];
+        const int64_t N = d * (d - 2) + s1;
+        const int64_t S = d * (d - 1) * (d - 4) + 2 * (d - 1) * s1 + s2 - s1 + (d - 4) * (s1 - d) + om - d * d - 8 * t;
+        const double cc = d >= 2 ? (double)reinterpret_cast<const AccT<F64> *>(Ccenter)[v] : 0.0;
+        const double T = cc + Tacc[v] + ldexp((double)qacc[v], -F);
+        double ef = 0.0;
+        uint8_t fl = 1;
+        if (S > 0) {
+            ef = log((double)S) - T / (double)S;
+            fl = 0;
+        }
+        if (out.ef) out.ef[i] = ef;
+        if (out.n_clusters) out.n_clusters[i] = N;
+        if (out.s) out.s[i] = S;
+        if (out.t) out.t[i] = T;
+        if (out.triangles) out.triangles[i] = t;
+        if (out.flag) out.flag[i] = fl;
+    }
+}
+
+// global_tri: take t and the corrections from the full triangle pass (qacc,
+// tcnt) instead of counting per listed node.
 int launch_nodes_exact(const int32_t *rp, const int32_t *ci, const Scratch &s, const int32_t *list, int32_t k,
-                       const int32_t *kptr, int32_t n, int precision, const ef_outputs &out, const Tune &t,
-                       cudaStream_t st) {
+                       const int32_t *kptr, int32_t n, int precision, bool global_tri, const ef_outputs &out,
+                       const Tune &t, cudaStream_t st) {
     if (k <= 0) return 0;
+    if (global_tri) {
+        int64_t g = ((int64_t)k + 255) / 256;
+        const unsigned ga = (unsigned)(g < 1 ? 1 : (g > (int64_t)t.num_sms * 16 ? (int64_t)t.num_sms * 16 : g));
+        if (precision == EF_PREC_FP64)
+            k_nodes_assemble<true><<<ga, 256, 0, st>>>(s.D, s.sig1, s.sig2, s.omega, s.Ccenter, s.Tacc, s.qacc, s.tcnt,
+                                                       s.counters, list, k, kptr, n, out);
+        else
+            k_nodes_assemble<false><<<ga, 256, 0, st>>>(s.D, s.sig1, s.sig2, s.omega, s.Ccenter, s.Tacc, s.qacc,
+                                                        s.tcnt, s.counters, list, k, kptr, n, out);
+        return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
     const unsigned grid = (unsigned)(k < t.num_sms * 8 ? k : t.num_sms * 8);
+    const int64_t *q = nullptr, *tc = nullptr;
     if (precision == EF_PREC_FP64)
-        k_nodes_exact<true><<<grid, NODE_THREADS, 0, st>>>(rp, ci, s.D, s.sig1, s.sig2, s.omega, s.Ccenter, s.ftab,
-                                                           s.tq, s.counters, list, k, kptr, n, out);
+        k_nodes_final<true><<<grid, NODE_THREADS, 0, st>>>(rp, ci, s.D, s.sig1, s.sig2, s.omega, s.Ccenter, s.Tacc,
+                                                           s.tq, s.counters, list, k, kptr, n, q, tc, out);
     else
-        k_nodes_exact<false><<<grid, NODE_THREADS, 0, st>>>(rp, ci, s.D, s.sig1, s.sig2, s.omega, s.Ccenter,
-                                                            s.ftab, s.tq, s.counters, list, k, kptr, n, out);
+        k_nodes_final<false><<<grid, NODE_THREADS, 0, st>>>(rp, ci, s.D, s.sig1, s.sig2, s.omega, s.Ccenter,
+                                                            s.Tacc, s.tq, s.counters, list, k, kptr, n, q, tc, out);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -440,9 +542,15 @@ __device__ __forceinline__ uint64_t order_key(double x) {
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
+// Order-preserving 32-bit key of a finite float (never 0), in a 64-bit slot.
+__device__ __forceinline__ uint64_t order_key32(float x) {
+    const uint32_t b = __float_as_uint(x);
+    return (uint64_t)((b >> 31) ? ~b : (b | 0x80000000u));
+}
+
 __global__ void k_keys_score(const float *__restrict__ score, int32_t n, uint64_t *__restrict__ key) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        key[v] = order_key((double)score[v]);
+        key[v] = order_key32(score[v]);
 }
 
 // role[v]: bit 1 candidate (from the selected list), bit 2 audit (node v is
