@@ -108,7 +108,20 @@ def parse():
     p.add_argument("--autotune", action="store_true", help="run ef_autotune on the workload before timing")
     p.add_argument("--no-surrogate", action="store_true", help="skip the learned ranking leg")
     p.add_argument("--surrogate-steps", type=int, default=3000)
+    p.add_argument("--rmat-sweep", action="store_true",
+                   help="add EF time and clusters/ms on R-MAT graphs of 2^16 nodes, M = 2..32 edges per node")
     return p.parse_args()
+
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    """The largest of one number per rank (a MAX all-reduce; the value itself at N = 1)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_env():
@@ -211,6 +224,35 @@ def cpu_baseline(g, seconds: float, seed: int = 0):
     return {"value": rate, "unit": "clusters/s", "cores": cores, "kind": "oracle",
             "sample": f"{nodes_done} uniformly random nodes (vertex-centric oracle, OpenMP dynamic,2), "
                       f"{credits / 4:.3g} clusters = credited/4, {t_used:.1f} s"}
+
+
+def rmat_sweep(ctx, args, dev) -> list:
+    """EF of R-MAT graphs with 2^16 nodes and M = 2..32 edges per node
+    (a, b, c = 0.57, 0.19, 0.19; the paper's Figs. 3-4 setting, parameters
+    not printed there): ms per graph and clusters per ms."""
+    import torch
+    import paper_2306_00606_gb300 as ef
+    rows = []
+    stream = torch.cuda.current_stream(dev)
+    for M in (2, 4, 8, 16, 32):
+        g = synth.rmat(16, M, synth.SEED_BASE + 100 + M)
+        rp = torch.from_numpy(g.row_ptr).to(dev)
+        ci = torch.from_numpy(g.col_idx).to(dev)
+        out = torch.empty(g.n, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            ef.ef_compute_ex(ctx.handle, rp, ci, precision=args.precision, ef=out)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            ef.ef_compute_ex(ctx.handle, rp, ci, precision=args.precision, ef=out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / 10
+        W = graph_stats(g)["W"]
+        rows.append({"M": M, "nodes": g.n, "nnz": g.nnz, "avg_degree": g.nnz / g.n, "clusters": W, "ms": ms,
+                     "clusters_per_ms": W / ms})
+    return rows
 
 
 def surrogate_leg(args, dev) -> dict:
@@ -377,12 +419,7 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        ms_ = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms_], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_ = float(t.item())
-        return ms_
+        return max_over_ranks(ev0.elapsed_time(ev1), world, dev)
 
     with ClockSampler(local) as clk:
         ms = timed(profile=not batched)
@@ -411,11 +448,7 @@ def run_ours(args):
         for _ in range(args.steps):
             step(io=io)
         torch.cuda.synchronize(dev)
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
         e2e = {"value": st["W"] * args.steps * world / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
@@ -462,6 +495,8 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, args.cpu_seconds)
+    if rank == 0 and args.rmat_sweep:
+        line["rmat_sweep"] = rmat_sweep(ctx, args, dev)
     if rank == 0 and world == 1 and not args.no_surrogate and args.scale == 1.0:
         del rp, ci, out
         ctx.close()

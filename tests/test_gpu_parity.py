@@ -263,6 +263,13 @@ def test_invalid_graphs_rejected(ctx, bad):
     assert ei.value.code == ef.EF_ERR_GRAPH
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_rmat_graph(ctx, precision):
+    # skewed R-MAT (a, b, c = .57, .19, .19): many hubs and triangles
+    g = synth.rmat(12, 8, 31)
+    assert_parity(run(ctx, g, precision), alg1_ref(g), precision)
+
+
 def test_empty_graph(ctx):
     import torch
     out = ctx.compute(torch.zeros(1, dtype=torch.int32, device="cuda"),
