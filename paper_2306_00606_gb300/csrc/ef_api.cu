@@ -91,9 +91,10 @@ namespace {
 thread_local char g_err[512];
 
 // Kernels one call launches (default wedge mode): part A 3 (+1 batched),
-// f table 1, orientation (a scan of 3 + node records + 2), small wedges 4,
-// class wedges 2, triangles 2 (hash tables, pair tests), finalize 1.
-constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 6 + 4 + 2 + 2 + 1;
+// f table 1, orientation (layout gather, a scan of 3, layout scatter, node
+// records, 2), small wedges 4, class wedges 2, triangles 2 (hash tables,
+// pair tests), finalize 1.
+constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 8 + 4 + 2 + 2 + 1;
 
 void set_err(ef_ctx *c, const char *fmt, ...) {
     char *dst = c ? c->err : g_err;
@@ -625,6 +626,8 @@ size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s) {
     s.outdeg = (int32_t *)take(4 * N);
     s.fp_row = (uint64_t *)take(8 * N);
     s.out_ptr = (int32_t *)take(4 * (N + 1));
+    s.lay_node = (int32_t *)take(4 * N);
+    s.lay_ptr = (int32_t *)take(4 * (N + 1));
     s.info = (int4 *)take(16 * N);
     s.out_col = (int32_t *)take(4 * (M + 8));
     s.out_D = (int32_t *)take(4 * (M + 1));

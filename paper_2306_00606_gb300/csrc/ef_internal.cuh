@@ -106,7 +106,10 @@ struct Scratch {
     int32_t *outdeg;     // n      out-degree in (degree, id) order
     uint64_t *fp_row;    // n      fingerprint of the lower-ranked neighbours, from the node's own row
     uint64_t *fp_push;   // n      the same, pushed by those neighbours (symmetry check)
-    int32_t *out_ptr;    // n+1    oriented CSR offsets
+    int32_t *out_ptr;    // n+1    oriented CSR offsets (a list runs from out_ptr[v] for outdeg[v] entries;
+                         //        out_ptr[n] = all entries); lists are stored in layout order
+    int32_t *lay_node;   // n      layout order: the work bins concatenated (degree classes)
+    int32_t *lay_ptr;    // n+1    out-degrees in layout order, then their scan
     int4    *info;       // n      {D, sigma1, out_ptr, out_ptr next} per node, for the orientation
     int32_t *out_col;    // m+8    oriented neighbour ids (ascending id within a row)
     int32_t *out_D;      // m+1    their degrees

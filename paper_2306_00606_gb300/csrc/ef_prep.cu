@@ -354,12 +354,70 @@ struct Orient {
     }
 };
 
-// info[v] = {D_v, sigma1(v), out_ptr[v], out_ptr[v+1]}: what the orientation
-// needs of a neighbour, in one 16-byte gather (sigma1 <= m < 2^31).
+// info[v] = {D_v, sigma1(v), start, end of v's out-list}: what the
+// orientation needs of a neighbour, in one 16-byte gather (sigma1 <= m < 2^31).
 __global__ void k_node_info(const int32_t *__restrict__ D, const int64_t *__restrict__ sig1,
-                            const int32_t *__restrict__ out_ptr, int32_t n, int4 *__restrict__ info) {
+                            const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ outdeg, int32_t n,
+                            int4 *__restrict__ info) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        info[v] = make_int4(D[v], (int)sig1[v], out_ptr[v], out_ptr[v + 1]);
+        info[v] = make_int4(D[v], (int)sig1[v], out_ptr[v], out_ptr[v] + outdeg[v]);
+}
+
+// Layout of the oriented CSR: the out-lists are stored work bin by work bin
+// (degree classes 1-4, 5-8, 9-16, 17-32, the warp class, the hub buckets),
+// not in node order, so that the lists of nodes of similar degree -- and
+// similar odds of being probed by the triangle pass -- share cache lines.
+// Nodes of degree 0 have no list.
+constexpr int LAYOUT_BINS = 5 + NUM_HUB_BUCKETS;
+__constant__ int c_layout_bins[LAYOUT_BINS] = {BIN_S4,       BIN_S8,       BIN_S16,      BIN_S32,
+                                               BIN_MID,      BIN_HUB0,     BIN_HUB0 + 1, BIN_HUB0 + 2,
+                                               BIN_HUB0 + 3, BIN_HUB0 + 4, BIN_HUB0 + 5, BIN_HUB0 + 6};
+static_assert(BIN_HUB0 + 6 == BIN_HUB_LAST, "layout bins cover the hub buckets");
+
+// base[q] = first layout position of bin q; base[LAYOUT_BINS] = all listed nodes.
+__device__ __forceinline__ void layout_bases(const int32_t *cnt, int *base) {
+    int acc = 0;
+    for (int q = 0; q < LAYOUT_BINS; ++q) {
+        base[q] = acc;
+        acc += cnt[c_layout_bins[q]];
+    }
+    base[LAYOUT_BINS] = acc;
+}
+
+// The node at layout position i < base[LAYOUT_BINS].
+__device__ __forceinline__ int layout_node(const int32_t *bins, int32_t n, const int *base, int i) {
+    int q = 0;
+    while (base[q + 1] <= i) ++q;
+    return bins[(size_t)c_layout_bins[q] * n + (i - base[q])];
+}
+
+__global__ void k_layout_gather(const int32_t *__restrict__ bins, const int32_t *__restrict__ cnt, int32_t n,
+                                const int32_t *__restrict__ outdeg, int32_t *__restrict__ lay_node,
+                                int32_t *__restrict__ lay_deg) {
+    __shared__ int s_base[LAYOUT_BINS + 1];
+    if (threadIdx.x == 0) layout_bases(cnt, s_base);
+    __syncthreads();
+    const int total = s_base[LAYOUT_BINS];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i >= total) {
+            lay_deg[i] = 0;
+            continue;
+        }
+        const int v = layout_node(bins, n, s_base, i);
+        lay_node[i] = v;
+        lay_deg[i] = outdeg[v];
+    }
+}
+
+__global__ void k_layout_scatter(const int32_t *__restrict__ cnt, int32_t n, const int32_t *__restrict__ lay_node,
+                                 const int32_t *__restrict__ lay_ptr, int32_t *__restrict__ out_ptr) {
+    __shared__ int s_base[LAYOUT_BINS + 1];
+    if (threadIdx.x == 0) layout_bases(cnt, s_base);
+    __syncthreads();
+    const int total = s_base[LAYOUT_BINS];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+        out_ptr[lay_node[i]] = lay_ptr[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) out_ptr[n] = lay_ptr[total];
 }
 
 __global__ void k_orient(const int32_t *__restrict__ rp, int32_t n, int64_t m, int tmax, int hub_min, Orient o,
@@ -582,8 +640,12 @@ int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
 // Oriented CSR and omega.
 int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
                   cudaStream_t st, int32_t *nmin, int32_t *nmax) {
-    if (launch_scan(s.outdeg, s.out_ptr, n, s.scan_tmp, st)) return -1;
-    k_node_info<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.D, s.sig1, s.out_ptr, n, s.info);
+    // out-list offsets in layout order (degree-0 nodes keep offset 0 and an empty list)
+    if (cudaMemsetAsync(s.out_ptr, 0, (size_t)(n + 1) * sizeof(int32_t), st) != cudaSuccess) return -1;
+    k_layout_gather<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.bins, s.counters, n, s.outdeg, s.lay_node, s.lay_ptr);
+    if (launch_scan(s.lay_ptr, s.lay_ptr, n, s.scan_tmp, st)) return -1;
+    k_layout_scatter<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.counters, n, s.lay_node, s.lay_ptr, s.out_ptr);
+    k_node_info<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.D, s.sig1, s.out_ptr, s.outdeg, n, s.info);
     const Orient o{ci, s.info, s.out_col, s.out_D, s.out_src, s.out_rng, nmin, nmax, n};
     k_orient<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, n, m, t.row_thread_max, t.hub_min, o, s.out_ptr, s.omega);
     k_orient_hub<<<t.num_sms * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters, s.omega);

@@ -69,16 +69,16 @@ __device__ __forceinline__ int bucket_of(int key, int nb) {
 
 // Thread per oriented entry: insert it into its owner's table (cleared to -1
 // beforehand) by linear probing over slots from the key's bucket.
-__global__ void k_out_hash(const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_col,
-                           const int32_t *__restrict__ out_src, int32_t n, int64_t hash_cap,
-                           int32_t *__restrict__ out_hash) {
+__global__ void k_out_hash(const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ outdeg,
+                           const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_src, int32_t n,
+                           int64_t hash_cap, int32_t *__restrict__ out_hash) {
     const int64_t total = out_ptr[n];
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int a = out_src[k];
         int64_t hb;
         int nb;
-        if (!out_table(out_ptr[a], out_ptr[a + 1], hash_cap, hb, nb)) continue;
+        if (!out_table(out_ptr[a], out_ptr[a] + outdeg[a], hash_cap, hb, nb)) continue;
         const int key = out_col[k];
         const int cap = 4 * nb;
         int sl = 4 * bucket_of(key, nb);
@@ -170,7 +170,8 @@ template <int TRI_UNIT, int TRI_BLOCKS>
 __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
     const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_D,
     const int2 *__restrict__ out_rng, const int32_t *__restrict__ out_src, const int32_t *__restrict__ out_hash,
-    int64_t hash_cap, const int32_t *__restrict__ D, int32_t n, const int64_t *__restrict__ tq,
+    int64_t hash_cap, const int32_t *__restrict__ outdeg, const int32_t *__restrict__ D, int32_t n,
+    const int64_t *__restrict__ tq,
     int64_t *__restrict__ qacc, int64_t *__restrict__ tcnt) {
     __shared__ int s_ex[TRI_WARPS][32];   // exclusive prefix of unit counts
     __shared__ int s_kend[TRI_WARPS][32], s_b[TRI_WARPS][32], s_Db[TRI_WARPS][32], s_bs[TRI_WARPS][32];
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
         int nu = 0;
         if (k < total) {
             const int a = out_src[k];
-            const int kend = out_ptr[a + 1];
+            const int kend = out_ptr[a] + outdeg[a];
             const int np = kend - (int)k - 1;
             if (np > 0) {
                 const int b = out_col[k];
@@ -301,8 +302,8 @@ static inline unsigned grid_of(int64_t work, int per_block, int64_t cap) {
 int launch_out_hash(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st) {
     const int num_sms = t.num_sms;
     if (cudaMemsetAsync(s.out_hash, 0xff, (size_t)hash_slots(m) * sizeof(int32_t), st) != cudaSuccess) return -1;
-    k_out_hash<<<grid_of(m / 2, 256, (int64_t)num_sms * 32), 256, 0, st>>>(s.out_ptr, s.out_col, s.out_src, n,
-                                                                          hash_slots(m), s.out_hash);
+    k_out_hash<<<grid_of(m / 2, 256, (int64_t)num_sms * 32), 256, 0, st>>>(s.out_ptr, s.outdeg, s.out_col, s.out_src,
+                                                                          n, hash_slots(m), s.out_hash);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -310,10 +311,12 @@ int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cuda
     const unsigned grid = grid_of(m / 2, TRI_WARPS * 32, (int64_t)t.num_sms * 16);
     if (t.tri_variant == 1)
         k_tri_pairs<4, 3><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_rng, s.out_src,
-                                                            s.out_hash, hash_slots(m), s.D, n, s.tq, s.qacc, s.tcnt);
+                                                            s.out_hash, hash_slots(m), s.outdeg, s.D, n, s.tq, s.qacc,
+                                                            s.tcnt);
     else
         k_tri_pairs<2, 4><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_rng, s.out_src,
-                                                            s.out_hash, hash_slots(m), s.D, n, s.tq, s.qacc, s.tcnt);
+                                                            s.out_hash, hash_slots(m), s.outdeg, s.D, n, s.tq, s.qacc,
+                                                            s.tcnt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
