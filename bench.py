@@ -108,6 +108,7 @@ def parse():
     p.add_argument("--autotune", action="store_true", help="run ef_autotune on the workload before timing")
     p.add_argument("--no-surrogate", action="store_true", help="skip the learned ranking leg")
     p.add_argument("--surrogate-steps", type=int, default=3000)
+    p.add_argument("--no-shards", action="store_true", help="skip the sharded-decomposition leg")
     p.add_argument("--rmat-sweep", action="store_true",
                    help="add EF time and clusters/ms on R-MAT graphs of 2^16 nodes, M = 2..32 edges per node")
     return p.parse_args()
@@ -252,6 +253,43 @@ def rmat_sweep(ctx, args, dev) -> list:
         W = graph_stats(g)["W"]
         rows.append({"M": M, "nodes": g.n, "nnz": g.nnz, "avg_degree": g.nnz / g.n, "clusters": W, "ms": ms,
                      "clusters_per_ms": W / ms})
+    return rows
+
+
+def shard_leg(ctx, rp, ci, args, dev, full_ms: float) -> list:
+    """The sharded decomposition on one device: for R shards, the time of
+    each shard's ef_compute_shard (CUDA events on the context stream, best of
+    3 rounds) and of the finalize from summed partials.  On R devices a job
+    would take the slowest shard, the all-reduce of 40 bytes per node and
+    the finalize."""
+    import torch
+    import paper_2306_00606_gb300 as ef
+    n = int(rp.shape[0]) - 1
+    stream = torch.cuda.current_stream(dev)
+    parts = ef.empty_partials(n, dev)
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1), r
+
+    rows = []
+    for R in (2, 4, 8):
+        best = [float("inf")] * R
+        for _ in range(3):
+            for r in range(R):
+                ms, (frac, _) = timed(lambda: ef.ef_compute_shard(ctx.handle, rp, ci, r, R, parts,
+                                                                   precision=args.precision))
+                best[r] = min(best[r], ms)
+        fin = min(timed(lambda: ef.ef_finalize_partials(ctx.handle, parts, frac, precision=args.precision,
+                                                         ef=out))[0] for _ in range(3))
+        rows.append({"shards": R, "shard_ms_max": max(best), "shard_ms_mean": sum(best) / R,
+                     "finalize_ms": fin, "unsharded_ms": full_ms,
+                     "projected_speedup_excl_allreduce": full_ms / (max(best) + fin)})
     return rows
 
 
@@ -495,6 +533,8 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, args.cpu_seconds)
+    if rank == 0 and world == 1 and not batched and not args.no_shards:
+        line["shards"] = shard_leg(ctx, rp, ci, args, dev, ms_step)
     if rank == 0 and args.rmat_sweep:
         line["rmat_sweep"] = rmat_sweep(ctx, args, dev)
     if rank == 0 and world == 1 and not args.no_surrogate and args.scale == 1.0:

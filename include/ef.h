@@ -204,6 +204,56 @@ int ef_compute_nodes(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
                      ef_outputs *out);
 
 /* ------------------------------------------------------------------------
+ * Sharded computation (Eq. 1 split over workers).  Every term of T_v comes
+ * from one cluster, counted at its middle node, and every triangle
+ * correction from one triangle, counted at its lowest-ranked node in the
+ * (degree, id) order.  So R workers that each hold the whole CSR can split
+ * Algorithm 1's cluster loop: shard r owns the nodes [lo, hi), lo the first
+ * row that starts at or after adjacency entry r m / R, takes the clusters
+ * and triangles counted at its nodes, and writes per-node partials, plus the
+ * closed-form sums N_v and S_v + 8 t_v of its own nodes.  The element-wise
+ * sum of the R partials (the one exchange: an all-reduce of 40 bytes per
+ * node) gives ef_finalize_partials, an element-wise pass with no graph
+ * input, the same N, S and triangle counts as ef_compute_ex, and EF within
+ * its precision's bound (T's FP64 sum depends on the order of additions).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    double  *t;          /* this shard's part of T_v at open degrees (its
+                            clusters counted without triangle corrections) */
+    int64_t *q;          /* triangle corrections to T_v, units of
+                            2^-frac_bits */
+    int64_t *triangles;  /* triangles through v that this shard listed */
+    int64_t *n_clusters; /* N_v for v in the shard's range, else 0 */
+    int64_t *s_open;     /* S_v + 8 t_v for v in the shard's range, else 0 */
+} ef_partials;
+
+/*
+ * Partials of shard `shard` of `num_shards` (0 <= shard < num_shards).
+ *   g: CSR (device); out: five device arrays of length n, all required;
+ *   they are overwritten, not accumulated into;
+ *   frac_bits (host, may be NULL): the fixed-point scale of q, the same for
+ *   every shard of one graph; range (host int32[2], may be NULL): the
+ *   shard's nodes [range[0], range[1]) (empty when R exceeds the rows).
+ * Validation and precision as ef_compute_ex (every shard validates the
+ * whole graph unless trust_input); host_io and async give EF_ERR_ARG.
+ * Shards may run on different devices or one after another.
+ */
+int ef_compute_shard(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
+                     int32_t shard, int32_t num_shards, const ef_options *opt,
+                     ef_partials *out, int32_t *frac_bits, int32_t *range);
+
+/*
+ * EF from partials summed over all shards of one graph: five device arrays
+ * of length n (q in units of 2^-frac_bits, 0..52, as ef_compute_shard
+ * reported).  Writes any requested member of *out (device arrays of length
+ * n) as ef_compute_ex would; reads no graph.  Only precision is read from
+ * *opt; host_io and async give EF_ERR_ARG.
+ */
+int ef_finalize_partials(ef_ctx *ctx, int32_t n, const ef_partials *sum,
+                         int32_t frac_bits, const ef_options *opt,
+                         ef_outputs *out);
+
+/* ------------------------------------------------------------------------
  * Learned ranking path.  A regression network 16-64-64-1 (ReLU, BF16
  * tensor-core products with FP32 accumulation) maps 16 cheap per-node
  * features to a predicted EF.  It is trained on exact EF produced by this

@@ -28,7 +28,8 @@ EXPORTED = ("ef_ctx_create", "ef_ctx_destroy", "ef_last_error", "ef_sync", "ef_g
             "ef_compute", "ef_compute_ex", "ef_compute_batched", "ef_get_tuning", "ef_set_tuning", "ef_autotune",
             "ef_compute_nodes", "ef_features", "ef_model_create", "ef_model_destroy", "ef_model_get", "ef_model_set",
             "ef_model_feature_mode", "ef_model_save", "ef_model_load", "ef_mlp_forward", "ef_mlp_grad",
-            "ef_surrogate_train", "ef_surrogate_rank", "ef_compute_static")
+            "ef_surrogate_train", "ef_surrogate_rank", "ef_compute_static", "ef_compute_shard",
+            "ef_finalize_partials")
 MODEL_PARAMS = 5313
 MODEL_FLOATS = MODEL_PARAMS + 32
 
@@ -52,6 +53,14 @@ class ef_options(ctypes.Structure):
 class ef_outputs(ctypes.Structure):
     _fields_ = [("ef", ctypes.c_void_p), ("n_clusters", ctypes.c_void_p), ("s", ctypes.c_void_p),
                 ("t", ctypes.c_void_p), ("triangles", ctypes.c_void_p), ("flag", ctypes.c_void_p)]
+
+
+class ef_partials(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_void_p), ("q", ctypes.c_void_p), ("triangles", ctypes.c_void_p),
+                ("n_clusters", ctypes.c_void_p), ("s_open", ctypes.c_void_p)]
+
+
+PARTIALS = ("t", "q", "triangles", "n_clusters", "s_open")   # float64, then int64 x4
 
 
 class ef_stats(ctypes.Structure):
@@ -141,6 +150,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(ef_options), vp, vp, vp,
                                       ctypes.POINTER(ef_rank_stats)]
     lib.ef_compute_static.argtypes = [ctypes.POINTER(ef_csr), i32, i64, i32, vp, vp]
+    lib.ef_compute_shard.argtypes = [vp, ctypes.POINTER(ef_csr), i32, i64, i32, i32, ctypes.POINTER(ef_options),
+                                     ctypes.POINTER(ef_partials), ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32)]
+    lib.ef_finalize_partials.argtypes = [vp, i32, ctypes.POINTER(ef_partials), i32, ctypes.POINTER(ef_options),
+                                         ctypes.POINTER(ef_outputs)]
     for name in EXPORTED:
         if name != "ef_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -272,6 +286,72 @@ def ef_compute_nodes(ctx: int, row_ptr, col_idx, nodes, *, precision: str = "fp6
     out = ef_outputs(_ptr(ef), _ptr(n_clusters), _ptr(s), _ptr(t), _ptr(triangles), _ptr(flag))
     _check(load_library().ef_compute_nodes(ctx, ctypes.byref(g), n, int(col_idx.shape[0]), _ptr(nodes),
                                            int(nodes.shape[0]), ctypes.byref(o), ctypes.byref(out)), ctx)
+
+
+def empty_partials(n: int, device) -> dict:
+    """Device buffers for one shard's partials (the five arrays of ef_partials)."""
+    import torch
+    return {k: torch.empty(n, dtype=torch.float64 if k == "t" else torch.int64, device=device) for k in PARTIALS}
+
+
+def ef_compute_shard(ctx: int, row_ptr, col_idx, shard: int, num_shards: int, parts: dict, *,
+                     precision: str = "fp64", trust_input: bool = False, wedge_mode: int = 0) -> tuple:
+    """Partials of one shard into ``parts`` (the five device tensors of
+    ``empty_partials``).  Returns (frac_bits, (lo, hi)): the fixed-point scale
+    of q and the shard's node range."""
+    n = int(row_ptr.shape[0]) - 1
+    g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
+    o = _options(precision, trust_input, False, False, False, wedge_mode, False)
+    p = ef_partials(*(_ptr(parts.get(k)) for k in PARTIALS))
+    frac = ctypes.c_int32()
+    rng = (ctypes.c_int32 * 2)()
+    _check(load_library().ef_compute_shard(ctx, ctypes.byref(g), n, int(col_idx.shape[0]), int(shard),
+                                           int(num_shards), ctypes.byref(o), ctypes.byref(p), ctypes.byref(frac),
+                                           rng), ctx)
+    return frac.value, tuple(rng)
+
+
+def ef_finalize_partials(ctx: int, parts: dict, frac_bits: int, *, precision: str = "fp64", ef=None,
+                         n_clusters=None, s=None, t=None, triangles=None, flag=None) -> None:
+    """EF from partials summed over every shard of one graph (device tensors; no graph input)."""
+    n = int(parts["t"].shape[0])
+    o = _options(precision, False, False, False, False, 0, False)
+    p = ef_partials(*(_ptr(parts.get(k)) for k in PARTIALS))
+    out = ef_outputs(_ptr(ef), _ptr(n_clusters), _ptr(s), _ptr(t), _ptr(triangles), _ptr(flag))
+    _check(load_library().ef_finalize_partials(ctx, n, ctypes.byref(p), int(frac_bits), ctypes.byref(o),
+                                               ctypes.byref(out)), ctx)
+
+
+def allreduce_partials(parts: dict, group=None) -> None:
+    """The one exchange of a sharded computation: element-wise sums over the
+    ranks of ``group`` (torch.distributed, in place, 40 bytes per node).  T
+    is summed in FP64; the other four arrays are integers and sum exactly."""
+    import torch.distributed as dist
+    for k in PARTIALS:
+        dist.all_reduce(parts[k], op=dist.ReduceOp.SUM, group=group)
+
+
+def compute_sharded(ctx: int, row_ptr, col_idx, rank: int, world: int, *, group=None, precision: str = "fp64",
+                    outputs=("ef",), trust_input: bool = False) -> dict:
+    """EF of every node with the cluster loop split over ``world`` ranks.
+
+    Each rank holds the whole CSR (device tensors), computes shard ``rank``,
+    takes part in ``allreduce_partials`` (skipped when world == 1) and
+    finalizes; every rank ends with the full outputs.
+    """
+    import torch
+    n = int(row_ptr.shape[0]) - 1
+    dev = row_ptr.device
+    parts = empty_partials(n, dev)
+    frac, _ = ef_compute_shard(ctx, row_ptr, col_idx, rank, world, parts, precision=precision,
+                               trust_input=trust_input)
+    if world > 1:
+        allreduce_partials(parts, group)
+    dt = dict(ef=torch.float64, n_clusters=torch.int64, s=torch.int64, t=torch.float64, triangles=torch.int64,
+              flag=torch.uint8)
+    res = {k: torch.empty(n, dtype=dt[k], device=dev) for k in outputs}
+    ef_finalize_partials(ctx, parts, frac, precision=precision, **res)
+    return res
 
 
 def ef_features(ctx: int, row_ptr, col_idx, x, *, mode: int = 0, trust_input: bool = False) -> None:

@@ -880,6 +880,90 @@ int ef_compute_nodes(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const i
     return final_check(ctx, s, !o.trust_input);
 }
 
+int ef_compute_shard(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, int32_t shard, int32_t num_shards,
+                     const ef_options *opt, ef_partials *out, int32_t *frac_bits, int32_t *range) {
+    using namespace ef;
+    if (!ctx) { set_err(nullptr, "null context"); return EF_ERR_ARG; }
+    ef_options o = {};
+    if (opt) o = *opt;
+    const ef_outputs none = {};
+    int rc = check_args(ctx, g, n, m, o, &none);
+    if (rc) return rc;
+    rc = check_learned_opts(ctx, o);
+    if (rc) return rc;
+    if (num_shards < 1 || shard < 0 || shard >= num_shards) {
+        set_err(ctx, "shard %d of %d", shard, num_shards);
+        return EF_ERR_ARG;
+    }
+    if (!out || (n > 0 && (!out->t || !out->q || !out->triangles || !out->n_clusters || !out->s_open))) {
+        set_err(ctx, "null partial array");
+        return EF_ERR_ARG;
+    }
+    if (o.wedge_mode < 0 || o.wedge_mode > 1) {
+        set_err(ctx, "wedge_mode %d is not available", o.wedge_mode);
+        return EF_ERR_UNSUPPORTED;
+    }
+    ctx->err[0] = 0;
+    if (n == 0) {
+        if (frac_bits) *frac_bits = TRI_FRAC_MAX;
+        if (range) memset(range, 0, 2 * sizeof(int32_t));
+        return EF_OK;
+    }
+    DeviceGuard dg(ctx->device);
+    Scratch s;
+    int64_t fcap;
+    rc = prepare_graph(ctx, g->row_ptr, g->col_idx, n, m, o, s, fcap);
+    if (rc) return rc;
+    const int32_t *rp = g->row_ptr, *ci = g->col_idx;
+    const Tune &t = ctx->tune;
+    cudaStream_t st = ctx->stream;
+    int32_t *rng = s.counters + CNT_RANGE;
+    LAUNCH(launch_shard_range(rp, n, m, shard, num_shards, rng, st), "shard range");
+    LAUNCH(launch_orient(rp, ci, n, m, s, t, st), "orientation");
+    LAUNCH(launch_out_hash(s, n, m, t, st), "out-list hash");
+    LAUNCH(launch_tri_pairs(s, n, m, t, st, rng), "triangle");
+    // the out-degrees are not needed any more: they hold the marks
+    LAUNCH(launch_mark_range(rng, n, s.outdeg, t, st), "shard marks");
+    LAUNCH(launch_bin_marked(s.outdeg, s, n, t, st), "shard bins");
+    LAUNCH(launch_wedge_small(rp, ci, s, o.precision, n, t, st), "small wedge");
+    LAUNCH(launch_wedge_big(rp, ci, s, o.precision, o.wedge_mode, n, m, t, st), "big wedge");
+    LAUNCH(launch_shard_out(rng, s, o.precision, n, *out, t, st), "shard partials");
+    CU(cudaMemcpyAsync(ctx->h_counters + CNT_TRIFRAC, s.counters + CNT_TRIFRAC, sizeof(int32_t),
+                       cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(ctx->h_counters + CNT_RANGE, rng, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    rc = final_check(ctx, s, !o.trust_input);
+    if (rc) return rc;
+    if (frac_bits) *frac_bits = ctx->h_counters[CNT_TRIFRAC];
+    if (range) memcpy(range, ctx->h_counters + CNT_RANGE, 2 * sizeof(int32_t));
+    return EF_OK;
+}
+
+int ef_finalize_partials(ef_ctx *ctx, int32_t n, const ef_partials *sum, int32_t frac_bits, const ef_options *opt,
+                         ef_outputs *out) {
+    using namespace ef;
+    if (!ctx) { set_err(nullptr, "null context"); return EF_ERR_ARG; }
+    ef_options o = {};
+    if (opt) o = *opt;
+    int rc = check_learned_opts(ctx, o);
+    if (rc) return rc;
+    if (n < 0 || !out) { set_err(ctx, "bad size n=%d or null outputs", n); return EF_ERR_ARG; }
+    if (!sum || (n > 0 && (!sum->t || !sum->q || !sum->triangles || !sum->n_clusters || !sum->s_open))) {
+        set_err(ctx, "null partial array");
+        return EF_ERR_ARG;
+    }
+    if (frac_bits < 0 || frac_bits > TRI_FRAC_MAX) {
+        set_err(ctx, "frac_bits %d outside 0..%d", frac_bits, TRI_FRAC_MAX);
+        return EF_ERR_ARG;
+    }
+    ctx->err[0] = 0;
+    if (n == 0) return EF_OK;
+    DeviceGuard dg(ctx->device);
+    LAUNCH(launch_finalize_sums(*sum, o.precision, n, frac_bits, *out, ctx->tune, ctx->stream), "finalize");
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaGetLastError());
+    return EF_OK;
+}
+
 int ef_features(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, int32_t mode, const ef_options *opt, float *x) {
     if (!ctx) { set_err(nullptr, "null context"); return EF_ERR_ARG; }
     ef_options o = {};

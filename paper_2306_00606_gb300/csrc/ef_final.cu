@@ -20,11 +20,36 @@
 // Precision: FP64 mode evaluates ln S - T/S in FP64.  FP32C evaluates it in
 // FP32 (absolute error a few 1e-6) except at nodes of degree > HUB_FP64_DEG,
 // where ln S is large and the cancellation in ln S - T/S is done in FP64.
+//
+// A sharded computation ends in k_finalize_sums: the shards' summed
+// partials already hold N and the open-degree sum S + 8t of every node, so
+// it needs no pass over the graph.  Its FP32C test for FP64 evaluation is on
+// S instead of the degree: S >= D (D-1) (D-4) (v's own clusters as middle
+// node have degree >= D - 4), so S > HUB_FP64_S holds at every node of
+// degree > HUB_FP64_DEG.
 #include "ef_internal.cuh"
 
 namespace ef {
 
 constexpr int HUB_FP64_DEG = 1000;
+constexpr int64_t HUB_FP64_S = (int64_t)HUB_FP64_DEG * (HUB_FP64_DEG - 1) * (HUB_FP64_DEG - 4);
+
+// EF = ln S - T / S for S > 0; wide: in FP64 also in FP32C mode.
+template <bool F64>
+__device__ __forceinline__ double ef_value(int64_t S, double T, bool wide) {
+    if (F64 || wide) {
+        const double Sd = (double)S;
+        return log(Sd) - T / Sd;
+    }
+    // ln S = ln(m) + e ln 2 with S = m 2^e, m in [0.5, 1).  ln 2 is split
+    // into 45426/2^16 (16 significant bits, so e times it is exact) plus
+    // the remainder ln 2 - 45426/2^16, keeping ln S at FP32 precision.
+    int e2;
+    const float Sf = (float)S;
+    const float mant = frexpf(Sf, &e2);
+    const float lnS = logf(mant) + (float)e2 * 0.693145751953125f + (float)e2 * 1.4286068203094e-06f;
+    return (double)(lnS - __fdiv_rn((float)T, Sf));
+}
 
 struct FinalArgs {
     const int32_t *D;
@@ -55,19 +80,7 @@ __global__ void __launch_bounds__(256) k_finalize(int32_t n, FinalArgs f) {
         uint8_t fl = 1;
         if (S > 0) {
             fl = 0;
-            if (F64 || d > HUB_FP64_DEG) {
-                const double Sd = (double)S;
-                ef = log(Sd) - T / Sd;
-            } else {
-                // ln S = ln(m) + e ln 2 with S = m 2^e, m in [0.5, 1).  ln 2 is split
-                // into 45426/2^16 (16 significant bits, so e times it is exact) plus
-                // the remainder ln 2 - 45426/2^16, keeping ln S at FP32 precision.
-                int e2;
-                const float Sf = (float)S;
-                const float mant = frexpf(Sf, &e2);
-                const float lnS = logf(mant) + (float)e2 * 0.693145751953125f + (float)e2 * 1.4286068203094e-06f;
-                ef = (double)(lnS - __fdiv_rn((float)T, Sf));
-            }
+            ef = ef_value<F64>(S, T, d > HUB_FP64_DEG);
         }
         const ef_outputs &o = f.o;
         if (o.ef) o.ef[v] = ef;
@@ -81,15 +94,48 @@ __global__ void __launch_bounds__(256) k_finalize(int32_t n, FinalArgs f) {
     if ((threadIdx.x & 31) == 0 && err) atomicOr(f.cnt + CNT_ERR, err);
 }
 
+// From the shards' summed partials: T_v = t + q 2^-F, S_v = S_open - 8 t_v.
+template <bool F64>
+__global__ void __launch_bounds__(256) k_finalize_sums(int32_t n, ef_partials p, int32_t frac, ef_outputs o) {
+    const double qscale = ldexp(1.0, -frac);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int64_t t = p.triangles[v];
+        const int64_t S = p.s_open[v] - 8 * t;
+        const double T = p.t[v] + (double)p.q[v] * qscale;
+        double ef = 0.0;
+        uint8_t fl = 1;
+        if (S > 0) {
+            fl = 0;
+            ef = ef_value<F64>(S, T, S > HUB_FP64_S);
+        }
+        if (o.ef) o.ef[v] = ef;
+        if (o.n_clusters) o.n_clusters[v] = p.n_clusters[v];
+        if (o.s) o.s[v] = S;
+        if (o.t) o.t[v] = T;
+        if (o.triangles) o.triangles[v] = t;
+        if (o.flag) o.flag[v] = fl;
+    }
+}
+
+static inline unsigned grid_n(int32_t n, const Tune &t) {
+    int64_t g = ((int64_t)n + 255) / 256;
+    const int64_t cap = (int64_t)t.num_sms * 32;
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
 int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs &out, const Tune &t,
                     cudaStream_t st) {
-    const int num_sms = t.num_sms;
     const FinalArgs f{s.D,    s.sig1,    s.sig2, s.omega, s.fp_row,   s.fp_push,
                       s.Tacc, s.Ccenter, s.qacc, s.tcnt,  s.counters, out};
-    int64_t g = ((int64_t)n + 255) / 256;
-    unsigned grid = (unsigned)(g < 1 ? 1 : (g > (int64_t)num_sms * 32 ? (int64_t)num_sms * 32 : g));
-    if (precision == EF_PREC_FP64) k_finalize<true><<<grid, 256, 0, st>>>(n, f);
-    else k_finalize<false><<<grid, 256, 0, st>>>(n, f);
+    if (precision == EF_PREC_FP64) k_finalize<true><<<grid_n(n, t), 256, 0, st>>>(n, f);
+    else k_finalize<false><<<grid_n(n, t), 256, 0, st>>>(n, f);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_finalize_sums(const ef_partials &p, int precision, int32_t n, int32_t frac_bits, const ef_outputs &out,
+                         const Tune &t, cudaStream_t st) {
+    if (precision == EF_PREC_FP64) k_finalize_sums<true><<<grid_n(n, t), 256, 0, st>>>(n, p, frac_bits, out);
+    else k_finalize_sums<false><<<grid_n(n, t), 256, 0, st>>>(n, p, frac_bits, out);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -133,7 +133,15 @@ struct Scratch {
     int32_t *hub_cidx;   // m+1    class index of each neighbour of a hub (at the hub's row positions)
 };
 
-enum : int { CNT_ERR = 32, CNT_MAXDEG = 33, CNT_BIGITEM = 34, CNT_HUB = 36, CNT_TRIFRAC = 37, NUM_COUNTERS = 64 };
+enum : int {
+    CNT_ERR = 32,
+    CNT_MAXDEG = 33,
+    CNT_BIGITEM = 34,
+    CNT_HUB = 36,
+    CNT_TRIFRAC = 37,
+    CNT_RANGE = 40,   // 40, 41: a shard's node range [lo, hi)
+    NUM_COUNTERS = 64
+};
 
 // Bytes of scratch for a graph (f tables excluded), and its layout when base != nullptr.
 size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s);
@@ -294,7 +302,8 @@ int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, i
 int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int wedge_mode,
                      int32_t n, int64_t m, const Tune &t, cudaStream_t st);
 int launch_out_hash(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st);
-int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st);
+int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st,
+                     const int32_t *owner_range = nullptr);
 int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs &out, const Tune &t,
                     cudaStream_t st);
 // learned path (ef_mlp.cu, ef_rank.cu)
@@ -310,6 +319,15 @@ int launch_features(const Scratch &s, const RankScratch &r, int32_t n, int mode,
 int launch_select_top(const RankScratch &r, int32_t n, int64_t k, int bits, const Tune &t, cudaStream_t st);
 int launch_bin_nodes(const int32_t *list, int32_t k, const int32_t *kptr, const int32_t *rp, const int32_t *ci,
                      const Scratch &s, int32_t *mark, int32_t n, const Tune &t, cudaStream_t st);
+int launch_bin_marked(const int32_t *mark, const Scratch &s, int32_t n, const Tune &t, cudaStream_t st);
+// shards (ef_shard.cu; the partials' finalize in ef_final.cu)
+int launch_shard_range(const int32_t *rp, int32_t n, int64_t m, int32_t shard, int32_t nshards, int32_t *range,
+                       cudaStream_t st);
+int launch_mark_range(const int32_t *range, int32_t n, int32_t *mark, const Tune &t, cudaStream_t st);
+int launch_shard_out(const int32_t *range, const Scratch &s, int precision, int32_t n, const ef_partials &out,
+                     const Tune &t, cudaStream_t st);
+int launch_finalize_sums(const ef_partials &p, int precision, int32_t n, int32_t frac_bits, const ef_outputs &out,
+                         const Tune &t, cudaStream_t st);
 int launch_nodes_exact(const int32_t *rp, const int32_t *ci, const Scratch &s, const int32_t *list, int32_t k,
                        const int32_t *kptr, int32_t n, int precision, bool global_tri, const ef_outputs &out,
                        const Tune &t, cudaStream_t st);

@@ -359,6 +359,16 @@ int launch_bin_nodes(const int32_t *list, int32_t k, const int32_t *kptr, const 
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// Work bins of the marked nodes only (mark filled by the caller).
+int launch_bin_marked(const int32_t *mark, const Scratch &s, int32_t n, const Tune &t, cudaStream_t st) {
+    if (cudaMemsetAsync(s.counters, 0, NUM_BINS * sizeof(int32_t), st) != cudaSuccess) return -1;
+    if (cudaMemsetAsync(s.counters + CNT_BIGITEM, 0, (CNT_HUB - CNT_BIGITEM + 1) * sizeof(int32_t), st) !=
+        cudaSuccess)
+        return -1;
+    k_bin_marked<<<t.grid((int64_t)n, 256), 256, 0, st>>>(mark, s.D, n, t.hub_min, s.bins, s.counters);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 constexpr int NODE_THREADS = 256;
 constexpr int NODE_ROW_SMEM = 4096;   // rows up to this length are staged for the triangle tests
 

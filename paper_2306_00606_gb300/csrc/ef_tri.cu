@@ -39,6 +39,10 @@
 // Corrections and counts go to per-node accumulators (qacc, tcnt) by L2
 // reductions: c's at once, b's once per unit, a's merged per lane over
 // consecutive units of the same owner.
+//
+// A shard of the pass lists the triangles whose lowest-ranked node lies in
+// its node range (a node id range: the oriented layout's list order comes
+// from atomics and differs between calls, node ids and ranks do not).
 #include "ef_internal.cuh"
 
 namespace ef {
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
     const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_D,
     const int2 *__restrict__ out_rng, const int32_t *__restrict__ out_src, const int32_t *__restrict__ out_hash,
     int64_t hash_cap, const int32_t *__restrict__ outdeg, const int32_t *__restrict__ D, int32_t n,
-    const int64_t *__restrict__ tq,
+    const int32_t *__restrict__ owner_range, const int64_t *__restrict__ tq,
     int64_t *__restrict__ qacc, int64_t *__restrict__ tcnt) {
     __shared__ int s_ex[TRI_WARPS][32];   // exclusive prefix of unit counts
     __shared__ int s_kend[TRI_WARPS][32], s_b[TRI_WARPS][32], s_Db[TRI_WARPS][32], s_bs[TRI_WARPS][32];
@@ -179,13 +183,15 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t total = out_ptr[n];
     const int64_t stride = (int64_t)gridDim.x * TRI_WARPS * 32;
+    // owners a in [a_lo, a_hi) open their pairs (all nodes, or one shard's range)
+    const int a_lo = owner_range ? owner_range[0] : 0, a_hi = owner_range ? owner_range[1] : n;
     for (int64_t K0 = ((int64_t)blockIdx.x * TRI_WARPS + w) * 32; K0 < total; K0 += stride) {
         const int64_t k = K0 + lane;
         int nu = 0;
         if (k < total) {
             const int a = out_src[k];
             const int kend = out_ptr[a] + outdeg[a];
-            const int np = kend - (int)k - 1;
+            const int np = a >= a_lo && a < a_hi ? kend - (int)k - 1 : 0;
             if (np > 0) {
                 const int b = out_col[k];
                 const int Db = out_D[k];
@@ -307,15 +313,16 @@ int launch_out_hash(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaS
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st) {
+int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st,
+                     const int32_t *owner_range) {
     const unsigned grid = grid_of(m / 2, TRI_WARPS * 32, (int64_t)t.num_sms * 16);
     if (t.tri_variant == 1)
         k_tri_pairs<4, 3><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_rng, s.out_src,
-                                                            s.out_hash, hash_slots(m), s.outdeg, s.D, n, s.tq, s.qacc,
+                                                            s.out_hash, hash_slots(m), s.outdeg, s.D, n, owner_range, s.tq, s.qacc,
                                                             s.tcnt);
     else
         k_tri_pairs<2, 4><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_rng, s.out_src,
-                                                            s.out_hash, hash_slots(m), s.outdeg, s.D, n, s.tq, s.qacc,
+                                                            s.out_hash, hash_slots(m), s.outdeg, s.D, n, owner_range, s.tq, s.qacc,
                                                             s.tcnt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
