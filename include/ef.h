@@ -364,7 +364,7 @@ int ef_surrogate_rank(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const 
  *   stream has finished this call's work.  Input is validated.
  * Scratch lives in a fixed 32 MiB device array inside the library, held by
  * every GPU that loads it until the process exits.  Graphs whose scratch
- * would exceed it (about 188 n + 44 m + 48 min(n, m) bytes) are rejected with
+ * would exceed it (about 172 n + 44 m + 48 min(n, m) bytes) are rejected with
  * EF_ERR_ARG and a message naming the limit; nothing runs on the GPU then.
  * The first call on a device looks up the array's address (make it before
  * any stream capture).  All calls share the array: calls that overlap on the

@@ -5,15 +5,13 @@
 // Pass order (one graph or one batch, all on the context stream):
 //   part A   one memset of the per-node accumulators and the counters;
 //            degrees + row_ptr checks + wedge bins; per-row checks,
-//            sigma1/sigma2, out-degrees, symmetry fingerprints; (batched)
-//            the check that no entry leaves its graph
-//   host     one small readback: validation word and max degree
-//            (skipped with trust_input)
+//            sigma1/sigma2, out-degrees, the symmetry sum; (batched) the
+//            check that no entry leaves its graph
+//   host     one small readback: validation word, symmetry sum and max
+//            degree (skipped with trust_input); part B runs on valid input only
 //   part B   f table (f(d) = d ln d and the triangle corrections, d < 3 maxdeg + 1);
 //            orientation (oriented CSR + omega); wedge pass (small, then mid +
 //            hub middle nodes); hash tables and pair tests; finalize (per node)
-//   host     final readback of the validation word (asymmetric input is
-//            only detected by the finalize pass)
 // The wedge pass and the orientation + triangle passes write disjoint
 // accumulators and could run on two streams; measured on the 4M-node
 // power-law graph, the concurrent form was slower (the triangle pass more
@@ -271,7 +269,7 @@ int compute_device(ef_ctx *ctx, const Job &j) {
         if (rc) return rc;
         CU(cudaMemcpyAsync(ctx->h_counters, s.counters, NUM_COUNTERS * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
-        if (ctx->h_counters[CNT_ERR]) return graph_error(ctx, ctx->h_counters[CNT_ERR]);
+        if (const int bits = prep_error_bits(ctx->h_counters)) return graph_error(ctx, bits);
         fcap = 3 * (int64_t)ctx->h_counters[CNT_MAXDEG] + 1;
     }
     // f table (double) followed by the fixed-point triangle corrections (int64)
@@ -319,9 +317,6 @@ int compute_device(ef_ctx *ctx, const Job &j) {
         if (rc) return rc;
         if (prof) CU(cudaEventRecord(ctx->ev[7], st));
     }
-    if (!o.trust_input)
-        CU(cudaMemcpyAsync(ctx->h_counters + CNT_ERR, s.counters + CNT_ERR, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                           st));
     return EF_OK;
 }
 
@@ -400,7 +395,6 @@ int run_job(ef_ctx *ctx, Job j, const ef_outputs *host_out) {
     if (!j.o.async) {
         CU(cudaStreamSynchronize(ctx->stream));
         if (j.o.profile) accumulate_stats(ctx, j.goff_dev != nullptr);
-        if (!j.o.trust_input && ctx->h_counters[ef::CNT_ERR]) return graph_error(ctx, ctx->h_counters[ef::CNT_ERR]);
     }
     CU(cudaGetLastError());
     return EF_OK;
@@ -480,7 +474,7 @@ int prepare_graph(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, 
         CU(cudaMemcpyAsync(ctx->h_counters, s.counters, NUM_COUNTERS * sizeof(int32_t), cudaMemcpyDeviceToHost,
                            ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
-        if (ctx->h_counters[CNT_ERR]) return graph_error(ctx, ctx->h_counters[CNT_ERR]);
+        if (const int bits = prep_error_bits(ctx->h_counters)) return graph_error(ctx, bits);
         fcap = 3 * (int64_t)ctx->h_counters[CNT_MAXDEG] + 1;
     }
     size_t have = (size_t)ctx->ftab_cap * 2 * sizeof(double);
@@ -624,7 +618,6 @@ size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s) {
     s.sig2 = (int64_t *)take(8 * N);
     s.omega = (int64_t *)take(8 * N);
     s.outdeg = (int32_t *)take(4 * N);
-    s.fp_row = (uint64_t *)take(8 * N);
     s.out_ptr = (int32_t *)take(4 * (N + 1));
     s.lay_node = (int32_t *)take(4 * N);
     s.lay_ptr = (int32_t *)take(4 * (N + 1));
@@ -640,7 +633,6 @@ size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s) {
     s.Tacc = (double *)take(8 * N);
     s.qacc = (int64_t *)take(8 * N);
     s.tcnt = (int64_t *)take(8 * N);
-    s.fp_push = (uint64_t *)take(8 * N);
     s.counters = (int32_t *)take(4 * NUM_COUNTERS);
     s.bins = (int32_t *)take(4 * N * NUM_BINS);
     s.big_chunks = (int32_t *)take(4 * (N + 1));

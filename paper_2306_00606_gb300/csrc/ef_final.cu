@@ -14,8 +14,7 @@
 // with D = D_v, sigma1 = sum of neighbour degrees, sigma2 = sum of their
 // squares, omega = sum of the neighbours' sigma1.  Then
 //   EF(v) = -sum over credited clusters of (d/S) ln(d/S) = ln S - T/S,
-// with EF = 0 and flag = 1 when S = 0.  A node whose two symmetry
-// fingerprints differ marks the input as asymmetric (a graph error).
+// with EF = 0 and flag = 1 when S = 0.
 //
 // Precision: FP64 mode evaluates ln S - T/S in FP64.  FP32C evaluates it in
 // FP32 (absolute error a few 1e-6) except at nodes of degree > HUB_FP64_DEG,
@@ -54,7 +53,6 @@ __device__ __forceinline__ double ef_value(int64_t S, double T, bool wide) {
 struct FinalArgs {
     const int32_t *D;
     const int64_t *sig1, *sig2, *omega;
-    const uint64_t *fp_row, *fp_push;
     const double *Tacc;
     const void *Ccenter;
     const int64_t *qacc, *tcnt;
@@ -66,12 +64,10 @@ template <bool F64>
 __global__ void __launch_bounds__(256) k_finalize(int32_t n, FinalArgs f) {
     const int F = f.cnt[CNT_TRIFRAC];
     const double qscale = ldexp(1.0, -F);
-    int err = 0;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const int64_t d = f.D[v];
         const int64_t t = f.tcnt[v];
         const int64_t s1 = f.sig1[v], s2 = f.sig2[v], om = f.omega[v];
-        if (f.fp_row[v] != f.fp_push[v]) err |= ERRB_ASYM;
         const int64_t N = d * (d - 2) + s1;
         const int64_t S = d * (d - 1) * (d - 4) + 2 * (d - 1) * s1 + s2 - s1 + (d - 4) * (s1 - d) + om - d * d - 8 * t;
         const AccT<F64> cc = d >= 2 ? reinterpret_cast<const AccT<F64> *>(f.Ccenter)[v] : (AccT<F64>)0;
@@ -90,8 +86,6 @@ __global__ void __launch_bounds__(256) k_finalize(int32_t n, FinalArgs f) {
         if (o.triangles) o.triangles[v] = t;
         if (o.flag) o.flag[v] = fl;
     }
-    err = __reduce_or_sync(FULL, err);
-    if ((threadIdx.x & 31) == 0 && err) atomicOr(f.cnt + CNT_ERR, err);
 }
 
 // From the shards' summed partials: T_v = t + q 2^-F, S_v = S_open - 8 t_v.
@@ -125,8 +119,7 @@ static inline unsigned grid_n(int32_t n, const Tune &t) {
 
 int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs &out, const Tune &t,
                     cudaStream_t st) {
-    const FinalArgs f{s.D,    s.sig1,    s.sig2, s.omega, s.fp_row,   s.fp_push,
-                      s.Tacc, s.Ccenter, s.qacc, s.tcnt,  s.counters, out};
+    const FinalArgs f{s.D, s.sig1, s.sig2, s.omega, s.Tacc, s.Ccenter, s.qacc, s.tcnt, s.counters, out};
     if (precision == EF_PREC_FP64) k_finalize<true><<<grid_n(n, t), 256, 0, st>>>(n, f);
     else k_finalize<false><<<grid_n(n, t), 256, 0, st>>>(n, f);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -26,6 +26,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -104,8 +105,6 @@ struct Scratch {
     int64_t *sig2;       // n      sum of squared neighbour degrees
     int64_t *omega;      // n      sum of the neighbours' sigma1
     int32_t *outdeg;     // n      out-degree in (degree, id) order
-    uint64_t *fp_row;    // n      fingerprint of the lower-ranked neighbours, from the node's own row
-    uint64_t *fp_push;   // n      the same, pushed by those neighbours (symmetry check)
     int32_t *out_ptr;    // n+1    oriented CSR offsets (a list runs from out_ptr[v] for outdeg[v] entries;
                          //        out_ptr[n] = all entries); lists are stored in layout order
     int32_t *lay_node;   // n      layout order: the work bins concatenated (degree classes)
@@ -140,13 +139,22 @@ enum : int {
     CNT_HUB = 36,
     CNT_TRIFRAC = 37,
     CNT_RANGE = 40,   // 40, 41: a shard's node range [lo, hi)
+    CNT_SYM = 44,     // 44, 45: the symmetry sum (uint64, 8-byte aligned)
     NUM_COUNTERS = 64
 };
+
+// Validation bits of a host copy of the counters after the row passes: the
+// device's error word, and asymmetry when the symmetry sum is not 0.
+inline int prep_error_bits(const int32_t *h) {
+    uint64_t sym;
+    memcpy(&sym, h + CNT_SYM, sizeof sym);
+    return h[CNT_ERR] | (sym ? ERRB_ASYM : 0);
+}
 
 // Bytes of scratch for a graph (f tables excluded), and its layout when base != nullptr.
 size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s);
 // Bytes from Tacc to the end of the counters: everything that must start at
-// zero (Tacc, qacc, tcnt, fp_push, counters), for one memset per call.
+// zero (Tacc, qacc, tcnt, counters), for one memset per call.
 size_t accumulator_bytes(const Scratch &s);
 
 // ----------------------------------------------------------------- helpers
@@ -155,13 +163,28 @@ __device__ __forceinline__ bool rank_less(int32_t Dx, int32_t x, int32_t Dy, int
     return Dx < Dy || (Dx == Dy && x < y);
 }
 
-// 64-bit fingerprint of a node id (a splitmix64 finaliser) for the symmetry
-// check; the added odd constant makes the sums count their terms too.
-__device__ __forceinline__ uint64_t node_print(int32_t x) {
-    uint64_t z = (uint64_t)(uint32_t)x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return (z ^ (z >> 31)) + 0x9E3779B97F4A7C15ull;
+// Symmetry check: every stored entry (v, x) adds
+//   edge_print(v, x) = a_v b_x - a_x b_v   (mod 2^64)
+// to one global sum, with a = a 32-bit mix of the node id (the MurmurHash3
+// finaliser) and b = a * odd + c (mod 2^32), multiplied as 64-bit products.
+// The term is antisymmetric, so in a symmetric CSR each entry's reverse
+// cancels it and the sum is 0; the terms of entries without their reverse
+// are pseudo-random 64-bit values that cancel only by accident (rows are
+// strictly ascending, so no entry repeats).
+struct NodeMix {
+    uint32_t a, b;
+};
+__device__ __forceinline__ NodeMix node_mix(int32_t x) {
+    uint32_t h = (uint32_t)x;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return NodeMix{h, h * 0x9E3779B1u + 0x7F4A7C15u};
+}
+__device__ __forceinline__ uint64_t edge_print(NodeMix v, NodeMix x) {
+    return (uint64_t)v.a * x.b - (uint64_t)x.a * v.b;
 }
 
 template <typename T>

@@ -1,5 +1,5 @@
-// Preparation passes of libef: CSR validation (with the symmetry
-// fingerprints), degrees and work bins, neighbour-degree sums, degree
+// Preparation passes of libef: CSR validation (with the symmetry sum),
+// degrees and work bins, neighbour-degree sums, degree
 // orientation for triangle listing, the f(d) = d ln d table, and a
 // device-wide exclusive scan.
 //
@@ -150,21 +150,15 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
 // Range, self-loop and strict-order checks; sigma1 = sum of neighbour degrees,
 // sigma2 = sum of their squares, and the out-degree in (degree, id) order.
 //
-// Symmetry check by fingerprints: for every entry x of N(v), the lower-ranked
-// end of {v, x} is pushed to the higher one, fp_push[hi] += print(lo), and
-// every row sums print(x) over its lower-ranked entries into fp_row.  In a
-// symmetric CSR both sums run over the same multiset at every node.  An
-// entry (v, x) without its reverse adds print(v) to one side of x (v lower)
-// or print(x) to one side of v (x lower) only; the finalize pass reports the
-// graph as asymmetric where the two differ.  A miss needs the unmatched
-// 64-bit prints to cancel exactly (probability about 2^-64 per node).
+// Symmetry check: every entry adds edge_print(v, x) to a per-thread sum,
+// reduced per warp into the global symmetry sum (counters[CNT_SYM]), which
+// is 0 for a symmetric CSR; the host reads it with the validation word.
 struct RowStats {
     int64_t s1 = 0, s2 = 0;
-    uint64_t fpr = 0;
+    uint64_t sym = 0;
     int od = 0, err = 0;
     __device__ __forceinline__ void entry(const int32_t *__restrict__ ci, const int32_t *__restrict__ D, int32_t n,
-                                          int v, int Dv, int a, int e, uint64_t pv,
-                                          uint64_t *__restrict__ fp_push) {
+                                          int v, int Dv, int a, int e, NodeMix mv) {
         const int x = ci[e];
         if (x < 0 || x >= n) { err |= ERRB_RANGE; return; }
         if (x == v) err |= ERRB_SELFLOOP;
@@ -172,17 +166,14 @@ struct RowStats {
         const int Dx = D[x];
         s1 += Dx;
         s2 += (int64_t)Dx * Dx;
-        if (rank_less(Dv, v, Dx, x)) {
-            ++od;
-            atomicAdd((unsigned long long *)(fp_push + x), (unsigned long long)pv);
-        } else {
-            fpr += node_print(x);
-        }
+        od += rank_less(Dv, v, Dx, x);
+        sym += edge_print(mv, node_mix(x));
     }
     // A whole short row by one thread, four entries at a time: their loads
     // are issued together, so four dependent chains are in flight.
     __device__ __forceinline__ void row(const int32_t *__restrict__ ci, const int32_t *__restrict__ D, int32_t n,
-                                        int v, int Dv, int a, int b, uint64_t pv, uint64_t *__restrict__ fp_push) {
+                                        int v, int Dv, int a, int b) {
+        const NodeMix mv = node_mix(v);
         int prev = 0;
         for (int e0 = a; e0 < b; e0 += 4) {
             int x[4], Dx[4];
@@ -205,12 +196,8 @@ struct RowStats {
                     if (later && before >= xq) err |= ERRB_UNSORTED;
                     s1 += Dx[q];
                     s2 += (int64_t)Dx[q] * Dx[q];
-                    if (rank_less(Dv, v, Dx[q], xq)) {
-                        ++od;
-                        atomicAdd((unsigned long long *)(fp_push + xq), (unsigned long long)pv);
-                    } else {
-                        fpr += node_print(xq);
-                    }
+                    od += rank_less(Dv, v, Dx[q], xq);
+                    sym += edge_print(mv, node_mix(xq));
                 }
             }
         }
@@ -220,14 +207,20 @@ struct RowStats {
 struct RowOut {
     int64_t *sig1, *sig2;
     int32_t *outdeg;
-    uint64_t *fp_row, *fp_push;
 };
+
+__device__ __forceinline__ void add_sym(int32_t *cnt, uint64_t sym) {
+    sym = warp_sum(sym);
+    if ((threadIdx.x & 31) == 0 && sym)
+        atomicAdd(reinterpret_cast<unsigned long long *>(cnt + CNT_SYM), (unsigned long long)sym);
+}
 
 __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
                             int tmax, int hub_min, const int32_t *__restrict__ D, RowOut ro,
                             int32_t *__restrict__ cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    uint64_t sym = 0;
     for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
          base += nwarps * 32) {
         const int v = (int)(base + lane);
@@ -237,12 +230,11 @@ __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__res
         const int Dv = ok ? b - a : 0;
         if (in && Dv <= tmax) {
             RowStats r;
-            const uint64_t pv = node_print(v);
-            if (ok) r.row(ci, D, n, v, Dv, a, b, pv, ro.fp_push);
+            if (ok) r.row(ci, D, n, v, Dv, a, b);
             ro.sig1[v] = r.s1;
             ro.sig2[v] = r.s2;
             ro.outdeg[v] = r.od;
-            ro.fp_row[v] = r.fpr;
+            sym += r.sym;
             if (r.err) atomicOr(cnt + CNT_ERR, r.err);
         }
         unsigned mid = __ballot_sync(FULL, Dv > tmax && Dv < hub_min);
@@ -251,22 +243,22 @@ __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__res
             mid &= mid - 1;
             const int u = (int)(base + j);
             const int ua = __shfl_sync(FULL, a, j), ub = __shfl_sync(FULL, b, j);
-            const uint64_t pu = node_print(u);
             RowStats r;
-            for (int e = ua + lane; e < ub; e += 32) r.entry(ci, D, n, u, ub - ua, ua, e, pu, ro.fp_push);
+            const NodeMix mu = node_mix(u);
+            for (int e = ua + lane; e < ub; e += 32) r.entry(ci, D, n, u, ub - ua, ua, e, mu);
             const int64_t s1 = warp_sum(r.s1), s2 = warp_sum(r.s2);
-            const uint64_t fpr = warp_sum(r.fpr);
             const int od = warp_sum(r.od);
             const int err = __reduce_or_sync(FULL, r.err);
+            sym += r.sym;
             if (lane == 0) {
                 ro.sig1[u] = s1;
                 ro.sig2[u] = s2;
                 ro.outdeg[u] = od;
-                ro.fp_row[u] = fpr;
                 if (err) atomicOr(cnt + CNT_ERR, err);
             }
         }
     }
+    add_sym(cnt, sym);
 }
 
 __global__ void __launch_bounds__(ROW_CTA) k_row_stats_hub(const int32_t *__restrict__ rp,
@@ -276,25 +268,26 @@ __global__ void __launch_bounds__(ROW_CTA) k_row_stats_hub(const int32_t *__rest
                                                            int32_t *__restrict__ cnt) {
     __shared__ int64_t s_buf[32];
     const int total = hub_total(cnt);
+    uint64_t sym = 0;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         const int u = hub_row(bins, n, cnt, it);
         const int a = rp[u], b = rp[u + 1];
-        const uint64_t pu = node_print(u);
         RowStats r;
-        for (int e = a + threadIdx.x; e < b; e += ROW_CTA) r.entry(ci, D, n, u, b - a, a, e, pu, ro.fp_push);
+        const NodeMix mu = node_mix(u);
+        for (int e = a + threadIdx.x; e < b; e += ROW_CTA) r.entry(ci, D, n, u, b - a, a, e, mu);
         const int64_t s1 = block_sum<int64_t>(r.s1, s_buf);
         const int64_t s2 = block_sum<int64_t>(r.s2, s_buf);
         const int64_t od = block_sum<int64_t>(r.od, s_buf);
-        const int64_t fpr = block_sum<int64_t>((int64_t)r.fpr, s_buf);   // wrapping sum
         const int err = __reduce_or_sync(FULL, r.err);
+        sym += r.sym;
         if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
         if (threadIdx.x == 0) {
             ro.sig1[u] = s1;
             ro.sig2[u] = s2;
             ro.outdeg[u] = (int32_t)od;
-            ro.fp_row[u] = (uint64_t)fpr;
         }
     }
+    add_sym(cnt, sym);
 }
 
 // ------------------------------------------------------------- orientation
@@ -630,7 +623,7 @@ static inline unsigned grid_for(int64_t work, int per_block, int64_t cap) {
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
                   cudaStream_t st) {
     k_degrees<<<grid_for(n, 1024, 1 << 30), 1024, 0, st>>>(rp, n, m, t.hub_min, s.D, s.bins, s.counters);
-    const RowOut ro{s.sig1, s.sig2, s.outdeg, s.fp_row, s.fp_push};
+    const RowOut ro{s.sig1, s.sig2, s.outdeg};
     k_row_stats<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, ci, n, m, t.row_thread_max, t.hub_min, s.D, ro,
                                                          s.counters);
     k_row_stats_hub<<<t.num_sms * 4, ROW_CTA, 0, st>>>(rp, ci, n, s.D, s.bins, ro, s.counters);

@@ -136,17 +136,13 @@ int launch_omega_mm(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, 
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// The 16 features of every node (in the order of the oracle's FEATURE_NAMES);
-// also the symmetry check of the fingerprints.  mode 1 uses the triangle
-// counts tcnt, mode 0 takes t = 0.
+// The 16 features of every node (in the order of the oracle's FEATURE_NAMES).
+// mode 1 uses the triangle counts tcnt, mode 0 takes t = 0.
 __global__ void k_features(int32_t n, int mode, const int32_t *__restrict__ D, const int64_t *__restrict__ sig1,
                            const int64_t *__restrict__ sig2, const int64_t *__restrict__ omega,
                            const int32_t *__restrict__ nmin, const int32_t *__restrict__ nmax,
-                           const int64_t *__restrict__ tcnt, const uint64_t *__restrict__ fp_row,
-                           const uint64_t *__restrict__ fp_push, float *__restrict__ X, int32_t *__restrict__ cnt) {
-    int err = 0;
+                           const int64_t *__restrict__ tcnt, float *__restrict__ X) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        if (fp_row[v] != fp_push[v]) err |= ERRB_ASYM;
         const int64_t d = D[v], s1 = sig1[v], s2 = sig2[v], om = omega[v];
         const int64_t t = mode ? tcnt[v] : 0;
         const float fd = (float)d;
@@ -179,13 +175,11 @@ __global__ void k_features(int32_t n, int mode, const int32_t *__restrict__ D, c
 #pragma unroll
         for (int q = 0; q < 4; ++q) dst[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
     }
-    err = __reduce_or_sync(FULL, err);
-    if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
 }
 
 int launch_features(const Scratch &s, const RankScratch &r, int32_t n, int mode, const Tune &t, cudaStream_t st) {
     k_features<<<t.grid((int64_t)n, 256), 256, 0, st>>>(n, mode, s.D, s.sig1, s.sig2, s.omega, r.nbr_min, r.nbr_max,
-                                                         s.tcnt, s.fp_row, s.fp_push, r.x, s.counters);
+                                                         s.tcnt, r.x);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -49,13 +49,11 @@ __global__ void k_mark_range(const int32_t *__restrict__ range, int32_t n, int32
 //   N_v      = D(D-2) + sigma1,
 //   S_open_v = D(D-1)(D-4) + 2(D-1) sigma1 + sigma2 - sigma1
 //              + (D-4)(sigma1 - D) + omega - D^2.
-// A node whose two symmetry fingerprints differ marks the input asymmetric.
 template <bool F64>
 __global__ void __launch_bounds__(256) k_shard_out(const int32_t *__restrict__ range, const Scratch s, int32_t n,
                                                    ef_partials p) {
     const int lo = range[0], hi = range[1];
     const AccT<F64> *cc = reinterpret_cast<const AccT<F64> *>(s.Ccenter);
-    int err = 0;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const bool own = v >= lo && v < hi;
         const int64_t d = s.D[v];
@@ -71,10 +69,7 @@ __global__ void __launch_bounds__(256) k_shard_out(const int32_t *__restrict__ r
         }
         p.n_clusters[v] = N;
         p.s_open[v] = S;
-        if (s.fp_row[v] != s.fp_push[v]) err |= ERRB_ASYM;
     }
-    err = __reduce_or_sync(FULL, err);
-    if ((threadIdx.x & 31) == 0 && err) atomicOr(s.counters + CNT_ERR, err);
 }
 
 static inline unsigned grid_n(int32_t n, const Tune &t) {

@@ -66,7 +66,7 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
         char msg[200];
         snprintf(msg, sizeof msg,
                  "ef_compute_static: graph needs %zu bytes of scratch, above the fixed %zu-byte maximum "
-                 "(about 188 n + 44 m + 48 min(n, m) bytes); use ef_compute_ex",
+                 "(about 172 n + 44 m + 48 min(n, m) bytes); use ef_compute_ex",
                  need, EF_STATIC_SCRATCH_BYTES);
         return fail(EF_ERR_ARG, msg);
     }
@@ -103,18 +103,15 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     if (cudaMemcpyAsync(h_cnt, s.counters, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: validation readback failed");
-    if (h_cnt[CNT_ERR]) return fail(EF_ERR_GRAPH, "ef_compute_static: input is not a symmetric simple sorted CSR");
+    if (prep_error_bits(h_cnt)) return fail(EF_ERR_GRAPH, "ef_compute_static: input is not a symmetric simple sorted CSR");
     ef_outputs out = {};
     out.ef = out_ef;
     if (launch_ftab(s.ftab, s.tq, s.counters, fcap, st) || launch_orient(rp, ci, n, m, s, t, st) ||
         launch_wedge_small(rp, ci, s, precision, n, t, st) || launch_wedge_big(rp, ci, s, precision, 0, n, m, t, st) ||
         launch_out_hash(s, n, m, t, st) || launch_tri_pairs(s, n, m, t, st) ||
-        launch_finalize(s, precision, n, out, t, st) ||
-        cudaMemcpyAsync(h_cnt, s.counters, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        launch_finalize(s, precision, n, out, t, st))
         return fail(EF_ERR_CUDA, "ef_compute_static: launch failed");
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: kernel execution failed");
-    // asymmetric input is only detected by the finalize pass
-    if (h_cnt[CNT_ERR]) return fail(EF_ERR_GRAPH, "ef_compute_static: input is not a symmetric simple sorted CSR");
     return EF_OK;
 }

@@ -219,7 +219,17 @@ def test_repeatable_fp64(ctx):
     np.testing.assert_allclose(a["ef"], b["ef"], rtol=1e-13, atol=1e-13)
 
 
-@pytest.mark.parametrize("bad", ["asym", "asym_extra", "asym_hub", "unsorted", "dup", "loop", "range", "rowptr"])
+def _insert_entries(rp, ci, entries):
+    """CSR with the (row, column) entries added, rows kept sorted."""
+    rows = [list(ci[rp[v]:rp[v + 1]]) for v in range(len(rp) - 1)]
+    for r, c in entries:
+        rows[r] = sorted(rows[r] + [c])
+    return (np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32),
+            np.concatenate(rows).astype(np.int32))
+
+
+@pytest.mark.parametrize("bad", ["asym", "asym_extra", "asym_hub", "asym_cycle", "unsorted", "dup", "loop", "range",
+                                 "rowptr"])
 def test_invalid_graphs_rejected(ctx, bad):
     import torch
     import paper_2306_00606_gb300 as ef
@@ -247,6 +257,14 @@ def test_invalid_graphs_rejected(ctx, bad):
         h = int(np.argmax(np.diff(rp)))
         ci = np.delete(ci, rp[h]).astype(np.int32)
         rp[h + 1:] -= 1
+    elif bad == "asym_cycle":
+        # entries u -> x -> w -> u in one direction only: every row gains one
+        # entry and every node appears once more as a column, so all row and
+        # column counts still agree
+        rows = [set(ci[rp[i]:rp[i + 1]].tolist()) for i in range(g.n)]
+        u, x, w = next((u, x, w) for u in range(g.n) for x in range(u + 1, g.n) for w in range(x + 1, g.n)
+                       if x not in rows[u] and w not in rows[x] and u not in rows[w])
+        rp, ci = _insert_entries(rp, ci, [(u, x), (x, w), (w, u)])
     elif bad == "unsorted":
         ci[a], ci[a + 1] = ci[a + 1], ci[a]
     elif bad == "dup":
