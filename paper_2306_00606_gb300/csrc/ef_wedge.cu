@@ -183,19 +183,30 @@ struct ClassEval<false> {
     static __device__ __forceinline__ Cls make(int b, int c) { return make_float2((float)b, (float)c); }
     static __device__ __forceinline__ float bval(Cls x) { return x.x; }
     static __device__ __forceinline__ float cval(Cls x) { return x.y; }
-    // returns R = (sum_j c_j f(base + b_i + b_j) - f(base + 2 b_i)) in natural-log units
+    // returns R = (sum_j c_j f(base + b_i + b_j) - f(base + 2 b_i)) in natural-log units.
+    // Chunks of CHUNK classes are summed in plain FP32 (every term is >= 0,
+    // so a chunk's rounding error is below CHUNK ulps of its sum) and the
+    // chunk sums with Kahan compensation: one FMA per class pair instead of
+    // a multiply and a four-operation compensated add.
+    static constexpr int CHUNK = 8;
     static __device__ __forceinline__ float row(const Cls *cls, int K, int base, Cls ci, const double *) {
         const float fb = (float)base + ci.x;
-        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+        float s = 0.f, c = 0.f;
         int j = 0;
-        for (; j + 2 <= K; j += 2) {
-            const float4 q = *reinterpret_cast<const float4 *>(cls + j);
-            kahan_add(s0, c0, q.y * dlog2d(fb + q.x));
-            kahan_add(s1, c1, q.w * dlog2d(fb + q.z));
+        for (; j + CHUNK <= K; j += CHUNK) {
+            float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < CHUNK; q += 2) {
+                const float4 v = *reinterpret_cast<const float4 *>(cls + j + q);
+                t0 = fmaf(v.y, dlog2d(fb + v.x), t0);
+                t1 = fmaf(v.w, dlog2d(fb + v.z), t1);
+            }
+            kahan_add(s, c, t0 + t1);
         }
-        if (j < K) kahan_add(s0, c0, cls[j].y * dlog2d(fb + cls[j].x));
-        const float sum = (s0 - c0) + (s1 - c1);
-        return (sum - dlog2d(fb + ci.x)) * (float)LN2;
+        float t = 0.f;
+        for (; j < K; ++j) t = fmaf(cls[j].y, dlog2d(fb + cls[j].x), t);
+        kahan_add(s, c, t);
+        return ((s - c) - dlog2d(fb + ci.x)) * (float)LN2;
     }
 };
 
