@@ -230,7 +230,9 @@ def cpu_baseline(g, seconds: float, seed: int = 0):
 def rmat_sweep(ctx, args, dev) -> list:
     """EF of R-MAT graphs with 2^16 nodes and M = 2..32 edges per node
     (a, b, c = 0.57, 0.19, 0.19; the paper's Figs. 3-4 setting, parameters
-    not printed there): ms per graph and clusters per ms."""
+    not printed there): ms per graph and clusters per ms on the GPU, and
+    the oracle's clusters per ms on the host cores (a node sample of about
+    2 s per graph)."""
     import torch
     import paper_2306_00606_gb300 as ef
     rows = []
@@ -251,8 +253,10 @@ def rmat_sweep(ctx, args, dev) -> list:
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / 10
         W = graph_stats(g)["W"]
+        cpu = cpu_baseline(g, 2.0, seed=M)
         rows.append({"M": M, "nodes": g.n, "nnz": g.nnz, "avg_degree": g.nnz / g.n, "clusters": W, "ms": ms,
-                     "clusters_per_ms": W / ms})
+                     "clusters_per_ms": W / ms, "oracle_clusters_per_ms": cpu["value"] / 1e3,
+                     "oracle_cores": cpu["cores"], "gpu_over_oracle": (W / ms) / (cpu["value"] / 1e3)})
     return rows
 
 

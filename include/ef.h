@@ -254,6 +254,72 @@ int ef_finalize_partials(ef_ctx *ctx, int32_t n, const ef_partials *sum,
                          ef_outputs *out);
 
 /* ------------------------------------------------------------------------
+ * SIR epidemic simulation (Section 3.1's model, Section 3.2's measurements),
+ * for checking how EF predicts a node's role in an epidemic.  Discrete,
+ * synchronous time steps t = 0, 1, ...:
+ *   - every node u infected at the start of step t tries once each
+ *     neighbour x that is susceptible then; the try succeeds when
+ *     R(sim, t, u, x) < floor(beta 2^32); x is infected at the end of the
+ *     step if any try succeeded, and its infector (parent) is the smallest
+ *     such u;
+ *   - u recovers at the end of step t when R(sim, t, u, 2^32 - 1) <
+ *     floor(gamma 2^32); immune nodes are never infected;
+ *   - a simulation ends at the first t with no infected node (its length).
+ * R is Philox4x32-10 (Salmon et al., SC 2011): counter (sim, t, u, x), key
+ * = seed, first output word, with sim = sim_base + the simulation's index.
+ * So a simulation's course depends on (seed, sim) only, and runs split
+ * across calls or devices reproduce one long run.
+ * Section 3.1 calibrates gamma = 1/3 and beta = 1.3 / (3 <k>).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    double beta;            /* infection probability per try, [0, 1] */
+    double gamma;           /* recovery probability per step, [0, 1] */
+    uint64_t seed;          /* Philox key */
+    int64_t sim_base;       /* id of simulation 0 of this call */
+    int32_t max_steps;      /* >= 1; simulations still active then stop
+                               there (length = max_steps, truncated = 1) */
+    int32_t depth;          /* spreading-power orders 1..depth (0..4) */
+    int32_t spread_min_size;/* only simulations whose final size is at
+                               least this add to spread and spread_sims
+                               (e.g. 25% of n: global outbreaks only) */
+    int32_t reserved;
+} ef_sir_params;
+
+/* Outputs (device arrays; any may be NULL).  B = number of simulations. */
+typedef struct {
+    int32_t *final_size;    /* [B] nodes ever infected, index case included */
+    int32_t *length;        /* [B] steps until no node is infected */
+    int32_t *peak_infected; /* [B] most nodes infected at the start of a step */
+    int32_t *peak_step;     /* [B] first step with that many */
+    uint8_t *truncated;     /* [B] 1: still active after max_steps */
+    int32_t *parent;        /* [B][n] infection tree: -1 never infected, the
+                               index case is its own parent */
+    int64_t *spread;        /* [depth][n] sum over the selected simulations
+                               of the spreading power of order k: the nodes
+                               of v's infection subtree within k generations
+                               below v (v not counted) */
+    int64_t *spread_sims;   /* [n] selected simulations in which v was
+                               infected */
+} ef_sir_outputs;
+
+/*
+ * Run num_sims simulations on graph g (device CSR, validated as in
+ * ef_compute_ex unless opt->trust_input).
+ *   index_cases: int32[num_sims] (device) start nodes;
+ *   immune: uint8[num_immune_sets][n] (device, 1 = immune) or NULL, and
+ *   immune_set: int32[num_sims] (device) the set of each simulation (-1:
+ *   none) or NULL.
+ * An index case outside [0, n) or immune, or a set index >= num_immune_sets,
+ * gives EF_ERR_ARG before any step runs.  Device memory: about 25 bytes per
+ * (simulation, node) pair.  host_io and async give EF_ERR_ARG.
+ */
+int ef_sir_run(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
+               const int32_t *index_cases, int32_t num_sims,
+               const uint8_t *immune, int32_t num_immune_sets,
+               const int32_t *immune_set, const ef_sir_params *params,
+               const ef_options *opt, ef_sir_outputs *out);
+
+/* ------------------------------------------------------------------------
  * Learned ranking path.  A regression network 16-64-64-1 (ReLU, BF16
  * tensor-core products with FP32 accumulation) maps 16 cheap per-node
  * features to a predicted EF.  It is trained on exact EF produced by this

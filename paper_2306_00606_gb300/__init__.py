@@ -29,7 +29,7 @@ EXPORTED = ("ef_ctx_create", "ef_ctx_destroy", "ef_last_error", "ef_sync", "ef_g
             "ef_compute_nodes", "ef_features", "ef_model_create", "ef_model_destroy", "ef_model_get", "ef_model_set",
             "ef_model_feature_mode", "ef_model_save", "ef_model_load", "ef_mlp_forward", "ef_mlp_grad",
             "ef_surrogate_train", "ef_surrogate_rank", "ef_compute_static", "ef_compute_shard",
-            "ef_finalize_partials")
+            "ef_finalize_partials", "ef_sir_run")
 MODEL_PARAMS = 5313
 MODEL_FLOATS = MODEL_PARAMS + 32
 
@@ -61,6 +61,18 @@ class ef_partials(ctypes.Structure):
 
 
 PARTIALS = ("t", "q", "triangles", "n_clusters", "s_open")   # float64, then int64 x4
+
+
+class ef_sir_params(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("sim_base", ctypes.c_int64), ("max_steps", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("spread_min_size", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ef_sir_outputs(ctypes.Structure):
+    _fields_ = [("final_size", ctypes.c_void_p), ("length", ctypes.c_void_p), ("peak_infected", ctypes.c_void_p),
+                ("peak_step", ctypes.c_void_p), ("truncated", ctypes.c_void_p), ("parent", ctypes.c_void_p),
+                ("spread", ctypes.c_void_p), ("spread_sims", ctypes.c_void_p)]
 
 
 class ef_stats(ctypes.Structure):
@@ -155,6 +167,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_int32)]
     lib.ef_finalize_partials.argtypes = [vp, i32, ctypes.POINTER(ef_partials), i32, ctypes.POINTER(ef_options),
                                          ctypes.POINTER(ef_outputs)]
+    lib.ef_sir_run.argtypes = [vp, ctypes.POINTER(ef_csr), i32, i64, vp, i32, vp, i32, vp,
+                               ctypes.POINTER(ef_sir_params), ctypes.POINTER(ef_options), ctypes.POINTER(ef_sir_outputs)]
     for name in EXPORTED:
         if name != "ef_last_error":
             getattr(lib, name).restype = ctypes.c_int
@@ -354,6 +368,30 @@ def compute_sharded(ctx: int, row_ptr, col_idx, rank: int, world: int, *, group=
     return res
 
 
+SIR_OUTPUTS = ("final_size", "length", "peak_infected", "peak_step", "truncated", "parent", "spread",
+               "spread_sims")
+
+
+def ef_sir_run(ctx: int, row_ptr, col_idx, index_cases, *, beta: float, gamma: float, seed: int, sim_base: int = 0,
+               max_steps: int = 100000, depth: int = 4, spread_min_size: int = 0, immune=None, immune_set=None,
+               trust_input: bool = False, **outputs) -> None:
+    """SIR simulations from the given index cases (device tensors); writes the
+    ef_sir_outputs members passed by name (device tensors)."""
+    n = int(row_ptr.shape[0]) - 1
+    g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
+    o = _options("fp64", trust_input, False, False, False, 0, False)
+    p = ef_sir_params(float(beta), float(gamma), int(seed) & (2 ** 64 - 1), int(sim_base), int(max_steps), int(depth),
+                      int(spread_min_size), 0)
+    bad = set(outputs) - set(SIR_OUTPUTS)
+    if bad:
+        raise TypeError(f"unknown SIR outputs {sorted(bad)}")
+    out = ef_sir_outputs(*(_ptr(outputs.get(k)) for k in SIR_OUTPUTS))
+    nsets = 0 if immune is None else int(immune.shape[0])
+    _check(load_library().ef_sir_run(ctx, ctypes.byref(g), n, int(col_idx.shape[0]), _ptr(index_cases),
+                                     int(index_cases.shape[0]), _ptr(immune), nsets, _ptr(immune_set),
+                                     ctypes.byref(p), ctypes.byref(o), ctypes.byref(out)), ctx)
+
+
 def ef_features(ctx: int, row_ptr, col_idx, x, *, mode: int = 0, trust_input: bool = False) -> None:
     """The 16 learned-path features of every node into x (device float32 [n, 16])."""
     n = int(row_ptr.shape[0]) - 1
@@ -525,3 +563,18 @@ class Context:
 
     def stats(self, reset: bool = False) -> dict:
         return ef_get_stats(self.handle, reset)
+
+    def sir(self, row_ptr, col_idx, index_cases, *, outputs=("final_size", "length", "peak_infected", "peak_step"),
+            depth: int = 4, **kw) -> dict:
+        """Allocate the requested SIR outputs on the device and run ef_sir_run."""
+        import torch
+        n = int(row_ptr.shape[0]) - 1
+        B = int(index_cases.shape[0])
+        dev = torch.device("cuda", self.device)
+        shape = dict(final_size=(B,), length=(B,), peak_infected=(B,), peak_step=(B,), truncated=(B,),
+                     parent=(B, n), spread=(depth, n), spread_sims=(n,))
+        dt = dict(final_size=torch.int32, length=torch.int32, peak_infected=torch.int32, peak_step=torch.int32,
+                  truncated=torch.uint8, parent=torch.int32, spread=torch.int64, spread_sims=torch.int64)
+        res = {k: torch.empty(shape[k], dtype=dt[k], device=dev) for k in outputs}
+        ef_sir_run(self.handle, row_ptr, col_idx, index_cases, depth=depth, **kw, **res)
+        return res

@@ -75,6 +75,8 @@ struct ef_ctx {
     void *acts = nullptr;            // training activations
     size_t acts_bytes = 0;
     double *dtmp = nullptr;          // small device scratch (feature sums)
+    void *sir = nullptr;             // SIR simulation state
+    size_t sir_bytes = 0;
 };
 
 struct ef_model {
@@ -698,6 +700,7 @@ int ef_ctx_destroy(ef_ctx *ctx) {
     cudaFree(ctx->rank);
     cudaFree(ctx->acts);
     cudaFree(ctx->dtmp);
+    cudaFree(ctx->sir);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     for (int i = 0; i < 10; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
@@ -952,6 +955,113 @@ int ef_finalize_partials(ef_ctx *ctx, int32_t n, const ef_partials *sum, int32_t
     DeviceGuard dg(ctx->device);
     LAUNCH(launch_finalize_sums(*sum, o.precision, n, frac_bits, *out, ctx->tune, ctx->stream), "finalize");
     CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaGetLastError());
+    return EF_OK;
+}
+
+// Steps between two host checks of whether any simulation is still running.
+constexpr int SIR_CHECK = 16;
+
+int ef_sir_run(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const int32_t *index_cases, int32_t num_sims,
+               const uint8_t *immune, int32_t num_immune_sets, const int32_t *immune_set,
+               const ef_sir_params *params, const ef_options *opt, ef_sir_outputs *out) {
+    using namespace ef;
+    if (!ctx) { set_err(nullptr, "null context"); return EF_ERR_ARG; }
+    ef_options o = {};
+    if (opt) o = *opt;
+    const ef_outputs none = {};
+    int rc = check_args(ctx, g, n, m, o, &none);
+    if (rc) return rc;
+    rc = check_learned_opts(ctx, o);
+    if (rc) return rc;
+    if (!params || !out) { set_err(ctx, "null parameters or outputs"); return EF_ERR_ARG; }
+    const ef_sir_params p = *params;
+    if (num_sims < 0 || (num_sims > 0 && !index_cases)) { set_err(ctx, "bad simulation list"); return EF_ERR_ARG; }
+    if (!(p.beta >= 0.0 && p.beta <= 1.0) || !(p.gamma >= 0.0 && p.gamma <= 1.0)) {
+        set_err(ctx, "beta %g or gamma %g outside [0, 1]", p.beta, p.gamma);
+        return EF_ERR_ARG;
+    }
+    if (p.max_steps < 1 || p.depth < 0 || p.depth > 4) {
+        set_err(ctx, "max_steps %d < 1 or depth %d outside 0..4", p.max_steps, p.depth);
+        return EF_ERR_ARG;
+    }
+    if (num_immune_sets < 0 || (num_immune_sets > 0 && !immune)) { set_err(ctx, "bad immune sets"); return EF_ERR_ARG; }
+    if (out->spread && p.depth == 0) { set_err(ctx, "spread requested with depth 0"); return EF_ERR_ARG; }
+    ctx->err[0] = 0;
+    if (num_sims == 0) return EF_OK;
+    if (n == 0) { set_err(ctx, "index cases given for an empty graph"); return EF_ERR_ARG; }
+    DeviceGuard dg(ctx->device);
+    Scratch s;
+    int64_t fcap;
+    rc = prepare_graph(ctx, g->row_ptr, g->col_idx, n, m, o, s, fcap);
+    if (rc) return rc;
+    const int32_t B = num_sims;
+    const size_t BN = (size_t)B * (size_t)n;
+    // state buffer
+    size_t off = 0;
+    auto place = [&](size_t bytes) { size_t o_ = off; off += al(bytes); return o_; };
+    const size_t o_status = place(BN), o_parent = out->parent ? 0 : place(4 * BN), o_cand = place(4 * BN),
+                 o_l0 = place(8 * BN), o_l1 = place(8 * BN), o_lc = place(16), o_act = place(16),
+                 o_cnt = place(4 * (size_t)B), o_peak = place(4 * (size_t)B), o_pstep = place(4 * (size_t)B),
+                 o_len = place(4 * (size_t)B), o_fs = place(4 * (size_t)B), o_done = place((size_t)B),
+                 o_err = place(4);
+    rc = ensure_buffer(ctx, &ctx->sir, &ctx->sir_bytes, off, 0);
+    if (rc) return rc;
+    char *b = (char *)ctx->sir;
+    SirState st;
+    st.status = (uint8_t *)(b + o_status);
+    st.parent = out->parent ? out->parent : (int32_t *)(b + o_parent);
+    st.cand = (int32_t *)(b + o_cand);
+    st.list[0] = (uint64_t *)(b + o_l0);
+    st.list[1] = (uint64_t *)(b + o_l1);
+    st.list_count = (int64_t *)(b + o_lc);
+    int64_t *active = (int64_t *)(b + o_act);
+    st.count = (int32_t *)(b + o_cnt);
+    st.peak = (int32_t *)(b + o_peak);
+    st.peak_step = (int32_t *)(b + o_pstep);
+    st.length = (int32_t *)(b + o_len);
+    st.fsize = (int32_t *)(b + o_fs);
+    st.done = (uint8_t *)(b + o_done);
+    st.err = (int32_t *)(b + o_err);
+    cudaStream_t cs = ctx->stream;
+    const Tune &t = ctx->tune;
+    const int64_t h_init[4] = {B, 0, 0, 0};   // list lengths {B, 0}, active counts {0, 0}
+    CU(cudaMemcpyAsync(st.list_count, h_init, sizeof h_init, cudaMemcpyHostToDevice, cs));
+    CU(cudaMemsetAsync(st.err, 0, sizeof(int32_t), cs));
+    LAUNCH(launch_sir_init(index_cases, B, n, immune, num_immune_sets, immune_set, st, t, cs), "SIR init");
+    CU(cudaMemcpyAsync(ctx->h_counters, st.err, sizeof(int32_t), cudaMemcpyDeviceToHost, cs));
+    CU(cudaStreamSynchronize(cs));
+    if (ctx->h_counters[0]) {
+        set_err(ctx, "an index case is outside [0, n) or immune, or an immune-set index is out of range");
+        return EF_ERR_ARG;
+    }
+    SirStep sp;
+    sp.seed = p.seed;
+    sp.sim_base = p.sim_base;
+    sp.beta_thr = (uint64_t)std::floor(p.beta * 4294967296.0);
+    sp.gamma_thr = (uint64_t)std::floor(p.gamma * 4294967296.0);
+    int64_t *h_active = reinterpret_cast<int64_t *>(ctx->h_counters + 48);
+    for (int32_t step = 0; step < p.max_steps; ++step) {
+        LAUNCH(launch_sir_step(g->row_ptr, g->col_idx, n, B, step, sp, st, active, t, cs), "SIR step");
+        if ((step + 1) % SIR_CHECK == 0 && step + 1 < p.max_steps) {
+            CU(cudaMemcpyAsync(h_active, active + (step & 1), sizeof(int64_t), cudaMemcpyDeviceToHost, cs));
+            CU(cudaStreamSynchronize(cs));
+            if (*h_active == 0) break;
+        }
+    }
+    LAUNCH(launch_sir_close(B, p.max_steps, st, out->truncated, t, cs), "SIR close");
+    if (out->final_size) CU(cudaMemcpyAsync(out->final_size, st.fsize, 4 * (size_t)B, cudaMemcpyDeviceToDevice, cs));
+    if (out->length) CU(cudaMemcpyAsync(out->length, st.length, 4 * (size_t)B, cudaMemcpyDeviceToDevice, cs));
+    if (out->peak_infected) CU(cudaMemcpyAsync(out->peak_infected, st.peak, 4 * (size_t)B, cudaMemcpyDeviceToDevice, cs));
+    if (out->peak_step) CU(cudaMemcpyAsync(out->peak_step, st.peak_step, 4 * (size_t)B, cudaMemcpyDeviceToDevice, cs));
+    if (out->spread || out->spread_sims) {
+        if (out->spread) CU(cudaMemsetAsync(out->spread, 0, 8 * (size_t)p.depth * (size_t)n, cs));
+        if (out->spread_sims) CU(cudaMemsetAsync(out->spread_sims, 0, 8 * (size_t)n, cs));
+        LAUNCH(launch_sir_tree(B, n, out->spread ? p.depth : 0, p.spread_min_size, st, out->spread, out->spread_sims,
+                               t, cs),
+               "SIR tree");
+    }
+    CU(cudaStreamSynchronize(cs));
     CU(cudaGetLastError());
     return EF_OK;
 }

@@ -45,6 +45,7 @@ enum : int {
     ERRB_ASYM = 16,     // x in N(u) but u not in N(x)
     ERRB_CROSS = 32,    // batched input: an entry outside its row's graph
     ERRB_NODE = 64,     // a requested node id outside [0, n)
+    ERRB_SIR_ARG = 128, // SIR: an index case outside [0, n) or immune, or an immune-set index out of range
 };
 
 // Work bins (each a list of node ids of capacity n), filled from the degrees.
@@ -343,6 +344,32 @@ int launch_select_top(const RankScratch &r, int32_t n, int64_t k, int bits, cons
 int launch_bin_nodes(const int32_t *list, int32_t k, const int32_t *kptr, const int32_t *rp, const int32_t *ci,
                      const Scratch &s, int32_t *mark, int32_t n, const Tune &t, cudaStream_t st);
 int launch_bin_marked(const int32_t *mark, const Scratch &s, int32_t n, const Tune &t, cudaStream_t st);
+// SIR simulation (ef_sir.cu): per (simulation, node) state at s * n + v.
+struct SirState {
+    uint8_t *status;      // B*n  0 susceptible, 1 infected, 2 recovered, 3 immune
+    int32_t *parent;      // B*n  infector (-1 never infected; the index case itself)
+    int32_t *cand;        // B*n  smallest successful infector of the current step
+    uint64_t *list[2];    // B*n each: frontier lists of s << 32 | v
+    int64_t *list_count;  // 2    their lengths
+    int32_t *count;       // B    infected at the start of the next step
+    int32_t *peak, *peak_step, *length, *fsize;   // B
+    uint8_t *done;        // B    1: no infected node left (or never started)
+    int32_t *err;         // error bits (ERRB_SIR_ARG)
+};
+struct SirStep {
+    uint64_t seed;        // Philox key
+    int64_t sim_base;     // counter word 0 = sim_base + simulation index
+    uint64_t beta_thr;    // floor(beta 2^32): a try succeeds when its draw is below
+    uint64_t gamma_thr;   // floor(gamma 2^32): recovery
+};
+int launch_sir_init(const int32_t *index_cases, int32_t B, int32_t n, const uint8_t *immune, int32_t num_sets,
+                    const int32_t *imm_set, const SirState &st, const Tune &t, cudaStream_t s);
+int launch_sir_step(const int32_t *rp, const int32_t *ci, int32_t n, int32_t B, int32_t step, const SirStep &p,
+                    const SirState &st, int64_t *active, const Tune &t, cudaStream_t s);
+int launch_sir_close(int32_t B, int32_t steps, const SirState &st, uint8_t *truncated, const Tune &t,
+                     cudaStream_t s);
+int launch_sir_tree(int32_t B, int32_t n, int32_t depth, int32_t min_size, const SirState &st, int64_t *spread,
+                    int64_t *infected, const Tune &t, cudaStream_t s);
 // shards (ef_shard.cu; the partials' finalize in ef_final.cu)
 int launch_shard_range(const int32_t *rp, int32_t n, int64_t m, int32_t shard, int32_t nshards, int32_t *range,
                        cudaStream_t st);
