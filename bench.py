@@ -109,6 +109,7 @@ def parse():
     p.add_argument("--no-surrogate", action="store_true", help="skip the learned ranking leg")
     p.add_argument("--surrogate-steps", type=int, default=3000)
     p.add_argument("--no-shards", action="store_true", help="skip the sharded-decomposition leg")
+    p.add_argument("--sir", action="store_true", help="run the SIR validation leg (Figs. 6-8 protocols, BA 1M)")
     p.add_argument("--rmat-sweep", action="store_true",
                    help="add EF time and clusters/ms on R-MAT graphs of 2^16 nodes, M = 2..32 edges per node")
     return p.parse_args()
@@ -295,6 +296,102 @@ def shard_leg(ctx, rp, ci, args, dev, full_ms: float) -> list:
                      "finalize_ms": fin, "unsharded_ms": full_ms,
                      "projected_speedup_excl_allreduce": full_ms / (max(best) + fin)})
     return rows
+
+
+def sir_leg(args, dev) -> dict:
+    """SIR validation of EF with Section 5.4's protocols on the BA n=1M, m=5
+    workload, calibrated as Section 3.1 (gamma = 1/3, beta = 1.3 / (3 <k>)):
+    Fig. 7: 10 equally spaced EF values, the node nearest to each as index
+    case of 100 simulations: share of global outbreaks (final size >= 25% of
+    the nodes), mean final size, length and time to peak; Fig. 6: Pearson's
+    r between the spreading power of order 1-4 over global outbreaks (from
+    random index cases) and exp(EF), and degree; Fig. 8: 5% of the nodes
+    immunized, 10 sets of increasing mean EF, 100 simulations each.  Times
+    are CUDA events around ef_sir_run; the oracle runs a few of the same
+    simulations on the host for a rate beside it."""
+    import torch
+    import paper_2306_00606_gb300 as ef
+    g = synth.workload(2)
+    n = g.n
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    ci = torch.from_numpy(g.col_idx).to(dev)
+    ctx = ef.Context(dev.index, torch.cuda.current_stream(dev))
+    E = ctx.compute(rp, ci, precision="fp64", outputs=("ef",))["ef"].cpu().numpy()
+    deg = np.diff(g.row_ptr).astype(np.float64)
+    beta, gamma = 1.3 / (3 * g.nnz / n), 1.0 / 3.0
+    glob = int(np.ceil(0.25 * n))
+    stream = torch.cuda.current_stream(dev)
+    timing = {"sims": 0, "ms": 0.0, "infections": 0}
+
+    def run(index, chunk=500, base=0, **kw):
+        outs = []
+        for c0 in range(0, len(index), chunk):
+            ix = torch.from_numpy(np.ascontiguousarray(index[c0:c0 + chunk], dtype=np.int32)).to(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            o = ctx.sir(rp, ci, ix, beta=beta, gamma=gamma, seed=2306, sim_base=base + c0, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            timing["ms"] += e0.elapsed_time(e1)
+            timing["sims"] += len(ix)
+            timing["infections"] += int(o["final_size"].sum())
+            outs.append({k: v.cpu().numpy() for k, v in o.items()})
+        return outs
+
+    # Fig. 7
+    levels = np.linspace(E.min(), E.max(), 10)
+    idx = np.array([int(np.argmin(np.abs(E - L))) for L in levels])
+    outs = run(np.repeat(idx, 100), outputs=("final_size", "length", "peak_step"))
+    fs = np.concatenate([o["final_size"] for o in outs]).reshape(10, 100)
+    ln = np.concatenate([o["length"] for o in outs]).reshape(10, 100)
+    pk = np.concatenate([o["peak_step"] for o in outs]).reshape(10, 100)
+    fig7 = [{"ef": float(E[i]), "degree": int(deg[i]), "global_pct": float((fs[j] >= glob).mean() * 100),
+             "mean_final_size": float(fs[j].mean()), "mean_length": float(ln[j].mean()),
+             "mean_time_to_peak": float(pk[j].mean())} for j, i in enumerate(idx)]
+    # Fig. 6
+    rng = np.random.default_rng(6)
+    rand_idx = rng.integers(0, n, 1000)
+    outs = run(rand_idx, base=10000, outputs=("final_size", "spread"), spread_min_size=glob)
+    G = int(sum((o["final_size"] >= glob).sum() for o in outs))
+    spread = sum(o["spread"].astype(np.float64) for o in outs)
+    fig6 = {"global_outbreaks": G, "simulations": len(rand_idx)}
+    if G > 0:
+        sp = spread / G
+        for kk in range(4):
+            fig6[f"order{kk + 1}"] = {"r_exp_ef": float(np.corrcoef(sp[kk], np.exp(E))[0, 1]),
+                                      "r_degree": float(np.corrcoef(sp[kk], deg)[0, 1])}
+    # Fig. 8
+    order = np.argsort(E, kind="stable")
+    bins = np.array_split(order, 20)   # 5% of the nodes each, by increasing EF
+    chosen = [bins[j] for j in np.linspace(0, 19, 10).astype(int)]
+    imm = np.zeros((10, n), np.uint8)
+    for j, b in enumerate(chosen):
+        imm[j, b] = 1
+    free = np.nonzero(imm.sum(axis=0) == 0)[0]
+    index = rng.choice(free, 1000)
+    sets = np.repeat(np.arange(10, dtype=np.int32), 100)
+    imm_d = torch.from_numpy(imm).to(dev)
+    fsz = []
+    for c0 in range(0, 1000, 500):
+        o = run(index[c0:c0 + 500], base=20000 + c0, outputs=("final_size",), immune=imm_d,
+                immune_set=torch.from_numpy(sets[c0:c0 + 500]).to(dev))
+        fsz.append(o[0]["final_size"])
+    fsz = np.concatenate(fsz).reshape(10, 100)
+    fig8 = [{"mean_ef_immunized": float(E[b].mean()), "global_pct": float((fsz[j] >= glob).mean() * 100)}
+            for j, b in enumerate(chosen)]
+    # the oracle on a few of the Fig. 7 simulations (top EF level: global outbreaks)
+    from oracle import sir as osir
+    t0 = time.perf_counter()
+    r = osir.simulate(g, np.repeat(idx[-1:], 4), beta, gamma, seed=2306, sim_base=900)
+    cpu_s = time.perf_counter() - t0
+    del ctx
+    return {"workload": "BA n=1e6, m=5", "beta": beta, "gamma": gamma, "global_threshold": glob,
+            "gpu": {"simulations": timing["sims"], "ms": timing["ms"],
+                    "simulations_per_s": timing["sims"] / (timing["ms"] / 1e3),
+                    "infections_per_s": timing["infections"] / (timing["ms"] / 1e3)},
+            "oracle": {"simulations": 4, "s": cpu_s, "infections_per_s": float(r["final_size"].sum()) / cpu_s,
+                       "kind": "numpy oracle, one host thread"},
+            "fig7_index_case_ef": fig7, "fig6_spreading_power": fig6, "fig8_immunization": fig8}
 
 
 def surrogate_leg(args, dev) -> dict:
@@ -539,6 +636,8 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(g, args.cpu_seconds)
     if rank == 0 and world == 1 and not batched and not args.no_shards:
         line["shards"] = shard_leg(ctx, rp, ci, args, dev, ms_step)
+    if rank == 0 and args.sir:
+        line["sir"] = sir_leg(args, dev)
     if rank == 0 and args.rmat_sweep:
         line["rmat_sweep"] = rmat_sweep(ctx, args, dev)
     if rank == 0 and world == 1 and not args.no_surrogate and args.scale == 1.0:

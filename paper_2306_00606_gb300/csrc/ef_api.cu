@@ -1000,16 +1000,16 @@ int ef_sir_run(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const int32_t
     // state buffer
     size_t off = 0;
     auto place = [&](size_t bytes) { size_t o_ = off; off += al(bytes); return o_; };
-    const size_t o_status = place(BN), o_parent = out->parent ? 0 : place(4 * BN), o_cand = place(4 * BN),
+    const size_t o_susc = place(4 * (size_t)B * (((size_t)n + 31) / 32)), o_parent = out->parent ? 0 : place(4 * BN), o_cand = place(4 * BN),
                  o_l0 = place(8 * BN), o_l1 = place(8 * BN), o_lc = place(16), o_act = place(16),
                  o_cnt = place(4 * (size_t)B), o_peak = place(4 * (size_t)B), o_pstep = place(4 * (size_t)B),
                  o_len = place(4 * (size_t)B), o_fs = place(4 * (size_t)B), o_done = place((size_t)B),
-                 o_err = place(4);
+                 o_err = place(4), o_heavy = place(8 * BN), o_hc = place(8);
     rc = ensure_buffer(ctx, &ctx->sir, &ctx->sir_bytes, off, 0);
     if (rc) return rc;
     char *b = (char *)ctx->sir;
     SirState st;
-    st.status = (uint8_t *)(b + o_status);
+    st.susc = (uint32_t *)(b + o_susc);
     st.parent = out->parent ? out->parent : (int32_t *)(b + o_parent);
     st.cand = (int32_t *)(b + o_cand);
     st.list[0] = (uint64_t *)(b + o_l0);
@@ -1023,11 +1023,14 @@ int ef_sir_run(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const int32_t
     st.fsize = (int32_t *)(b + o_fs);
     st.done = (uint8_t *)(b + o_done);
     st.err = (int32_t *)(b + o_err);
+    st.heavy = (uint64_t *)(b + o_heavy);
+    st.heavy_count = (int64_t *)(b + o_hc);
     cudaStream_t cs = ctx->stream;
     const Tune &t = ctx->tune;
     const int64_t h_init[4] = {B, 0, 0, 0};   // list lengths {B, 0}, active counts {0, 0}
     CU(cudaMemcpyAsync(st.list_count, h_init, sizeof h_init, cudaMemcpyHostToDevice, cs));
     CU(cudaMemsetAsync(st.err, 0, sizeof(int32_t), cs));
+    CU(cudaMemsetAsync(st.heavy_count, 0, sizeof(int64_t), cs));
     LAUNCH(launch_sir_init(index_cases, B, n, immune, num_immune_sets, immune_set, st, t, cs), "SIR init");
     CU(cudaMemcpyAsync(ctx->h_counters, st.err, sizeof(int32_t), cudaMemcpyDeviceToHost, cs));
     CU(cudaStreamSynchronize(cs));

@@ -346,7 +346,7 @@ int launch_bin_nodes(const int32_t *list, int32_t k, const int32_t *kptr, const 
 int launch_bin_marked(const int32_t *mark, const Scratch &s, int32_t n, const Tune &t, cudaStream_t st);
 // SIR simulation (ef_sir.cu): per (simulation, node) state at s * n + v.
 struct SirState {
-    uint8_t *status;      // B*n  0 susceptible, 1 infected, 2 recovered, 3 immune
+    uint32_t *susc;       // B*ceil(n/32)  susceptibility bits, a row of words per simulation
     int32_t *parent;      // B*n  infector (-1 never infected; the index case itself)
     int32_t *cand;        // B*n  smallest successful infector of the current step
     uint64_t *list[2];    // B*n each: frontier lists of s << 32 | v
@@ -354,6 +354,8 @@ struct SirState {
     int32_t *count;       // B    infected at the start of the next step
     int32_t *peak, *peak_step, *length, *fsize;   // B
     uint8_t *done;        // B    1: no infected node left (or never started)
+    uint64_t *heavy;      // B*n  this step's frontier entries of high degree
+    int64_t *heavy_count; // 1
     int32_t *err;         // error bits (ERRB_SIR_ARG)
 };
 struct SirStep {

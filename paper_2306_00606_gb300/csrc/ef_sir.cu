@@ -15,14 +15,21 @@
 // and key = the 64-bit seed, first output word: a simulation's course
 // depends on its id and the seed only, not on the batch or the launch.
 //
-// Layout: per (simulation s, node v), at s * n + v: the state byte, the
-// infector (parent) and the smallest successful infector of the current step
-// (cand).  The infected (s, u) pairs of a step form a frontier list of
+// Layout: per (simulation s, node v): a susceptibility bit (bit v & 31 of
+// word s * W + v / 32, W = ceil(n / 32): the only state the tries read, 1/8
+// of a state byte so that it stays in L2), at s * n + v the infector
+// (parent) and the smallest successful infector of the current step (cand).
+// Infected and recovered nodes are the ones without the bit and with a
+// parent, immune nodes the ones without either; recovery only leaves the
+// frontier.  The infected (s, u) pairs of a step form a frontier list of
 // 64-bit entries s << 32 | u; a step appends survivors and new infections
 // to the other list.  Kernels of a step:
 //   k_sir_spread  4 frontier entries per warp, 8 lanes each over the
 //                 entry's neighbours: tries, cand by atomicMin (the first
-//                 success appends x), the recovery draw (survivors append)
+//                 success appends x), the recovery draw (survivors append);
+//                 entries of degree > SIR_HEAVY are listed for
+//   k_sir_spread_heavy  a CTA per listed entry over its neighbours (hubs
+//                 would otherwise hold a warp for hundreds of rounds)
 //   k_sir_commit  over the new list: a node still susceptible becomes
 //                 infected with parent = cand
 //   k_sir_stats   per simulation: peak, peak step, length; clears the
@@ -33,9 +40,9 @@
 
 namespace ef {
 
-constexpr uint8_t SIR_S = 0, SIR_I = 1, SIR_R = 2, SIR_M = 3;
 constexpr int32_t NO_CAND = 0x7fffffff;
 constexpr uint32_t RECOVER_WORD = 0xffffffffu;
+constexpr int SIR_HEAVY = 64;   // frontier entries of higher degree are tried by a CTA each
 
 // Philox4x32-10, first output word only.
 __device__ __forceinline__ uint32_t philox_w0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t key) {
@@ -59,27 +66,43 @@ __device__ __forceinline__ uint32_t philox_w0(uint32_t c0, uint32_t c1, uint32_t
 
 __device__ __forceinline__ uint64_t sir_entry(int s, int v) { return (uint64_t)(uint32_t)s << 32 | (uint32_t)v; }
 
-// States, parents and candidates of every (simulation, node); immune sets;
-// the index cases and the first frontier.
-__global__ void k_sir_init(const int32_t *__restrict__ index_cases, int32_t B, int32_t n,
-                           const uint8_t *__restrict__ immune, int32_t num_sets, const int32_t *__restrict__ imm_set,
-                           SirState st) {
-    const int64_t total = (int64_t)B * n;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int s = (int)(i / n), v = (int)(i - (int64_t)s * n);
-        uint8_t state = SIR_S;
+__device__ __forceinline__ int64_t sir_words(int32_t n) { return ((int64_t)n + 31) >> 5; }
+
+__device__ __forceinline__ bool susceptible(const uint32_t *susc, int64_t wrow, int x) {
+    return (__ldg(susc + wrow + (x >> 5)) >> (x & 31)) & 1u;
+}
+
+// Susceptibility words (all nodes but the immune ones), parents and
+// candidates of every (simulation, node).
+__global__ void k_sir_init(int32_t B, int32_t n, const uint8_t *__restrict__ immune, int32_t num_sets,
+                           const int32_t *__restrict__ imm_set, SirState st) {
+    const int64_t W = sir_words(n), words = (int64_t)B * W, total = (int64_t)B * n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
+        const int s = (int)(i / W);
+        const int v0 = (int)(i - (int64_t)s * W) * 32;
+        uint32_t w = 0;
+        int set = -1;
         if (imm_set) {
-            const int set = imm_set[s];
-            if (set >= num_sets) atomicOr(st.err, ERRB_SIR_ARG);
-            else if (set >= 0 && immune[(int64_t)set * n + v]) state = SIR_M;
+            set = imm_set[s];
+            if (set >= num_sets) {
+                atomicOr(st.err, ERRB_SIR_ARG);
+                set = -1;
+            }
         }
-        st.status[i] = state;
+        for (int b = 0; b < 32 && v0 + b < n; ++b)
+            if (set < 0 || !immune[(int64_t)set * n + v0 + b]) w |= 1u << b;
+        st.susc[i] = w;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
         st.parent[i] = -1;
         st.cand[i] = NO_CAND;
     }
 }
 
+// The index cases and the first frontier (an immune index case is an error).
 __global__ void k_sir_seed(const int32_t *__restrict__ index_cases, int32_t B, int32_t n, SirState st) {
+    const int64_t W = sir_words(n);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < B; s += gridDim.x * blockDim.x) {
         const int u = index_cases[s];
         st.peak[s] = 1;
@@ -88,25 +111,28 @@ __global__ void k_sir_seed(const int32_t *__restrict__ index_cases, int32_t B, i
         st.count[s] = 0;
         st.done[s] = 0;
         st.fsize[s] = 1;
-        if (u < 0 || u >= n || st.status[(int64_t)s * n + u] == SIR_M) {
+        if (u < 0 || u >= n || !susceptible(st.susc, s * W, u)) {
             atomicOr(st.err, ERRB_SIR_ARG);
             st.done[s] = 1;   // no frontier entry: the simulation does not run
             st.fsize[s] = 0;
             continue;
         }
-        st.status[(int64_t)s * n + u] = SIR_I;
+        st.susc[s * W + (u >> 5)] &= ~(1u << (u & 31));   // one index case per row of words
         st.parent[(int64_t)s * n + u] = u;
         st.list[0][s] = sir_entry(s, u);
     }
 }
 
-// One step over the frontier list `cur` (count *ccur), appending to `nxt`.
+__device__ __forceinline__ void sir_append(bool app, uint64_t ent, uint64_t *__restrict__ nxt,
+                                           int64_t *__restrict__ cnxt, int32_t *__restrict__ count);
+
+// One step over the frontier list `cur` (count *ccur), appending to `nxt`;
+// entries of degree > SIR_HEAVY go to the heavy list instead.
 __global__ void __launch_bounds__(256) k_sir_spread(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                     int32_t n, int32_t t, SirStep p, SirState st,
                                                     const uint64_t *__restrict__ cur, const int64_t *__restrict__ ccur,
                                                     uint64_t *__restrict__ nxt, int64_t *__restrict__ cnxt) {
     const int lane = threadIdx.x & 31, oct = lane >> 3, l8 = lane & 7;
-    const unsigned lt = (1u << lane) - 1u;
     const int64_t total = *ccur;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4; base < total;
@@ -120,17 +146,20 @@ __global__ void __launch_bounds__(256) k_sir_spread(const int32_t *__restrict__ 
             u = (int)(uint32_t)e;
             a = rp[u];
             D = rp[u + 1] - a;
+            if (D > SIR_HEAVY) {
+                // tried by k_sir_spread_heavy, a CTA per entry
+                if (l8 == 0) st.heavy[atomicAdd((unsigned long long *)st.heavy_count, 1ull)] = e;
+                D = 0;
+            }
         }
         const uint32_t sim = (uint32_t)(p.sim_base + s);
-        const int64_t row = (int64_t)s * n;
+        const int64_t row = (int64_t)s * n, wrow = s * sir_words(n);
         // recovery (lane 0 of the octet): survivors stay in the frontier
         bool app = false;
         uint64_t ent = 0;
         if (valid && l8 == 0) {
             const uint32_t w = philox_w0(sim, (uint32_t)t, (uint32_t)u, RECOVER_WORD, p.seed);
-            if ((uint64_t)w < p.gamma_thr) {
-                st.status[row + u] = SIR_R;
-            } else {
+            if ((uint64_t)w >= p.gamma_thr) {
                 app = true;
                 ent = sir_entry(s, u);
             }
@@ -139,24 +168,13 @@ __global__ void __launch_bounds__(256) k_sir_spread(const int32_t *__restrict__ 
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
         for (int k0 = 0;; k0 += 8) {
-            // append this round's entries (one atomic per warp)
-            const unsigned bal = __ballot_sync(FULL, app);
-            if (bal) {
-                int64_t pos = 0;
-                const int leader = __ffs(bal) - 1;
-                if (lane == leader) pos = atomicAdd((unsigned long long *)cnxt, (unsigned long long)__popc(bal));
-                pos = __shfl_sync(FULL, pos, leader);
-                if (app) {
-                    nxt[pos + __popc(bal & lt)] = ent;
-                    atomicAdd(st.count + (int)(ent >> 32), 1);
-                }
-            }
+            sir_append(app, ent, nxt, cnxt, st.count);   // this round's entries
             if (k0 >= kmax) break;
             app = false;
             const int k = k0 + l8;
             if (valid && k < D) {
                 const int x = ci[a + k];
-                if (st.status[row + x] == SIR_S) {
+                if (susceptible(st.susc, wrow, x)) {
                     const uint32_t w = philox_w0(sim, (uint32_t)t, (uint32_t)u, (uint32_t)x, p.seed);
                     if ((uint64_t)w < p.beta_thr) {
                         const int old = atomicMin(st.cand + row + x, u);
@@ -171,17 +189,71 @@ __global__ void __launch_bounds__(256) k_sir_spread(const int32_t *__restrict__ 
     }
 }
 
+// Appends the lanes' entries (app) to nxt with one list atomic per warp and
+// one count update per simulation; every lane of the warp calls it.
+__device__ __forceinline__ void sir_append(bool app, uint64_t ent, uint64_t *__restrict__ nxt,
+                                           int64_t *__restrict__ cnxt, int32_t *__restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const unsigned bal = __ballot_sync(FULL, app);
+    if (!bal) return;
+    int64_t pos = 0;
+    const int leader = __ffs(bal) - 1;
+    if (lane == leader) pos = atomicAdd((unsigned long long *)cnxt, (unsigned long long)__popc(bal));
+    pos = __shfl_sync(FULL, pos, leader);
+    if (app) {
+        nxt[pos + __popc(bal & ((1u << lane) - 1u))] = ent;
+        const int es = (int)(ent >> 32);
+        const unsigned peers = __match_any_sync(bal, es);
+        if (lane == __ffs(peers) - 1) atomicAdd(count + es, __popc(peers));
+    }
+}
+
+// The tries of the frontier entries of degree > SIR_HEAVY: a CTA per entry,
+// its threads over the neighbours.
+__global__ void __launch_bounds__(256) k_sir_spread_heavy(const int32_t *__restrict__ rp,
+                                                          const int32_t *__restrict__ ci, int32_t n, int32_t t,
+                                                          SirStep p, SirState st, uint64_t *__restrict__ nxt,
+                                                          int64_t *__restrict__ cnxt) {
+    const int64_t total = *st.heavy_count;
+    for (int64_t h = blockIdx.x; h < total; h += gridDim.x) {
+        const uint64_t e = st.heavy[h];
+        const int s = (int)(e >> 32), u = (int)(uint32_t)e;
+        const int a = rp[u], D = rp[u + 1] - a;
+        const uint32_t sim = (uint32_t)(p.sim_base + s);
+        const int64_t row = (int64_t)s * n, wrow = s * sir_words(n);
+        for (int k0 = 0; k0 < D; k0 += blockDim.x) {
+            const int k = k0 + threadIdx.x;
+            bool app = false;
+            uint64_t ent = 0;
+            if (k < D) {
+                const int x = ci[a + k];
+                if (susceptible(st.susc, wrow, x)) {
+                    const uint32_t w = philox_w0(sim, (uint32_t)t, (uint32_t)u, (uint32_t)x, p.seed);
+                    if ((uint64_t)w < p.beta_thr && atomicMin(st.cand + row + x, u) == NO_CAND) {
+                        app = true;
+                        ent = sir_entry(s, x);
+                    }
+                }
+            }
+            sir_append(app, ent, nxt, cnxt, st.count);
+        }
+    }
+}
+
 // New infections of the step: the entries of `nxt` whose node is still
-// susceptible (the others are survivors).
+// susceptible (the others are survivors).  Each entry is listed once, so its
+// bit is read plainly and cleared atomically (its word is shared).
 __global__ void k_sir_commit(int32_t n, SirState st, const uint64_t *__restrict__ nxt,
                              const int64_t *__restrict__ cnxt) {
-    const int64_t total = *cnxt;
+    const int64_t total = *cnxt, W = sir_words(n);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t e = nxt[i];
         const int s = (int)(e >> 32), x = (int)(uint32_t)e;
         const int64_t j = (int64_t)s * n + x;
-        if (st.status[j] == SIR_S) {
-            st.status[j] = SIR_I;
+        uint32_t *word = st.susc + s * W + (x >> 5);
+        const uint32_t bit = 1u << (x & 31);
+        if (*word & bit) {
+            atomicAnd(word, ~bit);
             st.parent[j] = st.cand[j];
             st.cand[j] = NO_CAND;
             atomicAdd(st.fsize + s, 1);
@@ -196,6 +268,7 @@ __global__ void k_sir_stats(int32_t B, int32_t t, SirState st, int64_t *__restri
                             int64_t *__restrict__ active) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         *ccur = 0;   // the list just read is the next step's output
+        *st.heavy_count = 0;
         active[(t + 1) & 1] = 0;
     }
     int act = 0;
@@ -268,8 +341,8 @@ static inline unsigned grid_for(int64_t work, int per_block, int64_t cap) {
 
 int launch_sir_init(const int32_t *index_cases, int32_t B, int32_t n, const uint8_t *immune, int32_t num_sets,
                     const int32_t *imm_set, const SirState &st, const Tune &t, cudaStream_t s) {
-    k_sir_init<<<grid_for((int64_t)B * n, 256, (int64_t)t.num_sms * 32), 256, 0, s>>>(index_cases, B, n, immune,
-                                                                                     num_sets, imm_set, st);
+    k_sir_init<<<grid_for((int64_t)B * n, 256, (int64_t)t.num_sms * 32), 256, 0, s>>>(B, n, immune, num_sets,
+                                                                                     imm_set, st);
     k_sir_seed<<<grid_for(B, 256, (int64_t)t.num_sms * 4), 256, 0, s>>>(index_cases, B, n, st);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -280,6 +353,7 @@ int launch_sir_step(const int32_t *rp, const int32_t *ci, int32_t n, int32_t B, 
     uint64_t *cur = st.list[c], *nxt = st.list[c ^ 1];
     int64_t *ccur = st.list_count + c, *cnxt = st.list_count + (c ^ 1);
     k_sir_spread<<<t.num_sms * 8, 256, 0, s>>>(rp, ci, n, step, p, st, cur, ccur, nxt, cnxt);
+    k_sir_spread_heavy<<<t.num_sms * 8, 256, 0, s>>>(rp, ci, n, step, p, st, nxt, cnxt);
     k_sir_commit<<<t.num_sms * 8, 256, 0, s>>>(n, st, nxt, cnxt);
     k_sir_stats<<<grid_for(B, 256, (int64_t)t.num_sms * 4), 256, 0, s>>>(B, step, st, ccur, active);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
