@@ -110,6 +110,9 @@ def parse():
     p.add_argument("--surrogate-steps", type=int, default=3000)
     p.add_argument("--no-shards", action="store_true", help="skip the sharded-decomposition leg")
     p.add_argument("--sir", action="store_true", help="run the SIR validation leg (Figs. 6-8 protocols, BA 1M)")
+    p.add_argument("--sir-batch", type=int, default=0, metavar="B",
+                   help="only time one ef_sir_run of B simulations from the highest-degree node of BA 1M "
+                        "(one call, for profiling)")
     p.add_argument("--rmat-sweep", action="store_true",
                    help="add EF time and clusters/ms on R-MAT graphs of 2^16 nodes, M = 2..32 edges per node")
     return p.parse_args()
@@ -394,6 +397,32 @@ def sir_leg(args, dev) -> dict:
             "fig7_index_case_ef": fig7, "fig6_spreading_power": fig6, "fig8_immunization": fig8}
 
 
+def sir_batch(args) -> int:
+    """One ef_sir_run call: B simulations from the highest-degree node of the
+    BA n=1M, m=5 workload (Section 3.1's calibration, seed 2), CUDA events."""
+    import torch
+    import paper_2306_00606_gb300 as ef
+    dev = torch.device("cuda", 0)
+    g = synth.workload(2)
+    rp = torch.from_numpy(g.row_ptr).to(dev)
+    ci = torch.from_numpy(g.col_idx).to(dev)
+    ctx = ef.Context(0, torch.cuda.current_stream(dev))
+    top = int(np.argmax(np.diff(g.row_ptr)))
+    idx = torch.full((args.sir_batch,), top, dtype=torch.int32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    o = ctx.sir(rp, ci, idx, beta=1.3 / (3 * g.nnz / g.n), gamma=1.0 / 3.0, seed=2,
+                outputs=("final_size", "length"))
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    inf = int(o["final_size"].sum())
+    print(json.dumps({"sir_batch": args.sir_batch, "ms": ms, "simulations_per_s": args.sir_batch / ms * 1e3,
+                      "infections_per_s": inf / ms * 1e3, "max_length": int(o["length"].max())}))
+    ctx.close()
+    return 0
+
+
 def surrogate_leg(args, dev) -> dict:
     """The learned ranking path on the BA n=16M, m=4 workload: a network
     trained on exact EF of the ER 2000 and BA 1M workloads (features and
@@ -660,6 +689,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sir_batch:
+        return sir_batch(args)
     return run_ours(args)
 
 

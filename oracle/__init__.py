@@ -16,6 +16,11 @@ Three independent computations live here:
   out-degree counted edge by edge (Section 3.3's definition), pure Python,
   for tiny graphs only (``oracle.brute``).
 
+Beside them: ``oracle.surrogate`` (the learned ranking path's features,
+network and metrics), ``oracle.shard`` (Algorithm 1's loop over a range of
+middle nodes, the sharded form) and ``oracle.sir`` (the SIR simulation of
+Section 3.1 with Philox4x32-10 draws).
+
 Graphs are passed as (row_ptr, col_idx) int32 numpy arrays of a symmetric
 CSR with sorted rows, or any object carrying those two attributes.
 """
