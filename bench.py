@@ -572,10 +572,9 @@ def run_ours(args):
     ctx.stats(reset=True)
 
     # ---- device-resident timing (inputs in HBM; > L2, no flush) ----
-    # Single graphs: the timed steps also carry the library's per-pass events.
-    # Batches: the timed steps replay the captured CUDA graph (no events
-    # inside); a second region of as many eager, profiled steps gives the
-    # per-pass breakdown.
+    # The timed steps carry no events inside (batches replay the captured
+    # CUDA graph); a second region of as many profiled steps, with the
+    # library's events between the passes, gives the per-pass breakdown.
     def timed(profile):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -590,11 +589,10 @@ def run_ours(args):
         return max_over_ranks(ev0.elapsed_time(ev1), world, dev)
 
     with ClockSampler(local) as clk:
-        ms = timed(profile=not batched)
+        ms = timed(profile=False)
     replays = ctx.stats()["graph_replays"]
-    if batched:
-        ctx.stats(reset=True)
-        timed(profile=True)
+    ctx.stats(reset=True)
+    timed(profile=True)
     passes = ctx.stats(reset=True)
     ms_step = ms / args.steps
     value = st["W"] * args.steps * world / (ms / 1e3)
