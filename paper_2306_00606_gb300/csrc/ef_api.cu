@@ -995,75 +995,94 @@ int ef_sir_run(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const int32_t
     int64_t fcap;
     rc = prepare_graph(ctx, g->row_ptr, g->col_idx, n, m, o, s, fcap);
     if (rc) return rc;
-    const int32_t B = num_sims;
-    const size_t BN = (size_t)B * (size_t)n;
-    // state buffer
+    cudaStream_t cs = ctx->stream;
+    const Tune &t = ctx->tune;
+    SirStep sp;
+    sp.seed = p.seed;
+    sp.beta_thr = (uint64_t)std::floor(p.beta * 4294967296.0);
+    sp.gamma_thr = (uint64_t)std::floor(p.gamma * 4294967296.0);
+    // state of one batch of at most SIR_BATCH simulations
+    const int32_t Bmax = num_sims < SIR_BATCH ? num_sims : SIR_BATCH;
+    const size_t N = (size_t)n, WBmax = ((size_t)Bmax + 31) / 32;
     size_t off = 0;
     auto place = [&](size_t bytes) { size_t o_ = off; off += al(bytes); return o_; };
-    const size_t o_susc = place(4 * (size_t)B * (((size_t)n + 31) / 32)), o_parent = out->parent ? 0 : place(4 * BN), o_cand = place(4 * BN),
-                 o_l0 = place(8 * BN), o_l1 = place(8 * BN), o_lc = place(16), o_act = place(16),
-                 o_cnt = place(4 * (size_t)B), o_peak = place(4 * (size_t)B), o_pstep = place(4 * (size_t)B),
-                 o_len = place(4 * (size_t)B), o_fs = place(4 * (size_t)B), o_done = place((size_t)B),
-                 o_err = place(4), o_heavy = place(8 * BN), o_hc = place(8);
+    const size_t o_susc = place(4 * N * WBmax), o_inf0 = place(4 * N * WBmax), o_inf1 = place(4 * N * WBmax),
+                 o_new = place(4 * N * WBmax), o_cand = place(4 * N * (size_t)Bmax),
+                 o_parent = out->parent ? 0 : place(4 * N * (size_t)Bmax), o_f0 = place(4 * N), o_f1 = place(4 * N),
+                 o_touch = place(4 * N), o_heavy = place(4 * N), o_fmark = place(4 * N), o_tmark = place(4 * N),
+                 o_counts = place(16), o_act = place(16), o_cnt = place(4 * (size_t)Bmax),
+                 o_peak = place(4 * (size_t)Bmax), o_pstep = place(4 * (size_t)Bmax), o_len = place(4 * (size_t)Bmax),
+                 o_fs = place(4 * (size_t)Bmax), o_done = place((size_t)Bmax), o_err = place(4);
     rc = ensure_buffer(ctx, &ctx->sir, &ctx->sir_bytes, off, 0);
     if (rc) return rc;
     char *b = (char *)ctx->sir;
-    SirState st;
-    st.susc = (uint32_t *)(b + o_susc);
-    st.parent = out->parent ? out->parent : (int32_t *)(b + o_parent);
-    st.cand = (int32_t *)(b + o_cand);
-    st.list[0] = (uint64_t *)(b + o_l0);
-    st.list[1] = (uint64_t *)(b + o_l1);
-    st.list_count = (int64_t *)(b + o_lc);
     int64_t *active = (int64_t *)(b + o_act);
-    st.count = (int32_t *)(b + o_cnt);
-    st.peak = (int32_t *)(b + o_peak);
-    st.peak_step = (int32_t *)(b + o_pstep);
-    st.length = (int32_t *)(b + o_len);
-    st.fsize = (int32_t *)(b + o_fs);
-    st.done = (uint8_t *)(b + o_done);
-    st.err = (int32_t *)(b + o_err);
-    st.heavy = (uint64_t *)(b + o_heavy);
-    st.heavy_count = (int64_t *)(b + o_hc);
-    cudaStream_t cs = ctx->stream;
-    const Tune &t = ctx->tune;
-    const int64_t h_init[4] = {B, 0, 0, 0};   // list lengths {B, 0}, active counts {0, 0}
-    CU(cudaMemcpyAsync(st.list_count, h_init, sizeof h_init, cudaMemcpyHostToDevice, cs));
-    CU(cudaMemsetAsync(st.err, 0, sizeof(int32_t), cs));
-    CU(cudaMemsetAsync(st.heavy_count, 0, sizeof(int64_t), cs));
-    LAUNCH(launch_sir_init(index_cases, B, n, immune, num_immune_sets, immune_set, st, t, cs), "SIR init");
-    CU(cudaMemcpyAsync(ctx->h_counters, st.err, sizeof(int32_t), cudaMemcpyDeviceToHost, cs));
-    CU(cudaStreamSynchronize(cs));
-    if (ctx->h_counters[0]) {
-        set_err(ctx, "an index case is outside [0, n) or immune, or an immune-set index is out of range");
-        return EF_ERR_ARG;
-    }
-    SirStep sp;
-    sp.seed = p.seed;
-    sp.sim_base = p.sim_base;
-    sp.beta_thr = (uint64_t)std::floor(p.beta * 4294967296.0);
-    sp.gamma_thr = (uint64_t)std::floor(p.gamma * 4294967296.0);
     int64_t *h_active = reinterpret_cast<int64_t *>(ctx->h_counters + 48);
-    for (int32_t step = 0; step < p.max_steps; ++step) {
-        LAUNCH(launch_sir_step(g->row_ptr, g->col_idx, n, B, step, sp, st, active, t, cs), "SIR step");
-        if ((step + 1) % SIR_CHECK == 0 && step + 1 < p.max_steps) {
-            CU(cudaMemcpyAsync(h_active, active + (step & 1), sizeof(int64_t), cudaMemcpyDeviceToHost, cs));
-            CU(cudaStreamSynchronize(cs));
-            if (*h_active == 0) break;
+    if (out->spread) CU(cudaMemsetAsync(out->spread, 0, 8 * (size_t)p.depth * N, cs));
+    if (out->spread_sims) CU(cudaMemsetAsync(out->spread_sims, 0, 8 * N, cs));
+    for (int32_t c0 = 0; c0 < num_sims; c0 += SIR_BATCH) {
+        SirState st;
+        st.B = num_sims - c0 < SIR_BATCH ? num_sims - c0 : SIR_BATCH;
+        st.WB = (st.B + 31) / 32;
+        st.susc = (uint32_t *)(b + o_susc);
+        st.inf[0] = (uint32_t *)(b + o_inf0);
+        st.inf[1] = (uint32_t *)(b + o_inf1);
+        st.newinf = (uint32_t *)(b + o_new);
+        st.cand = (int32_t *)(b + o_cand);
+        st.parent = out->parent ? out->parent + (size_t)c0 * N : (int32_t *)(b + o_parent);
+        st.front[0] = (int32_t *)(b + o_f0);
+        st.front[1] = (int32_t *)(b + o_f1);
+        st.touched = (int32_t *)(b + o_touch);
+        st.heavy = (int32_t *)(b + o_heavy);
+        st.fmark = (int32_t *)(b + o_fmark);
+        st.tmark = (int32_t *)(b + o_tmark);
+        st.counts = (int32_t *)(b + o_counts);
+        st.count = (int32_t *)(b + o_cnt);
+        st.peak = (int32_t *)(b + o_peak);
+        st.peak_step = (int32_t *)(b + o_pstep);
+        st.length = (int32_t *)(b + o_len);
+        st.fsize = (int32_t *)(b + o_fs);
+        st.done = (uint8_t *)(b + o_done);
+        st.err = (int32_t *)(b + o_err);
+        const size_t words = 4 * N * (size_t)st.WB;
+        CU(cudaMemsetAsync(st.inf[0], 0, words, cs));
+        CU(cudaMemsetAsync(st.inf[1], 0, words, cs));
+        CU(cudaMemsetAsync(st.newinf, 0, words, cs));
+        CU(cudaMemsetAsync(st.fmark, 0, 4 * N, cs));
+        CU(cudaMemsetAsync(st.tmark, 0, 4 * N, cs));
+        CU(cudaMemsetAsync(st.counts, 0, 16, cs));
+        CU(cudaMemsetAsync(active, 0, 16, cs));
+        CU(cudaMemsetAsync(st.err, 0, sizeof(int32_t), cs));
+        LAUNCH(launch_sir_init(index_cases + c0, n, immune, num_immune_sets, immune_set ? immune_set + c0 : nullptr,
+                               st, t, cs),
+               "SIR init");
+        CU(cudaMemcpyAsync(ctx->h_counters, st.err, sizeof(int32_t), cudaMemcpyDeviceToHost, cs));
+        CU(cudaStreamSynchronize(cs));
+        if (ctx->h_counters[0]) {
+            set_err(ctx, "an index case is outside [0, n) or immune, or an immune-set index is out of range");
+            return EF_ERR_ARG;
         }
+        sp.sim_base = p.sim_base + c0;
+        for (int32_t step = 0; step < p.max_steps; ++step) {
+            LAUNCH(launch_sir_step(g->row_ptr, g->col_idx, n, step, sp, st, active, t, cs), "SIR step");
+            if ((step + 1) % SIR_CHECK == 0 && step + 1 < p.max_steps) {
+                CU(cudaMemcpyAsync(h_active, active + (step & 1), sizeof(int64_t), cudaMemcpyDeviceToHost, cs));
+                CU(cudaStreamSynchronize(cs));
+                if (*h_active == 0) break;
+            }
+        }
+        LAUNCH(launch_sir_close(p.max_steps, st, out->truncated ? out->truncated + c0 : nullptr, t, cs), "SIR close");
+        const size_t bb = 4 * (size_t)st.B;
+        if (out->final_size) CU(cudaMemcpyAsync(out->final_size + c0, st.fsize, bb, cudaMemcpyDeviceToDevice, cs));
+        if (out->length) CU(cudaMemcpyAsync(out->length + c0, st.length, bb, cudaMemcpyDeviceToDevice, cs));
+        if (out->peak_infected) CU(cudaMemcpyAsync(out->peak_infected + c0, st.peak, bb, cudaMemcpyDeviceToDevice, cs));
+        if (out->peak_step) CU(cudaMemcpyAsync(out->peak_step + c0, st.peak_step, bb, cudaMemcpyDeviceToDevice, cs));
+        if (out->spread || out->spread_sims)
+            LAUNCH(launch_sir_tree(n, out->spread ? p.depth : 0, p.spread_min_size, st, out->spread, out->spread_sims,
+                                   t, cs),
+                   "SIR tree");
     }
-    LAUNCH(launch_sir_close(B, p.max_steps, st, out->truncated, t, cs), "SIR close");
-    if (out->final_size) CU(cudaMemcpyAsync(out->final_size, st.fsize, 4 * (size_t)B, cudaMemcpyDeviceToDevice, cs));
-    if (out->length) CU(cudaMemcpyAsync(out->length, st.length, 4 * (size_t)B, cudaMemcpyDeviceToDevice, cs));
-    if (out->peak_infected) CU(cudaMemcpyAsync(out->peak_infected, st.peak, 4 * (size_t)B, cudaMemcpyDeviceToDevice, cs));
-    if (out->peak_step) CU(cudaMemcpyAsync(out->peak_step, st.peak_step, 4 * (size_t)B, cudaMemcpyDeviceToDevice, cs));
-    if (out->spread || out->spread_sims) {
-        if (out->spread) CU(cudaMemsetAsync(out->spread, 0, 8 * (size_t)p.depth * (size_t)n, cs));
-        if (out->spread_sims) CU(cudaMemsetAsync(out->spread_sims, 0, 8 * (size_t)n, cs));
-        LAUNCH(launch_sir_tree(B, n, out->spread ? p.depth : 0, p.spread_min_size, st, out->spread, out->spread_sims,
-                               t, cs),
-               "SIR tree");
-    }
+    if (out->spread) LAUNCH(launch_sir_cumulate(n, p.depth, out->spread, t, cs), "SIR spread");
     CU(cudaStreamSynchronize(cs));
     CU(cudaGetLastError());
     return EF_OK;

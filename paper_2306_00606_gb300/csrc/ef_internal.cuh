@@ -344,18 +344,23 @@ int launch_select_top(const RankScratch &r, int32_t n, int64_t k, int bits, cons
 int launch_bin_nodes(const int32_t *list, int32_t k, const int32_t *kptr, const int32_t *rp, const int32_t *ci,
                      const Scratch &s, int32_t *mark, int32_t n, const Tune &t, cudaStream_t st);
 int launch_bin_marked(const int32_t *mark, const Scratch &s, int32_t n, const Tune &t, cudaStream_t st);
-// SIR simulation (ef_sir.cu): per (simulation, node) state at s * n + v.
+// SIR simulation (ef_sir.cu): a batch of at most SIR_BATCH simulations,
+// node-major bit words (WB = ceil(B / 32) per node), frontier lists of nodes.
+constexpr int SIR_BATCH = 1024;
 struct SirState {
-    uint32_t *susc;       // B*ceil(n/32)  susceptibility bits, a row of words per simulation
-    int32_t *parent;      // B*n  infector (-1 never infected; the index case itself)
-    int32_t *cand;        // B*n  smallest successful infector of the current step
-    uint64_t *list[2];    // B*n each: frontier lists of s << 32 | v
-    int64_t *list_count;  // 2    their lengths
-    int32_t *count;       // B    infected at the start of the next step
-    int32_t *peak, *peak_step, *length, *fsize;   // B
-    uint8_t *done;        // B    1: no infected node left (or never started)
-    uint64_t *heavy;      // B*n  this step's frontier entries of high degree
-    int64_t *heavy_count; // 1
+    int32_t B, WB;        // simulations of the batch, words per node
+    uint32_t *susc;       // n*WB   susceptible (bit s % 32 of word s / 32)
+    uint32_t *inf[2];     // n*WB   infected at the start of this step / of the next
+    uint32_t *newinf;     // n*WB   infected during this step
+    int32_t *cand;        // n*B    smallest successful infector of the step (x * B + s)
+    int32_t *parent;      // B*n    infection tree (s * n + v): -1 never infected, the index case itself
+    int32_t *front[2];    // n      nodes infected in some simulation, this step / the next
+    int32_t *touched;     // n      nodes with a successful try this step
+    int32_t *heavy;       // n      frontier nodes of high degree this step
+    int32_t *fmark, *tmark;   // n  step stamps deduplicating the appends to front and touched
+    int32_t *counts;      // 4      lengths of front[0], front[1], touched, heavy
+    int32_t *count, *peak, *peak_step, *length, *fsize;   // B
+    uint8_t *done;        // B      1: no infected node left (or never started)
     int32_t *err;         // error bits (ERRB_SIR_ARG)
 };
 struct SirStep {
@@ -364,14 +369,14 @@ struct SirStep {
     uint64_t beta_thr;    // floor(beta 2^32): a try succeeds when its draw is below
     uint64_t gamma_thr;   // floor(gamma 2^32): recovery
 };
-int launch_sir_init(const int32_t *index_cases, int32_t B, int32_t n, const uint8_t *immune, int32_t num_sets,
+int launch_sir_init(const int32_t *index_cases, int32_t n, const uint8_t *immune, int32_t num_sets,
                     const int32_t *imm_set, const SirState &st, const Tune &t, cudaStream_t s);
-int launch_sir_step(const int32_t *rp, const int32_t *ci, int32_t n, int32_t B, int32_t step, const SirStep &p,
+int launch_sir_step(const int32_t *rp, const int32_t *ci, int32_t n, int32_t step, const SirStep &p,
                     const SirState &st, int64_t *active, const Tune &t, cudaStream_t s);
-int launch_sir_close(int32_t B, int32_t steps, const SirState &st, uint8_t *truncated, const Tune &t,
-                     cudaStream_t s);
-int launch_sir_tree(int32_t B, int32_t n, int32_t depth, int32_t min_size, const SirState &st, int64_t *spread,
+int launch_sir_close(int32_t steps, const SirState &st, uint8_t *truncated, const Tune &t, cudaStream_t s);
+int launch_sir_tree(int32_t n, int32_t depth, int32_t min_size, const SirState &st, int64_t *exact,
                     int64_t *infected, const Tune &t, cudaStream_t s);
+int launch_sir_cumulate(int32_t n, int32_t depth, int64_t *spread, const Tune &t, cudaStream_t s);
 // shards (ef_shard.cu; the partials' finalize in ef_final.cu)
 int launch_shard_range(const int32_t *rp, int32_t n, int64_t m, int32_t shard, int32_t nshards, int32_t *range,
                        cudaStream_t st);

@@ -15,34 +15,33 @@
 // and key = the 64-bit seed, first output word: a simulation's course
 // depends on its id and the seed only, not on the batch or the launch.
 //
-// Layout: per (simulation s, node v): a susceptibility bit (bit v & 31 of
-// word s * W + v / 32, W = ceil(n / 32): the only state the tries read, 1/8
-// of a state byte so that it stays in L2), at s * n + v the infector
-// (parent) and the smallest successful infector of the current step (cand).
-// Infected and recovered nodes are the ones without the bit and with a
-// parent, immune nodes the ones without either; recovery only leaves the
-// frontier.  The infected (s, u) pairs of a step form a frontier list of
-// 64-bit entries s << 32 | u; a step appends survivors and new infections
-// to the other list.  Kernels of a step:
-//   k_sir_spread  4 frontier entries per warp, 8 lanes each over the
-//                 entry's neighbours: tries, cand by atomicMin (the first
-//                 success appends x), the recovery draw (survivors append);
-//                 entries of degree > SIR_HEAVY are listed for
-//   k_sir_spread_heavy  a CTA per listed entry over its neighbours (hubs
-//                 would otherwise hold a warp for hundreds of rounds)
-//   k_sir_commit  over the new list: a node still susceptible becomes
-//                 infected with parent = cand
-//   k_sir_stats   per simulation: peak, peak step, length; clears the
-//                 emptied list's count for the next step
-// Launch shapes read the list counts from device memory, so the host only
-// reads the number of active simulations every SIR_CHECK steps.
+// Layout, node-major: a batch of B <= SIR_BATCH simulations runs together,
+// and each node keeps WB = ceil(B / 32) words of one bit per simulation:
+// susceptible, infected at the start of the step (inf[cur]), infected at the
+// start of the next (inf[nxt]), and infected during this step (newinf).  A
+// node infected in any simulation is in the step's frontier once; its
+// neighbour list is read once for all simulations, and for a neighbour x
+// the words inf[cur][u] & susc[x] say which simulations try the edge, the
+// words read by consecutive lanes.  cand (node-major, x * B + s) holds the
+// smallest successful infector of the step, parent (simulation-major, the
+// output layout) the infection tree.  Kernels of a step:
+//   k_sir_spread        a warp per frontier node: recovery draws (slot 0),
+//                       then (slot, word) lanes over the neighbours; nodes
+//                       of degree > SIR_HEAVY are listed for
+//   k_sir_spread_heavy  a CTA per listed node over its neighbours
+//   k_sir_commit        per node with a success: new infections, parents
+//   k_sir_clear         zeroes the frontier's inf[cur] words for reuse
+//   k_sir_stats         per simulation: peak, its step, length
+// Lists are deduplicated by per-node step stamps, per-simulation counts are
+// summed in shared memory per block, and the host reads whether any
+// simulation is still running every SIR_CHECK steps.
 #include "ef_internal.cuh"
 
 namespace ef {
 
 constexpr int32_t NO_CAND = 0x7fffffff;
 constexpr uint32_t RECOVER_WORD = 0xffffffffu;
-constexpr int SIR_HEAVY = 64;   // frontier entries of higher degree are tried by a CTA each
+constexpr int SIR_HEAVY = 256;   // frontier nodes of higher degree take a CTA each
 
 // Philox4x32-10, first output word only.
 __device__ __forceinline__ uint32_t philox_w0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t key) {
@@ -64,223 +63,234 @@ __device__ __forceinline__ uint32_t philox_w0(uint32_t c0, uint32_t c1, uint32_t
     return c0;
 }
 
-__device__ __forceinline__ uint64_t sir_entry(int s, int v) { return (uint64_t)(uint32_t)s << 32 | (uint32_t)v; }
+// Lane geometry of a warp over (slot, word) pairs: wbp = WB rounded up to a
+// power of two, 32 / wbp slots (nodes or neighbours) per warp.
+struct SirLanes {
+    int wbp, slots, slot, w;
+    bool wv;
+    __device__ __forceinline__ explicit SirLanes(int WB) {
+        wbp = 1;
+        while (wbp < WB) wbp <<= 1;
+        slots = 32 / wbp;
+        const int lane = threadIdx.x & 31;
+        slot = lane / wbp;
+        w = lane % wbp;
+        wv = w < WB;
+    }
+};
 
-__device__ __forceinline__ int64_t sir_words(int32_t n) { return ((int64_t)n + 31) >> 5; }
-
-__device__ __forceinline__ bool susceptible(const uint32_t *susc, int64_t wrow, int x) {
-    return (__ldg(susc + wrow + (x >> 5)) >> (x & 31)) & 1u;
+// Append v to list (count *cnt) unless it was appended with this stamp.
+__device__ __forceinline__ void sir_append(int32_t *list, int32_t *cnt, int32_t *mark, int v, int stamp) {
+    if (atomicExch(mark + v, stamp) != stamp) list[atomicAdd(cnt, 1)] = v;
 }
 
-// Susceptibility words (all nodes but the immune ones), parents and
-// candidates of every (simulation, node).
-__global__ void k_sir_init(int32_t B, int32_t n, const uint8_t *__restrict__ immune, int32_t num_sets,
-                           const int32_t *__restrict__ imm_set, SirState st) {
-    const int64_t W = sir_words(n), words = (int64_t)B * W, total = (int64_t)B * n;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
-        const int s = (int)(i / W);
-        const int v0 = (int)(i - (int64_t)s * W) * 32;
-        uint32_t w = 0;
-        int set = -1;
-        if (imm_set) {
-            set = imm_set[s];
+__global__ void k_sir_fill(int32_t *__restrict__ a, int64_t len, int32_t value) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = value;
+}
+
+// Susceptibility words: every simulation but those whose immune set holds v.
+__global__ void k_sir_init_susc(int32_t n, const uint8_t *__restrict__ immune, int32_t num_sets,
+                                const int32_t *__restrict__ imm_set, SirState st) {
+    const int64_t words = (int64_t)n * st.WB;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(i / st.WB), w = (int)(i - (int64_t)v * st.WB);
+        uint32_t word = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int s = w * 32 + b;
+            if (s >= st.B) break;
+            int set = imm_set ? imm_set[s] : -1;
             if (set >= num_sets) {
                 atomicOr(st.err, ERRB_SIR_ARG);
                 set = -1;
             }
+            if (set < 0 || !immune[(int64_t)set * n + v]) word |= 1u << b;
         }
-        for (int b = 0; b < 32 && v0 + b < n; ++b)
-            if (set < 0 || !immune[(int64_t)set * n + v0 + b]) w |= 1u << b;
-        st.susc[i] = w;
-    }
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-        st.parent[i] = -1;
-        st.cand[i] = NO_CAND;
+        st.susc[i] = word;
     }
 }
 
 // The index cases and the first frontier (an immune index case is an error).
-__global__ void k_sir_seed(const int32_t *__restrict__ index_cases, int32_t B, int32_t n, SirState st) {
-    const int64_t W = sir_words(n);
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < B; s += gridDim.x * blockDim.x) {
+__global__ void k_sir_seed(const int32_t *__restrict__ index_cases, int32_t n, SirState st) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < st.B; s += gridDim.x * blockDim.x) {
         const int u = index_cases[s];
         st.peak[s] = 1;
         st.peak_step[s] = 0;
         st.length[s] = 0;
-        st.count[s] = 0;
-        st.done[s] = 0;
+        st.count[s] = 1;
         st.fsize[s] = 1;
-        if (u < 0 || u >= n || !susceptible(st.susc, s * W, u)) {
+        st.done[s] = 0;
+        const uint32_t bit = 1u << (s & 31);
+        if (u < 0 || u >= n || !(st.susc[(int64_t)u * st.WB + (s >> 5)] & bit)) {
             atomicOr(st.err, ERRB_SIR_ARG);
-            st.done[s] = 1;   // no frontier entry: the simulation does not run
+            st.done[s] = 1;
+            st.count[s] = 0;
             st.fsize[s] = 0;
             continue;
         }
-        st.susc[s * W + (u >> 5)] &= ~(1u << (u & 31));   // one index case per row of words
+        atomicAnd(st.susc + (int64_t)u * st.WB + (s >> 5), ~bit);   // index cases may share a node
+        atomicOr(st.inf[0] + (int64_t)u * st.WB + (s >> 5), bit);
         st.parent[(int64_t)s * n + u] = u;
-        st.list[0][s] = sir_entry(s, u);
+        sir_append(st.front[0], st.counts + 0, st.fmark, u, -1);
     }
 }
 
-__device__ __forceinline__ void sir_append(bool app, uint64_t ent, uint64_t *__restrict__ nxt,
-                                           int64_t *__restrict__ cnxt, int32_t *__restrict__ count);
+// Tries of u's infected simulations (its inf[cur] words iw) over the
+// neighbours k_first, k_first + stride, ... (the warp's slots taking
+// consecutive neighbours).
+__device__ __forceinline__ void sir_tries(const int32_t *__restrict__ ci, int a, int D, int u, int t, uint32_t iw,
+                                          const SirLanes &L, int k_first, int stride, const SirStep &p,
+                                          const SirState &st) {
+    for (int k0 = k_first; k0 < D; k0 += stride) {
+        const int k = k0 + L.slot;
+        const int x = k < D ? ci[a + k] : -1;
+        uint32_t act = x >= 0 && L.wv ? iw & st.susc[(int64_t)x * st.WB + L.w] : 0u;
+        while (act) {
+            const int b = __ffs(act) - 1;
+            act &= act - 1;
+            const int s = L.w * 32 + b;
+            const uint32_t r = philox_w0((uint32_t)(p.sim_base + s), (uint32_t)t, (uint32_t)u, (uint32_t)x, p.seed);
+            if ((uint64_t)r < p.beta_thr && atomicMin(st.cand + (int64_t)x * st.B + s, u) == NO_CAND) {
+                atomicOr(st.newinf + (int64_t)x * st.WB + L.w, 1u << b);
+                sir_append(st.touched, st.counts + 2, st.tmark, x, t + 1);
+            }
+        }
+    }
+}
 
-// One step over the frontier list `cur` (count *ccur), appending to `nxt`;
-// entries of degree > SIR_HEAVY go to the heavy list instead.
+// One step over the frontier front[cur]: recoveries, survivors into
+// inf[nxt] and front[nxt], tries of the nodes of degree <= SIR_HEAVY.
 __global__ void __launch_bounds__(256) k_sir_spread(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                                    int32_t n, int32_t t, SirStep p, SirState st,
-                                                    const uint64_t *__restrict__ cur, const int64_t *__restrict__ ccur,
-                                                    uint64_t *__restrict__ nxt, int64_t *__restrict__ cnxt) {
-    const int lane = threadIdx.x & 31, oct = lane >> 3, l8 = lane & 7;
-    const int64_t total = *ccur;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4; base < total;
-         base += nwarps * 4) {
-        const int64_t item = base + oct;
-        const bool valid = item < total;
-        int s = 0, u = 0, a = 0, D = 0;
-        if (valid) {
-            const uint64_t e = cur[item];
-            s = (int)(e >> 32);
-            u = (int)(uint32_t)e;
-            a = rp[u];
-            D = rp[u + 1] - a;
-            if (D > SIR_HEAVY) {
-                // tried by k_sir_spread_heavy, a CTA per entry
-                if (l8 == 0) st.heavy[atomicAdd((unsigned long long *)st.heavy_count, 1ull)] = e;
-                D = 0;
-            }
-        }
-        const uint32_t sim = (uint32_t)(p.sim_base + s);
-        const int64_t row = (int64_t)s * n, wrow = s * sir_words(n);
-        // recovery (lane 0 of the octet): survivors stay in the frontier
-        bool app = false;
-        uint64_t ent = 0;
-        if (valid && l8 == 0) {
-            const uint32_t w = philox_w0(sim, (uint32_t)t, (uint32_t)u, RECOVER_WORD, p.seed);
-            if ((uint64_t)w >= p.gamma_thr) {
-                app = true;
-                ent = sir_entry(s, u);
-            }
-        }
-        int kmax = D;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
-        for (int k0 = 0;; k0 += 8) {
-            sir_append(app, ent, nxt, cnxt, st.count);   // this round's entries
-            if (k0 >= kmax) break;
-            app = false;
-            const int k = k0 + l8;
-            if (valid && k < D) {
-                const int x = ci[a + k];
-                if (susceptible(st.susc, wrow, x)) {
-                    const uint32_t w = philox_w0(sim, (uint32_t)t, (uint32_t)u, (uint32_t)x, p.seed);
-                    if ((uint64_t)w < p.beta_thr) {
-                        const int old = atomicMin(st.cand + row + x, u);
-                        if (old == NO_CAND) {
-                            app = true;
-                            ent = sir_entry(s, x);
-                        }
-                    }
-                }
-            }
-        }
-    }
-}
-
-// Appends the lanes' entries (app) to nxt with one list atomic per warp and
-// one count update per simulation; every lane of the warp calls it.
-__device__ __forceinline__ void sir_append(bool app, uint64_t ent, uint64_t *__restrict__ nxt,
-                                           int64_t *__restrict__ cnxt, int32_t *__restrict__ count) {
-    const int lane = threadIdx.x & 31;
-    const unsigned bal = __ballot_sync(FULL, app);
-    if (!bal) return;
-    int64_t pos = 0;
-    const int leader = __ffs(bal) - 1;
-    if (lane == leader) pos = atomicAdd((unsigned long long *)cnxt, (unsigned long long)__popc(bal));
-    pos = __shfl_sync(FULL, pos, leader);
-    if (app) {
-        nxt[pos + __popc(bal & ((1u << lane) - 1u))] = ent;
-        const int es = (int)(ent >> 32);
-        const unsigned peers = __match_any_sync(bal, es);
-        if (lane == __ffs(peers) - 1) atomicAdd(count + es, __popc(peers));
-    }
-}
-
-// The tries of the frontier entries of degree > SIR_HEAVY: a CTA per entry,
-// its threads over the neighbours.
-__global__ void __launch_bounds__(256) k_sir_spread_heavy(const int32_t *__restrict__ rp,
-                                                          const int32_t *__restrict__ ci, int32_t n, int32_t t,
-                                                          SirStep p, SirState st, uint64_t *__restrict__ nxt,
-                                                          int64_t *__restrict__ cnxt) {
-    const int64_t total = *st.heavy_count;
-    for (int64_t h = blockIdx.x; h < total; h += gridDim.x) {
-        const uint64_t e = st.heavy[h];
-        const int s = (int)(e >> 32), u = (int)(uint32_t)e;
+                                                    int32_t t, SirStep p, SirState st) {
+    __shared__ int s_rec[SIR_BATCH];
+    for (int i = threadIdx.x; i < st.B; i += blockDim.x) s_rec[i] = 0;
+    __syncthreads();
+    const int c = t & 1, nx = c ^ 1, lane = threadIdx.x & 31;
+    const SirLanes L(st.WB);
+    const int total = st.counts[c];
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < total; i += nwarps) {
+        const int u = st.front[c][i];
         const int a = rp[u], D = rp[u + 1] - a;
-        const uint32_t sim = (uint32_t)(p.sim_base + s);
-        const int64_t row = (int64_t)s * n, wrow = s * sir_words(n);
-        for (int k0 = 0; k0 < D; k0 += blockDim.x) {
-            const int k = k0 + threadIdx.x;
-            bool app = false;
-            uint64_t ent = 0;
-            if (k < D) {
-                const int x = ci[a + k];
-                if (susceptible(st.susc, wrow, x)) {
-                    const uint32_t w = philox_w0(sim, (uint32_t)t, (uint32_t)u, (uint32_t)x, p.seed);
-                    if ((uint64_t)w < p.beta_thr && atomicMin(st.cand + row + x, u) == NO_CAND) {
-                        app = true;
-                        ent = sir_entry(s, x);
-                    }
+        const uint32_t iw = L.wv ? st.inf[c][(int64_t)u * st.WB + L.w] : 0u;
+        uint32_t sv = iw;
+        if (L.slot == 0 && L.wv) {
+            uint32_t m = iw;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const int s = L.w * 32 + b;
+                const uint32_t r =
+                    philox_w0((uint32_t)(p.sim_base + s), (uint32_t)t, (uint32_t)u, RECOVER_WORD, p.seed);
+                if ((uint64_t)r < p.gamma_thr) {
+                    sv &= ~(1u << b);
+                    atomicAdd(s_rec + s, 1);
                 }
             }
-            sir_append(app, ent, nxt, cnxt, st.count);
+            st.inf[nx][(int64_t)u * st.WB + L.w] = sv;
         }
+        const bool survives = __any_sync(FULL, L.slot == 0 && sv != 0u);
+        if (survives && lane == 0) sir_append(st.front[nx], st.counts + nx, st.fmark, u, t + 1);
+        if (D > SIR_HEAVY) {
+            if (lane == 0) st.heavy[atomicAdd(st.counts + 3, 1)] = u;
+            continue;
+        }
+        sir_tries(ci, a, D, u, t, iw, L, 0, L.slots, p, st);
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < st.B; s += blockDim.x)
+        if (s_rec[s]) atomicSub(st.count + s, s_rec[s]);
+}
+
+__global__ void __launch_bounds__(256) k_sir_spread_heavy(const int32_t *__restrict__ rp,
+                                                          const int32_t *__restrict__ ci, int32_t t, SirStep p,
+                                                          SirState st) {
+    const int c = t & 1, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const SirLanes L(st.WB);
+    const int total = st.counts[3];
+    for (int i = blockIdx.x; i < total; i += gridDim.x) {
+        const int u = st.heavy[i];
+        const int a = rp[u], D = rp[u + 1] - a;
+        const uint32_t iw = L.wv ? st.inf[c][(int64_t)u * st.WB + L.w] : 0u;
+        sir_tries(ci, a, D, u, t, iw, L, wid * L.slots, nw * L.slots, p, st);
     }
 }
 
-// New infections of the step: the entries of `nxt` whose node is still
-// susceptible (the others are survivors).  Each entry is listed once, so its
-// bit is read plainly and cleared atomically (its word is shared).
-__global__ void k_sir_commit(int32_t n, SirState st, const uint64_t *__restrict__ nxt,
-                             const int64_t *__restrict__ cnxt) {
-    const int64_t total = *cnxt, W = sir_words(n);
+// New infections of the step: per node with a success, its newinf words.
+__global__ void __launch_bounds__(256) k_sir_commit(int32_t n, int32_t t, SirState st) {
+    __shared__ int s_new[SIR_BATCH];
+    for (int i = threadIdx.x; i < st.B; i += blockDim.x) s_new[i] = 0;
+    __syncthreads();
+    const int nx = (t & 1) ^ 1;
+    const SirLanes L(st.WB);
+    const int total = st.counts[2];
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const unsigned mine = (L.wbp == 32 ? FULL : (1u << L.wbp) - 1u) << (L.slot * L.wbp);
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * L.slots; base < total;
+         base += nwarps * L.slots) {
+        const int64_t i = base + L.slot;
+        const int x = i < total ? st.touched[i] : -1;
+        uint32_t nb = 0;
+        if (x >= 0 && L.wv) {
+            const int64_t j = (int64_t)x * st.WB + L.w;
+            nb = st.newinf[j];
+            if (nb) {
+                st.newinf[j] = 0;
+                st.susc[j] &= ~nb;
+                st.inf[nx][j] |= nb;
+                uint32_t m = nb;
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int s = L.w * 32 + b;
+                    int32_t *cs = st.cand + (int64_t)x * st.B + s;
+                    st.parent[(int64_t)s * n + x] = *cs;
+                    *cs = NO_CAND;
+                    atomicAdd(s_new + s, 1);
+                }
+            }
+        }
+        // the node joins the next frontier once (it may already be there as a survivor)
+        const unsigned any = __ballot_sync(FULL, nb != 0u);
+        if (L.w == 0 && (any & mine)) sir_append(st.front[nx], st.counts + nx, st.fmark, x, t + 1);
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < st.B; s += blockDim.x)
+        if (s_new[s]) {
+            atomicAdd(st.count + s, s_new[s]);
+            atomicAdd(st.fsize + s, s_new[s]);
+        }
+}
+
+// The frontier's words of inf[cur], zeroed: the buffer is the next step's inf[nxt].
+__global__ void k_sir_clear(int32_t t, SirState st) {
+    const int c = t & 1;
+    const int64_t total = (int64_t)st.counts[c] * st.WB;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t e = nxt[i];
-        const int s = (int)(e >> 32), x = (int)(uint32_t)e;
-        const int64_t j = (int64_t)s * n + x;
-        uint32_t *word = st.susc + s * W + (x >> 5);
-        const uint32_t bit = 1u << (x & 31);
-        if (*word & bit) {
-            atomicAnd(word, ~bit);
-            st.parent[j] = st.cand[j];
-            st.cand[j] = NO_CAND;
-            atomicAdd(st.fsize + s, 1);
-        }
+        const int v = st.front[c][i / st.WB];
+        st.inf[c][(int64_t)v * st.WB + (i % st.WB)] = 0u;
     }
 }
 
-// After step t: |I_{t+1}| per simulation is count[s].  active[t & 1] counts
-// warps with a simulation still running; active[(t + 1) & 1] is cleared for
-// the next step.
-__global__ void k_sir_stats(int32_t B, int32_t t, SirState st, int64_t *__restrict__ ccur,
-                            int64_t *__restrict__ active) {
+// After step t: count[s] = infected at the start of step t + 1.  active[t & 1]
+// counts warps with a simulation still running; the emptied lists and
+// active[(t + 1) & 1] are cleared for the next step.
+__global__ void k_sir_stats(int32_t t, SirState st, int64_t *__restrict__ active) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *ccur = 0;   // the list just read is the next step's output
-        *st.heavy_count = 0;
+        st.counts[t & 1] = 0;
+        st.counts[2] = 0;
+        st.counts[3] = 0;
         active[(t + 1) & 1] = 0;
     }
     int act = 0;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < B; s += gridDim.x * blockDim.x) {
-        const int c = st.count[s];
-        st.count[s] = 0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < st.B; s += gridDim.x * blockDim.x) {
         if (st.done[s]) continue;
-        if (c > st.peak[s]) {
-            st.peak[s] = c;
+        const int cnt = st.count[s];
+        if (cnt > st.peak[s]) {
+            st.peak[s] = cnt;
             st.peak_step[s] = t + 1;
         }
-        if (c == 0) {
+        if (cnt == 0) {
             st.length[s] = t + 1;
             st.done[s] = 1;
         } else {
@@ -292,8 +302,8 @@ __global__ void k_sir_stats(int32_t B, int32_t t, SirState st, int64_t *__restri
 }
 
 // Simulations still running after the last step: truncated at `steps`.
-__global__ void k_sir_close(int32_t B, int32_t steps, SirState st, uint8_t *__restrict__ truncated) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < B; s += gridDim.x * blockDim.x) {
+__global__ void k_sir_close(int32_t steps, SirState st, uint8_t *__restrict__ truncated) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < st.B; s += gridDim.x * blockDim.x) {
         const bool tr = !st.done[s];
         if (tr) st.length[s] = steps;
         if (truncated) truncated[s] = tr;
@@ -304,9 +314,9 @@ __global__ void k_sir_close(int32_t B, int32_t steps, SirState st, uint8_t *__re
 // ancestor at generation g; exact[g-1][anc] counts those, over simulations
 // with final size >= min_size.  infected[v] counts those simulations in
 // which v was infected.
-__global__ void k_sir_tree(int32_t B, int32_t n, int32_t depth, int32_t min_size, SirState st,
+__global__ void k_sir_tree(int32_t n, int32_t depth, int32_t min_size, SirState st,
                            unsigned long long *__restrict__ exact, unsigned long long *__restrict__ infected) {
-    const int64_t total = (int64_t)B * n;
+    const int64_t total = (int64_t)st.B * n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int s = (int)(i / n), v = (int)(i - (int64_t)s * n);
         const int32_t *par = st.parent + (int64_t)s * n;
@@ -339,39 +349,42 @@ static inline unsigned grid_for(int64_t work, int per_block, int64_t cap) {
     return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
-int launch_sir_init(const int32_t *index_cases, int32_t B, int32_t n, const uint8_t *immune, int32_t num_sets,
+int launch_sir_init(const int32_t *index_cases, int32_t n, const uint8_t *immune, int32_t num_sets,
                     const int32_t *imm_set, const SirState &st, const Tune &t, cudaStream_t s) {
-    k_sir_init<<<grid_for((int64_t)B * n, 256, (int64_t)t.num_sms * 32), 256, 0, s>>>(B, n, immune, num_sets,
-                                                                                     imm_set, st);
-    k_sir_seed<<<grid_for(B, 256, (int64_t)t.num_sms * 4), 256, 0, s>>>(index_cases, B, n, st);
+    const int64_t cap = (int64_t)t.num_sms * 32, nb = (int64_t)n * st.B;
+    k_sir_fill<<<grid_for(nb, 256, cap), 256, 0, s>>>(st.cand, nb, NO_CAND);
+    k_sir_fill<<<grid_for(nb, 256, cap), 256, 0, s>>>(st.parent, nb, -1);
+    k_sir_init_susc<<<grid_for((int64_t)n * st.WB, 256, cap), 256, 0, s>>>(n, immune, num_sets, imm_set, st);
+    k_sir_seed<<<grid_for(st.B, 256, cap), 256, 0, s>>>(index_cases, n, st);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_sir_step(const int32_t *rp, const int32_t *ci, int32_t n, int32_t B, int32_t step, const SirStep &p,
+int launch_sir_step(const int32_t *rp, const int32_t *ci, int32_t n, int32_t step, const SirStep &p,
                     const SirState &st, int64_t *active, const Tune &t, cudaStream_t s) {
-    const int c = step & 1;
-    uint64_t *cur = st.list[c], *nxt = st.list[c ^ 1];
-    int64_t *ccur = st.list_count + c, *cnxt = st.list_count + (c ^ 1);
-    k_sir_spread<<<t.num_sms * 8, 256, 0, s>>>(rp, ci, n, step, p, st, cur, ccur, nxt, cnxt);
-    k_sir_spread_heavy<<<t.num_sms * 8, 256, 0, s>>>(rp, ci, n, step, p, st, nxt, cnxt);
-    k_sir_commit<<<t.num_sms * 8, 256, 0, s>>>(n, st, nxt, cnxt);
-    k_sir_stats<<<grid_for(B, 256, (int64_t)t.num_sms * 4), 256, 0, s>>>(B, step, st, ccur, active);
+    const unsigned g = (unsigned)t.num_sms * 8;
+    k_sir_spread<<<g, 256, 0, s>>>(rp, ci, step, p, st);
+    k_sir_spread_heavy<<<g, 256, 0, s>>>(rp, ci, step, p, st);
+    k_sir_commit<<<g, 256, 0, s>>>(n, step, st);
+    k_sir_clear<<<g, 256, 0, s>>>(step, st);
+    k_sir_stats<<<grid_for(st.B, 256, (int64_t)t.num_sms * 4), 256, 0, s>>>(step, st, active);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_sir_close(int32_t B, int32_t steps, const SirState &st, uint8_t *truncated, const Tune &t,
-                     cudaStream_t s) {
-    k_sir_close<<<grid_for(B, 256, (int64_t)t.num_sms * 4), 256, 0, s>>>(B, steps, st, truncated);
+int launch_sir_close(int32_t steps, const SirState &st, uint8_t *truncated, const Tune &t, cudaStream_t s) {
+    k_sir_close<<<grid_for(st.B, 256, (int64_t)t.num_sms * 4), 256, 0, s>>>(steps, st, truncated);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_sir_tree(int32_t B, int32_t n, int32_t depth, int32_t min_size, const SirState &st, int64_t *spread,
+int launch_sir_tree(int32_t n, int32_t depth, int32_t min_size, const SirState &st, int64_t *exact,
                     int64_t *infected, const Tune &t, cudaStream_t s) {
-    k_sir_tree<<<grid_for((int64_t)B * n, 256, (int64_t)t.num_sms * 32), 256, 0, s>>>(
-        B, n, depth, min_size, st, reinterpret_cast<unsigned long long *>(spread),
+    k_sir_tree<<<grid_for((int64_t)st.B * n, 256, (int64_t)t.num_sms * 32), 256, 0, s>>>(
+        n, depth, min_size, st, reinterpret_cast<unsigned long long *>(exact),
         reinterpret_cast<unsigned long long *>(infected));
-    if (spread && depth > 0)
-        k_sir_cumulate<<<grid_for(n, 256, (int64_t)t.num_sms * 32), 256, 0, s>>>(n, depth, spread);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_sir_cumulate(int32_t n, int32_t depth, int64_t *spread, const Tune &t, cudaStream_t s) {
+    k_sir_cumulate<<<grid_for(n, 256, (int64_t)t.num_sms * 32), 256, 0, s>>>(n, depth, spread);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
