@@ -138,21 +138,35 @@ __global__ void k_sir_seed(const int32_t *__restrict__ index_cases, int32_t n, S
 // Tries of u's infected simulations (its inf[cur] words iw) over the
 // neighbours k_first, k_first + stride, ... (the warp's slots taking
 // consecutive neighbours).
+// The loads of SIR_UNROLL neighbours are issued before any of their tries.
+constexpr int SIR_UNROLL = 4;
 __device__ __forceinline__ void sir_tries(const int32_t *__restrict__ ci, int a, int D, int u, int t, uint32_t iw,
                                           const SirLanes &L, int k_first, int stride, const SirStep &p,
                                           const SirState &st) {
-    for (int k0 = k_first; k0 < D; k0 += stride) {
-        const int k = k0 + L.slot;
-        const int x = k < D ? ci[a + k] : -1;
-        uint32_t act = x >= 0 && L.wv ? iw & st.susc[(int64_t)x * st.WB + L.w] : 0u;
-        while (act) {
-            const int b = __ffs(act) - 1;
-            act &= act - 1;
-            const int s = L.w * 32 + b;
-            const uint32_t r = philox_w0((uint32_t)(p.sim_base + s), (uint32_t)t, (uint32_t)u, (uint32_t)x, p.seed);
-            if ((uint64_t)r < p.beta_thr && atomicMin(st.cand + (int64_t)x * st.B + s, u) == NO_CAND) {
-                atomicOr(st.newinf + (int64_t)x * st.WB + L.w, 1u << b);
-                sir_append(st.touched, st.counts + 2, st.tmark, x, t + 1);
+    for (int k0 = k_first; k0 < D; k0 += SIR_UNROLL * stride) {
+        int x[SIR_UNROLL];
+        uint32_t act[SIR_UNROLL];
+#pragma unroll
+        for (int q = 0; q < SIR_UNROLL; ++q) {
+            const int k = k0 + q * stride + L.slot;
+            x[q] = k < D ? ci[a + k] : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < SIR_UNROLL; ++q)
+            act[q] = x[q] >= 0 && L.wv ? iw & st.susc[(int64_t)x[q] * st.WB + L.w] : 0u;
+#pragma unroll
+        for (int q = 0; q < SIR_UNROLL; ++q) {
+            uint32_t m = act[q];
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const int s = L.w * 32 + b;
+                const uint32_t r =
+                    philox_w0((uint32_t)(p.sim_base + s), (uint32_t)t, (uint32_t)u, (uint32_t)x[q], p.seed);
+                if ((uint64_t)r < p.beta_thr && atomicMin(st.cand + (int64_t)x[q] * st.B + s, u) == NO_CAND) {
+                    atomicOr(st.newinf + (int64_t)x[q] * st.WB + L.w, 1u << b);
+                    sir_append(st.touched, st.counts + 2, st.tmark, x[q], t + 1);
+                }
             }
         }
     }
