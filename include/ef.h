@@ -310,8 +310,10 @@ typedef struct {
  *   immune_set: int32[num_sims] (device) the set of each simulation (-1:
  *   none) or NULL.
  * An index case outside [0, n) or immune, or a set index >= num_immune_sets,
- * gives EF_ERR_ARG before any step runs.  Device memory: about 8 bytes per
- * (simulation, node) pair.  host_io and async give EF_ERR_ARG.
+ * gives EF_ERR_ARG before any step runs.  Simulations run in batches of up
+ * to 1024 (one bit per simulation per node, node-major); device memory is
+ * about 8 bytes per (simulation, node) pair of a batch.  host_io and async
+ * give EF_ERR_ARG.
  */
 int ef_sir_run(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m,
                const int32_t *index_cases, int32_t num_sims,
