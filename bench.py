@@ -63,8 +63,8 @@ def algorithmic_bytes(g, st):
     big = d[d > 32]
     csr = 4 * (n + 1) + 4 * m
     return {
-        # row_ptr + col_idx read; D, sigma1, sigma2, outdeg, fp_row written
-        "prep_ms": csr + 4 * n + 16 * n + 4 * n + 8 * n,
+        # row_ptr + col_idx read; D, sigma1, sigma2, outdeg written
+        "prep_ms": csr + 4 * n + 16 * n + 4 * n,
         # CSR + outdeg read; out_ptr, out_col/out_D/out_src (m/2 each), omega written
         "orient_ms": csr + 4 * n + 4 * (n + 1) + 12 * (m // 2) + 8 * n,
         # rows of the middle nodes read; Ccenter written, one 8-byte credit per row entry
@@ -74,8 +74,8 @@ def algorithmic_bytes(g, st):
         "tri_hash_ms": 4 * (n + 1) + 4 * (m // 2) + 8 * (m // 2),
         # out_ptr, out_col, out_D, out_src read; qacc, tcnt written
         "tri_pairs_ms": 4 * (n + 1) + 12 * (m // 2) + 16 * n,
-        # D and 9 eight-byte per-node arrays read, EF written
-        "finalize_ms": 4 * n + 9 * 8 * n + 8 * n,
+        # D and 7 eight-byte per-node arrays read, EF written
+        "finalize_ms": 4 * n + 7 * 8 * n + 8 * n,
     }
 
 
@@ -192,6 +192,26 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def class_evals(g, hub_min: int = 513) -> int:
+    """f evaluations of the degree-class wedge kernels: K (K + 1) per middle
+    node of degree > 32, K its classes.  Neighbour degrees below 256 (warp
+    kernel, degree < hub_min) or 2048 (CTA kernel) merge into one class per
+    degree; larger ones are a class each, as the kernels build them."""
+    d = g.degrees.astype(np.int64)
+    big = np.nonzero(d > 32)[0]
+    if big.size == 0:
+        return 0
+    rp = g.row_ptr.astype(np.int64)
+    lens = d[big]
+    owner = np.repeat(np.arange(big.size), lens)
+    idx = np.arange(owner.size) - np.repeat(np.cumsum(lens) - lens, lens) + np.repeat(rp[big], lens)
+    dn = d[g.col_idx[idx]]
+    dense = dn < np.where(d[big] < hub_min, 256, 2048)[owner]
+    keys = np.unique(owner[dense] * (int(d.max()) + 1) + dn[dense])
+    K = np.bincount(keys // (int(d.max()) + 1), minlength=big.size) + np.bincount(owner[~dense], minlength=big.size)
+    return int((K * (K + 1)).sum())
 
 
 def graph_stats(g):
@@ -634,6 +654,18 @@ def run_ours(args):
                 "algorithmic_bytes": alg[dom], "launch_ms": per[dom], "peak_source": src,
                 "note": "bytes = each input read once and each output written once (per-pass formulas "
                         "in DESIGN.md); " + PASS_NOTE[dom]}
+    # the wedge passes against the MUFU issue bound: one lg2 per f evaluation,
+    # 16 special-function results per SM per clock
+    evals = st["small_evals"] + class_evals(g)
+    wedge_ms = per["wedge_small_ms"] + per["wedge_big_ms"]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_max_mhz") or 2070.0
+    mufu = sms * 16 * mhz * 1e6
+    roofline_alu = {"bound": "alu", "kernels": "wedge passes (k_wedge_small, k_wedge_mid, k_wedge_hub)",
+                    "f_evaluations": evals, "achieved": evals / (wedge_ms / 1e3) / 1e9 if wedge_ms > 0 else None,
+                    "peak": mufu / 1e9, "unit": "Geval/s",
+                    "frac": evals / (wedge_ms / 1e3) / mufu if wedge_ms > 0 else None,
+                    "peak_source": f"{sms} SMs x 16 MUFU results per clock x {mhz:.0f} MHz"}
     path_bytes = 4 * (n + 1) + 4 * g.nnz + 8 * n
     roofline_path = {"bound": "hbm", "algorithmic_bytes": path_bytes,
                      "achieved": path_bytes / (ms_step / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
@@ -654,6 +686,8 @@ def run_ours(args):
         "passes_ms": per,
         "roofline": roofline,
         "roofline_path": roofline_path,
+        "roofline_alu": roofline_alu,
+        "credits_per_s": 4 * value,
         "passes_gbs": {k: alg[k] / (per[k] / 1e3) / 1e9 if per[k] > 0 else None for k in PASSES},
         "e2e": e2e,
         "gpu_launches": int(passes["kernels"]),
