@@ -105,6 +105,40 @@ def test_batched_against_oracle(ctx, precision):
         np.testing.assert_allclose(got["ef"], ref["EF"], rtol=0, atol=EF_ATOL32)
 
 
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_full_size_ws_batch_sampled(ctx, precision):
+    """The 4096-graph Watts-Strogatz workload at full size, run as the bench
+    runs it (one ef_compute_batched call replayed as a CUDA graph): every
+    node's N against its closed form, sum N = 4W, and sampled nodes (random,
+    the ends of the largest and smallest graphs) against the vertex oracle."""
+    import torch
+    import paper_2306_00606_gb300 as ef
+    g = synth.workload(4)
+    off = g.graph_off
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    res = _alloc(g.n)
+    for _ in range(2):   # the second call replays the captured graph
+        ef.ef_compute_batched(ctx.handle, rp, ci, off, precision=precision, graph=True, **res)
+    got = _host(res)
+    d = np.diff(g.row_ptr).astype(np.int64)
+    sig1 = np.add.reduceat(d[g.col_idx], g.row_ptr[:-1].astype(np.int64), dtype=np.int64)
+    np.testing.assert_array_equal(got["n_clusters"], d * (d - 2) + sig1)
+    assert int(got["n_clusters"].sum()) == 4 * g.wedges()
+    sizes = np.diff(off)
+    big, small = int(np.argmax(sizes)), int(np.argmin(sizes))
+    rng = np.random.default_rng(4)
+    nodes = np.unique(np.concatenate([rng.choice(g.n, 48, replace=False), [off[big], off[big + 1] - 1],
+                                      [off[small], off[small + 1] - 1], [int(np.argmax(d))]])).astype(np.int32)
+    ref = oracle.vertex(g, nodes)
+    for k, r in (("n_clusters", "N"), ("s", "S"), ("triangles", "t"), ("flag", "flag")):
+        np.testing.assert_array_equal(got[k][nodes], ref[r])
+    if precision == "fp64":
+        np.testing.assert_allclose(got["ef"][nodes], ref["EF"], rtol=EF_RTOL64, atol=1e-12)
+    else:
+        np.testing.assert_allclose(got["ef"][nodes], ref["EF"], rtol=0, atol=EF_ATOL32)
+
+
 def test_batched_rejects_edge_between_graphs(ctx):
     import paper_2306_00606_gb300 as ef
     parts = [synth.cycle(20), synth.cycle(30)]

@@ -171,11 +171,11 @@ def _sample(g, k_random, k_hub, rng, hub_rank_lo=20):
 
 
 @pytest.mark.parametrize("precision", ["fp32c", "fp64"])
-@pytest.mark.parametrize("idx", [2, 3])
+@pytest.mark.parametrize("idx", [2, 3, 5])
 def test_full_size_workloads_sampled(ctx, idx, precision):
-    """BA n=1e6 m=5 and the power-law model n=4e6 at full size: every node's N_v
-    against its closed form, sum N = 4W, and sampled nodes (hubs included)
-    against the vertex-centric oracle."""
+    """BA n=1e6 m=5, the power-law model n=4e6 and BA n=1.6e7 m=4 at full
+    size: every node's N_v against its closed form, sum N = 4W, and sampled
+    nodes (hubs included) against the vertex-centric oracle."""
     g = synth.workload(idx)
     got = run(ctx, g, precision)
     np.testing.assert_array_equal(got["n_clusters"], _closed_counts(g))
