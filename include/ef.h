@@ -123,6 +123,12 @@ typedef struct {
                                step, 1 four (0) */
     int32_t grid_per_sm;    /* blocks per SM of the grid-stride row passes
                                (1..256; 64) */
+    int32_t layout;         /* order of the oriented out-lists: 1 node order
+                               (keeps a graph's own locality), 2 by degree
+                               class (lists of similar degree share cache
+                               lines), 0 automatic: node order for
+                               ef_compute_batched, degree classes otherwise
+                               (0) */
 } ef_tuning;
 
 /* Create a context on CUDA device `device` issuing work on `stream`
@@ -181,7 +187,7 @@ int ef_set_tuning(ef_ctx *ctx, const ef_tuning *t);
 
 /*
  * Autotuner: validates the graph once (unless trust_input), then times
- * candidate launch parameters on it (coordinate descent over the four
+ * candidate launch parameters on it (coordinate descent over the five
  * ef_tuning fields, two sweeps; each candidate one warm-up and `reps` timed
  * runs as a replayed CUDA graph, CUDA events on the context stream), keeps
  * the fastest on the context and returns it in *best.  A batch is tuned by

@@ -111,7 +111,7 @@ class ef_rank_stats(ctypes.Structure):
 
 class ef_tuning(ctypes.Structure):
     _fields_ = [("row_thread_max", ctypes.c_int32), ("hub_min", ctypes.c_int32), ("tri_variant", ctypes.c_int32),
-                ("grid_per_sm", ctypes.c_int32)]
+                ("grid_per_sm", ctypes.c_int32), ("layout", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

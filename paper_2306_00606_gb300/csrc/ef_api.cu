@@ -43,10 +43,9 @@ struct GraphKey {
     int64_t m, fcap;
     int32_t n, G, precision, wedge_mode, trust, pad;
     ef::Tune tune;
-    int32_t pad2;
     bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
-static_assert(sizeof(GraphKey) == 11 * 8 + 2 * 8 + 6 * 4 + sizeof(ef::Tune) + 4, "GraphKey has padding");
+static_assert(sizeof(GraphKey) == 11 * 8 + 2 * 8 + 6 * 4 + sizeof(ef::Tune), "GraphKey has padding");
 
 }  // namespace
 
@@ -201,7 +200,7 @@ int part_b(ef_ctx *ctx, const Job &j, const ef::Scratch &s, int64_t fcap, bool p
     using namespace ef;
     const Tune &t = ctx->tune;
     LAUNCH(launch_ftab(s.ftab, s.tq, s.counters, fcap, st), "f table");
-    LAUNCH(launch_orient(j.rp, j.ci, j.n, j.m, s, t, st), "orientation");
+    LAUNCH(launch_orient(j.rp, j.ci, j.n, j.m, s, t, st, nullptr, nullptr, j.goff_dev != nullptr), "orientation");
     if (prof) CU(cudaEventRecord(ctx->ev[2], st));
     LAUNCH(launch_wedge_small(j.rp, j.ci, s, j.o.precision, j.n, t, st), "small wedge");
     if (prof) CU(cudaEventRecord(ctx->ev[3], st));
@@ -405,23 +404,26 @@ int run_job(ef_ctx *ctx, Job j, const ef_outputs *host_out) {
 int check_tuning(ef_ctx *ctx, const ef_tuning &t) {
     if (t.row_thread_max < 1 || t.row_thread_max > ef::SMALL_MAX || t.hub_min < ef::SMALL_MAX + 1 ||
         t.hub_min > ef::MID_MAX + 1 || t.tri_variant < 0 || t.tri_variant > 1 || t.grid_per_sm < 1 ||
-        t.grid_per_sm > 256) {
+        t.grid_per_sm > 256 || t.layout < 0 || t.layout > 2) {
         set_err(ctx, "tuning out of range: row_thread_max %d (1..%d), hub_min %d (%d..%d), tri_variant %d (0..1), "
-                     "grid_per_sm %d (1..256)",
+                     "grid_per_sm %d (1..256), layout %d (0..2)",
                 t.row_thread_max, ef::SMALL_MAX, t.hub_min, ef::SMALL_MAX + 1, ef::MID_MAX + 1, t.tri_variant,
-                t.grid_per_sm);
+                t.grid_per_sm, t.layout);
         return EF_ERR_ARG;
     }
     return EF_OK;
 }
 
-ef_tuning to_abi(const ef::Tune &t) { return ef_tuning{t.row_thread_max, t.hub_min, t.tri_variant, t.grid_per_sm}; }
+ef_tuning to_abi(const ef::Tune &t) {
+    return ef_tuning{t.row_thread_max, t.hub_min, t.tri_variant, t.grid_per_sm, t.layout};
+}
 
 void from_abi(ef::Tune &t, const ef_tuning &a) {
     t.row_thread_max = a.row_thread_max;
     t.hub_min = a.hub_min;
     t.tri_variant = a.tri_variant;
     t.grid_per_sm = a.grid_per_sm;
+    t.layout = a.layout;
 }
 
 std::mutex g_default_mu;
@@ -821,19 +823,20 @@ int ef_autotune(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_opt
         return EF_OK;
     };
     // coordinate descent, two sweeps over the knobs
-    static const int rows[] = {8, 16, 32}, hubs[] = {129, 257, 513}, tris[] = {0, 1}, grids[] = {16, 32, 64, 128};
+    static const int rows[] = {8, 16, 32}, hubs[] = {129, 257, 513}, tris[] = {0, 1}, grids[] = {16, 32, 64, 128},
+                     layouts[] = {1, 2};
     ef::Tune cur = ctx->tune;
     double cur_ms;
     rc = time_it(cur_ms);
     if (rc) { ctx->tune = start; return rc; }
     for (int sweep = 0; sweep < 2; ++sweep) {
-        for (int knob = 0; knob < 4; ++knob) {
-            const int *vals = knob == 0 ? rows : knob == 1 ? hubs : knob == 2 ? tris : grids;
-            const int nv = knob == 0 ? 3 : knob == 1 ? 3 : knob == 2 ? 2 : 4;
+        for (int knob = 0; knob < 5; ++knob) {
+            const int *vals = knob == 0 ? rows : knob == 1 ? hubs : knob == 2 ? tris : knob == 3 ? grids : layouts;
+            const int nv = knob == 0 ? 3 : knob == 1 ? 3 : knob == 2 ? 2 : knob == 3 ? 4 : 2;
             for (int i = 0; i < nv; ++i) {
                 ef::Tune cand = cur;
                 int &field = knob == 0 ? cand.row_thread_max : knob == 1 ? cand.hub_min
-                             : knob == 2 ? cand.tri_variant : cand.grid_per_sm;
+                             : knob == 2 ? cand.tri_variant : knob == 3 ? cand.grid_per_sm : cand.layout;
                 if (field == vals[i]) continue;
                 field = vals[i];
                 ctx->tune = cand;

@@ -91,6 +91,7 @@ struct Tune {
     int hub_min = MID_MAX + 1;        // rows / middle nodes of degree >= this take a CTA (33..MID_MAX+1)
     int tri_variant = 0;              // pair-test kernel: 0 two candidates per lane step, 1 four
     int grid_per_sm = 64;             // blocks per SM of the grid-stride row passes
+    int layout = 0;                   // oriented CSR: 0 automatic, 1 node order, 2 degree-bin order
     int num_sms = 0;
     unsigned grid(int64_t work, int per_block) const {
         int64_t g = (work + per_block - 1) / per_block;
@@ -313,8 +314,10 @@ struct RankScratch {
 namespace ef {
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
                   cudaStream_t st);
+// The out-lists in degree-bin order (t.layout 2, or 0 on a single graph) or
+// node order (t.layout 1, or 0 on a batch: the graphs' own locality).
 int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
-                  cudaStream_t st, int32_t *nmin = nullptr, int32_t *nmax = nullptr);
+                  cudaStream_t st, int32_t *nmin = nullptr, int32_t *nmax = nullptr, bool batched = false);
 int launch_big_items(const Scratch &s, int32_t n, cudaStream_t st);
 int launch_batch_check(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const int64_t *goff, int32_t G,
                        const Scratch &s, const Tune &t, cudaStream_t st);

@@ -632,12 +632,18 @@ int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
 
 // Oriented CSR and omega.
 int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
-                  cudaStream_t st, int32_t *nmin, int32_t *nmax) {
-    // out-list offsets in layout order (degree-0 nodes keep offset 0 and an empty list)
-    if (cudaMemsetAsync(s.out_ptr, 0, (size_t)(n + 1) * sizeof(int32_t), st) != cudaSuccess) return -1;
-    k_layout_gather<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.bins, s.counters, n, s.outdeg, s.lay_node, s.lay_ptr);
-    if (launch_scan(s.lay_ptr, s.lay_ptr, n, s.scan_tmp, st)) return -1;
-    k_layout_scatter<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.counters, n, s.lay_node, s.lay_ptr, s.out_ptr);
+                  cudaStream_t st, int32_t *nmin, int32_t *nmax, bool batched) {
+    const bool bins = t.layout == 2 || (t.layout == 0 && !batched);
+    if (bins) {
+        // out-list offsets in layout order (degree-0 nodes keep offset 0 and an empty list)
+        if (cudaMemsetAsync(s.out_ptr, 0, (size_t)(n + 1) * sizeof(int32_t), st) != cudaSuccess) return -1;
+        k_layout_gather<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.bins, s.counters, n, s.outdeg, s.lay_node,
+                                                                 s.lay_ptr);
+        if (launch_scan(s.lay_ptr, s.lay_ptr, n, s.scan_tmp, st)) return -1;
+        k_layout_scatter<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.counters, n, s.lay_node, s.lay_ptr, s.out_ptr);
+    } else if (launch_scan(s.outdeg, s.out_ptr, n, s.scan_tmp, st)) {
+        return -1;
+    }
     k_node_info<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.D, s.sig1, s.out_ptr, s.outdeg, n, s.info);
     const Orient o{ci, s.info, s.out_col, s.out_D, s.out_src, s.out_rng, nmin, nmax, n};
     k_orient<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, n, m, t.row_thread_max, t.hub_min, o, s.out_ptr, s.omega);
