@@ -126,9 +126,11 @@ typedef struct {
     int32_t layout;         /* order of the oriented out-lists: 1 node order
                                (keeps a graph's own locality), 2 by degree
                                class (lists of similar degree share cache
-                               lines), 0 automatic: node order for
-                               ef_compute_batched, degree classes otherwise
-                               (0) */
+                               lines), 0 automatic: degree classes when the
+                               nodes of degree > 32 span more than half of
+                               the ids, else node order; with trust_input
+                               (nothing read back) degree classes for one
+                               graph and node order for a batch (0) */
 } ef_tuning;
 
 /* Create a context on CUDA device `device` issuing work on `stream`

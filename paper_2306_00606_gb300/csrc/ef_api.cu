@@ -41,7 +41,7 @@ struct GraphKey {
     const void *rp, *ci, *goff_dev, *scratch, *ftab;
     const void *outs[6];
     int64_t m, fcap;
-    int32_t n, G, precision, wedge_mode, trust, pad;
+    int32_t n, G, precision, wedge_mode, trust, bins;
     ef::Tune tune;
     bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
@@ -74,6 +74,7 @@ struct ef_ctx {
     void *acts = nullptr;            // training activations
     size_t acts_bytes = 0;
     double *dtmp = nullptr;          // small device scratch (feature sums)
+    bool bins = true;                // out-lists of the current graph in degree-bin order (bin_layout)
     void *sir = nullptr;             // SIR simulation state
     size_t sir_bytes = 0;
 };
@@ -200,7 +201,7 @@ int part_b(ef_ctx *ctx, const Job &j, const ef::Scratch &s, int64_t fcap, bool p
     using namespace ef;
     const Tune &t = ctx->tune;
     LAUNCH(launch_ftab(s.ftab, s.tq, s.counters, fcap, st), "f table");
-    LAUNCH(launch_orient(j.rp, j.ci, j.n, j.m, s, t, st, nullptr, nullptr, j.goff_dev != nullptr), "orientation");
+    LAUNCH(launch_orient(j.rp, j.ci, j.n, j.m, s, t, st, nullptr, nullptr, ctx->bins), "orientation");
     if (prof) CU(cudaEventRecord(ctx->ev[2], st));
     LAUNCH(launch_wedge_small(j.rp, j.ci, s, j.o.precision, j.n, t, st), "small wedge");
     if (prof) CU(cudaEventRecord(ctx->ev[3], st));
@@ -264,6 +265,7 @@ int compute_device(ef_ctx *ctx, const Job &j) {
     if (o.trust_input) {
         const int64_t bound = (int64_t)j.n - 1 < j.m ? (int64_t)j.n - 1 : j.m;
         fcap = 3 * (bound > 0 ? bound : 0) + 1;
+        ctx->bins = bin_layout(ctx->tune, nullptr, j.n, j.goff_dev != nullptr);
     } else {
         if (prof) CU(cudaEventRecord(ctx->ev[0], st));
         rc = part_a(ctx, j, s, st);
@@ -272,6 +274,7 @@ int compute_device(ef_ctx *ctx, const Job &j) {
         CU(cudaStreamSynchronize(st));
         if (const int bits = prep_error_bits(ctx->h_counters)) return graph_error(ctx, bits);
         fcap = 3 * (int64_t)ctx->h_counters[CNT_MAXDEG] + 1;
+        ctx->bins = bin_layout(ctx->tune, ctx->h_counters, j.n, j.goff_dev != nullptr);
     }
     // f table (double) followed by the fixed-point triangle corrections (int64)
     size_t have = (size_t)ctx->ftab_cap * 2 * sizeof(double);
@@ -298,6 +301,7 @@ int compute_device(ef_ctx *ctx, const Job &j) {
         key.precision = o.precision;
         key.wedge_mode = o.wedge_mode;
         key.trust = o.trust_input;
+        key.bins = ctx->bins;
         key.tune = ctx->tune;
         rc = run_graph(ctx, key, [&](cudaStream_t cs) {
             if (o.trust_input) {
@@ -474,12 +478,14 @@ int prepare_graph(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, 
     if (o.trust_input) {
         const int64_t bound = (int64_t)n - 1 < m ? (int64_t)n - 1 : m;
         fcap = 3 * (bound > 0 ? bound : 0) + 1;
+        ctx->bins = bin_layout(ctx->tune, nullptr, n, false);
     } else {
         CU(cudaMemcpyAsync(ctx->h_counters, s.counters, NUM_COUNTERS * sizeof(int32_t), cudaMemcpyDeviceToHost,
                            ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
         if (const int bits = prep_error_bits(ctx->h_counters)) return graph_error(ctx, bits);
         fcap = 3 * (int64_t)ctx->h_counters[CNT_MAXDEG] + 1;
+        ctx->bins = bin_layout(ctx->tune, ctx->h_counters, n, false);
     }
     size_t have = (size_t)ctx->ftab_cap * 2 * sizeof(double);
     rc = ensure_buffer(ctx, (void **)&ctx->ftab, &have, (size_t)fcap * 2 * sizeof(double), 0);
@@ -507,7 +513,7 @@ int features_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n
     using namespace ef;
     cudaStream_t st = ctx->stream;
     if (with_orient || mode == 1)
-        LAUNCH(launch_orient(rp, ci, n, m, s, ctx->tune, st, r.nbr_min, r.nbr_max), "orientation");
+        LAUNCH(launch_orient(rp, ci, n, m, s, ctx->tune, st, r.nbr_min, r.nbr_max, ctx->bins), "orientation");
     else
         LAUNCH(launch_omega_mm(rp, ci, n, m, s, r, ctx->tune, st), "omega");
     if (mode == 1) {
@@ -531,7 +537,8 @@ int nodes_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, i
     using namespace ef;
     cudaStream_t st = ctx->stream;
     if (global_tri && !tri_done) {
-        if (!orient_done) LAUNCH(launch_orient(rp, ci, n, m, s, ctx->tune, st), "orientation");
+        if (!orient_done)
+            LAUNCH(launch_orient(rp, ci, n, m, s, ctx->tune, st, nullptr, nullptr, ctx->bins), "orientation");
         LAUNCH(launch_out_hash(s, n, m, ctx->tune, st), "out-list hash");
         LAUNCH(launch_tri_pairs(s, n, m, ctx->tune, st), "triangle");
     }
@@ -917,7 +924,7 @@ int ef_compute_shard(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, int32_t
     cudaStream_t st = ctx->stream;
     int32_t *rng = s.counters + CNT_RANGE;
     LAUNCH(launch_shard_range(rp, n, m, shard, num_shards, rng, st), "shard range");
-    LAUNCH(launch_orient(rp, ci, n, m, s, t, st), "orientation");
+    LAUNCH(launch_orient(rp, ci, n, m, s, t, st, nullptr, nullptr, ctx->bins), "orientation");
     LAUNCH(launch_out_hash(s, n, m, t, st), "out-list hash");
     LAUNCH(launch_tri_pairs(s, n, m, t, st, rng), "triangle");
     // the out-degrees are not needed any more: they hold the marks

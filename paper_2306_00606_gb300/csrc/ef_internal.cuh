@@ -142,8 +142,26 @@ enum : int {
     CNT_TRIFRAC = 37,
     CNT_RANGE = 40,   // 40, 41: a shard's node range [lo, hi)
     CNT_SYM = 44,     // 44, 45: the symmetry sum (uint64, 8-byte aligned)
+    CNT_BIGLO = 46,   // n - 1 - (smallest id of a node of degree > SMALL_MAX), if any
+    CNT_BIGHI = 47,   // largest id of a node of degree > SMALL_MAX, if any
     NUM_COUNTERS = 64
 };
+
+// Order of the oriented out-lists: degree-bin order (true) or node order,
+// from t.layout, or in automatic mode (0) from where the nodes of degree >
+// SMALL_MAX lie in a host copy of the counters after the degree pass (h;
+// nullptr when none was read back): degree bins when they span more than
+// half of the ids (their hot out-lists would be scattered in node order),
+// node order when they are clustered or absent (lattices, BA and R-MAT
+// graphs number their hubs close together).  Without counters: degree bins
+// for one graph, node order for a batch.
+inline bool bin_layout(const Tune &t, const int32_t *h, int32_t n, bool batched) {
+    if (t.layout != 0) return t.layout == 2;
+    if (!h) return !batched;
+    if (h[BIN_BIG] == 0) return false;
+    const int64_t lo = (int64_t)n - 1 - h[CNT_BIGLO], hi = h[CNT_BIGHI];
+    return hi - lo > (int64_t)n / 2;
+}
 
 // Validation bits of a host copy of the counters after the row passes: the
 // device's error word, and asymmetry when the symmetry sum is not 0.
@@ -314,10 +332,9 @@ struct RankScratch {
 namespace ef {
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
                   cudaStream_t st);
-// The out-lists in degree-bin order (t.layout 2, or 0 on a single graph) or
-// node order (t.layout 1, or 0 on a batch: the graphs' own locality).
+// The out-lists in degree-bin order (bins) or node order.
 int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
-                  cudaStream_t st, int32_t *nmin = nullptr, int32_t *nmax = nullptr, bool batched = false);
+                  cudaStream_t st, int32_t *nmin = nullptr, int32_t *nmax = nullptr, bool bins = true);
 int launch_big_items(const Scratch &s, int32_t n, cudaStream_t st);
 int launch_batch_check(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const int64_t *goff, int32_t G,
                        const Scratch &s, const Tune &t, cudaStream_t st);

@@ -94,7 +94,7 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
     if (threadIdx.x < NUM_BINS) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    int mx = 0, err = 0, b0 = -1, b1 = -1, p0 = 0, p1 = 0;
+    int mx = 0, err = 0, b0 = -1, b1 = -1, p0 = 0, p1 = 0, blo = 0, bhi = 0;
     if (v < n) {
         const int a = rp[v], b = rp[v + 1];
         int d = 0;
@@ -106,6 +106,8 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
             b0 = d <= 4 ? BIN_S4 : d <= 8 ? BIN_S8 : d <= 16 ? BIN_S16 : BIN_S32;
         } else if (d > SMALL_MAX) {
             b0 = BIN_BIG;
+            blo = n - 1 - v;
+            bhi = v;
             if (d < hub_min) {
                 b1 = BIN_MID;
             } else {
@@ -121,9 +123,16 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
     for (int o = 16; o > 0; o >>= 1) {
         mx = max(mx, __shfl_xor_sync(FULL, mx, o));
         err |= __shfl_xor_sync(FULL, err, o);
+        blo = max(blo, __shfl_xor_sync(FULL, blo, o));
+        bhi = max(bhi, __shfl_xor_sync(FULL, bhi, o));
     }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) { s_mx[w] = mx; s_err[w] = err; }
+    if (l == 0) {
+        s_mx[w] = mx;
+        s_err[w] = err;
+        if (blo) atomicMax(cnt + CNT_BIGLO, blo);
+        if (bhi) atomicMax(cnt + CNT_BIGHI, bhi);
+    }
     __syncthreads();
     if (threadIdx.x < NUM_BINS)
         s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(cnt + threadIdx.x, s_cnt[threadIdx.x]) : 0;
@@ -632,8 +641,7 @@ int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
 
 // Oriented CSR and omega.
 int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
-                  cudaStream_t st, int32_t *nmin, int32_t *nmax, bool batched) {
-    const bool bins = t.layout == 2 || (t.layout == 0 && !batched);
+                  cudaStream_t st, int32_t *nmin, int32_t *nmax, bool bins) {
     if (bins) {
         // out-list offsets in layout order (degree-0 nodes keep offset 0 and an empty list)
         if (cudaMemsetAsync(s.out_ptr, 0, (size_t)(n + 1) * sizeof(int32_t), st) != cudaSuccess) return -1;

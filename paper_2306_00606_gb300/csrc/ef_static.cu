@@ -104,9 +104,10 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
         cudaStreamSynchronize(st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: validation readback failed");
     if (prep_error_bits(h_cnt)) return fail(EF_ERR_GRAPH, "ef_compute_static: input is not a symmetric simple sorted CSR");
+    const bool bins = bin_layout(t, h_cnt, n, false);
     ef_outputs out = {};
     out.ef = out_ef;
-    if (launch_ftab(s.ftab, s.tq, s.counters, fcap, st) || launch_orient(rp, ci, n, m, s, t, st) ||
+    if (launch_ftab(s.ftab, s.tq, s.counters, fcap, st) || launch_orient(rp, ci, n, m, s, t, st, nullptr, nullptr, bins) ||
         launch_wedge_small(rp, ci, s, precision, n, t, st) || launch_wedge_big(rp, ci, s, precision, 0, n, m, t, st) ||
         launch_out_hash(s, n, m, t, st) || launch_tri_pairs(s, n, m, t, st) ||
         launch_finalize(s, precision, n, out, t, st))
