@@ -635,7 +635,7 @@ size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s) {
     s.info = (int4 *)take(16 * N);
     s.out_col = (int32_t *)take(4 * (M + 8));
     s.out_D = (int32_t *)take(4 * (M + 1));
-    s.out_rng = (int2 *)take(8 * (M + 1));
+    s.out_pd = (int2 *)take(8 * (M + 1));
     s.out_hash = (int32_t *)take(4 * (M + 8));
     s.out_src = (int32_t *)take(4 * (M + 1));
     s.Ccenter = take(8 * N);

@@ -114,7 +114,7 @@ struct Scratch {
     int4    *info;       // n      {D, sigma1, out_ptr, out_ptr next} per node, for the orientation
     int32_t *out_col;    // m+8    oriented neighbour ids (ascending id within a row)
     int32_t *out_D;      // m+1    their degrees
-    int2    *out_rng;    // m+1    their own out-list ranges [out_ptr[x], out_ptr[x+1])
+    int2    *out_pd;     // m+1    probe descriptors of their own out-lists (probe_desc)
     int32_t *out_hash;   // m+8    hash tables of the out-lists longer than SHORT_MAX
     int32_t *out_src;    // m+1    owner of each oriented edge
     double  *Tacc;       // n      open-degree credits received as an end (FP64 reductions)
@@ -138,6 +138,7 @@ enum : int {
     CNT_ERR = 32,
     CNT_MAXDEG = 33,
     CNT_BIGITEM = 34,
+    CNT_MIDITEM = 35,
     CNT_HUB = 36,
     CNT_TRIFRAC = 37,
     CNT_RANGE = 40,   // 40, 41: a shard's node range [lo, hi)
@@ -223,6 +224,49 @@ __device__ __forceinline__ T group_sum(T v) {
 }
 
 // lower_bound over a sorted int32 array (generic address space)
+// ----------------------------------------------- out-list membership tables
+// Table of the out-list [ls, le) of one node: slots [base, base + 4 nb) of
+// out_hash, base = 2 ls rounded up to a multiple of 4 and 4 nb = 2 (le - ls)
+// rounded down to one, so the tables of consecutive out-lists never overlap
+// and every bucket is 16-byte aligned.  Only lists longer than SHORT_MAX have
+// one, and only when it lies inside the array (always, for a symmetric CSR:
+// the out-lists then hold m/2 entries in all).
+__host__ __device__ __forceinline__ int64_t hash_slots(int64_t m) { return m + 8; }   // slots of out_hash
+
+__device__ __forceinline__ bool out_table(int ls, int le, int64_t hash_cap, int64_t &base, int &nb) {
+    const int p = le - ls;
+    base = ((int64_t)2 * ls + 3) & ~(int64_t)3;
+    nb = (2 * p) >> 2;
+    return p > SHORT_MAX && base + 4 * (int64_t)nb <= hash_cap;
+}
+
+// Bits of the quad of entries [e0, e0 + 4) that lie in [ls, le).
+__device__ __forceinline__ unsigned range_bits(int e0, int ls, int le) {
+    const int lo = max(ls - e0, 0), hi = min(le - e0, 4);
+    return hi > lo ? ((1u << hi) - 1u) & ~((1u << lo) - 1u) : 0u;
+}
+
+// Probe descriptor of the out-list [ls, le) (what the triangle pass needs to
+// test membership in it, decided once per node instead of once per test):
+//   kind 0, a list of at most SHORT_MAX entries: x = its first quad of
+//     out_col, y = which entries of that quad (bits 0-3) and the next (4-7)
+//     belong to it;
+//   kind 1, a hashed list: x = its first bucket (quad) of out_hash, y = the
+//     bucket count;
+//   kind 2, a longer list without a table (malformed input only): x = ls,
+//     y = le.
+// The kind sits in bits 30-31 of y (counts and offsets stay below 2^30).
+constexpr int DESC_KIND_SHIFT = 30;
+constexpr int DESC_MASK = (1 << DESC_KIND_SHIFT) - 1;
+__device__ __forceinline__ int2 probe_desc(int ls, int le, int64_t hash_cap) {
+    int64_t hb;
+    int nb;
+    if (out_table(ls, le, hash_cap, hb, nb)) return make_int2((int)(hb >> 2), (int)((unsigned)nb | 1u << DESC_KIND_SHIFT));
+    if (le - ls > SHORT_MAX) return make_int2(ls, (int)((unsigned)le | 2u << DESC_KIND_SHIFT));
+    const int q0 = ls >> 2;
+    return make_int2(q0, (int)(range_bits(4 * q0, ls, le) | range_bits(4 * q0 + 4, ls, le) << 4));
+}
+
 __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int len, int32_t key) {
     int lo = 0, hi = len;
     while (lo < hi) {

@@ -90,7 +90,7 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int *total = nullptr)
 __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, int hub_min,
                           int32_t *__restrict__ D, int32_t *__restrict__ bins, int32_t *__restrict__ cnt) {
     __shared__ int s_cnt[NUM_BINS], s_base[NUM_BINS];
-    __shared__ int s_mx[32], s_err[32];
+    __shared__ int s_mx[32], s_err[32], s_blo[32], s_bhi[32];
     if (threadIdx.x < NUM_BINS) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -130,24 +130,29 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
     if (l == 0) {
         s_mx[w] = mx;
         s_err[w] = err;
-        if (blo) atomicMax(cnt + CNT_BIGLO, blo);
-        if (bhi) atomicMax(cnt + CNT_BIGHI, bhi);
+        s_blo[w] = blo;
+        s_bhi[w] = bhi;
     }
     __syncthreads();
     if (threadIdx.x < NUM_BINS)
         s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(cnt + threadIdx.x, s_cnt[threadIdx.x]) : 0;
     if (w == 0) {
+        // one global atomic per statistic and block (the same few addresses
+        // for every block: per-warp atomics there cost 0.07 ms at n = 4M)
         const int nw = blockDim.x >> 5;
         mx = l < nw ? s_mx[l] : 0;
         err = l < nw ? s_err[l] : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mx = max(mx, __shfl_xor_sync(FULL, mx, o));
-            err |= __shfl_xor_sync(FULL, err, o);
-        }
+        blo = l < nw ? s_blo[l] : 0;
+        bhi = l < nw ? s_bhi[l] : 0;
+        mx = __reduce_max_sync(FULL, mx);
+        err = __reduce_or_sync(FULL, err);
+        blo = __reduce_max_sync(FULL, blo);
+        bhi = __reduce_max_sync(FULL, bhi);
         if (l == 0) {
             if (mx) atomicMax(cnt + CNT_MAXDEG, mx);
             if (err) atomicOr(cnt + CNT_ERR, err);
+            if (blo) atomicMax(cnt + CNT_BIGLO, blo);
+            if (bhi) atomicMax(cnt + CNT_BIGHI, bhi);
         }
     }
     __syncthreads();
@@ -301,14 +306,14 @@ __global__ void __launch_bounds__(ROW_CTA) k_row_stats_hub(const int32_t *__rest
 
 // ------------------------------------------------------------- orientation
 // Appends the out-neighbours x of u (in (degree, id) order) to the oriented
-// CSR in ascending id order, with D_x, x's own out-list range and the owner
-// u; and gathers omega_u = sum over N(u) of sigma1(x), the last per-node sum
+// CSR in ascending id order, with D_x, the probe descriptor of x's own
+// out-list and the owner u; and gathers omega_u = sum over N(u) of sigma1(x), the last per-node sum
 // the closed form of S needs.
 struct Orient {
     const int32_t *ci;
-    const int4 *info;   // per node {D, sigma1, out_ptr, out_ptr next}
+    const int4 *info;   // per node {D, sigma1, probe descriptor of its out-list}
     int32_t *out_col, *out_D, *out_src;
-    int2 *out_rng;
+    int2 *out_pd;
     int32_t *nmin, *nmax;   // optional: smallest / largest neighbour degree (node features)
     int32_t n;
     __device__ __forceinline__ int4 node(int x) const {
@@ -324,7 +329,7 @@ struct Orient {
         out_col[k] = x;
         out_D[k] = nf.x;
         out_src[k] = u;
-        out_rng[k] = make_int2(nf.z, nf.w);
+        out_pd[k] = make_int2(nf.z, nf.w);
     }
     // A whole short row by one thread, four entries at a time (loads issued
     // together); returns omega_v.
@@ -356,13 +361,16 @@ struct Orient {
     }
 };
 
-// info[v] = {D_v, sigma1(v), start, end of v's out-list}: what the
+// info[v] = {D_v, sigma1(v), probe descriptor of v's out-list}: what the
 // orientation needs of a neighbour, in one 16-byte gather (sigma1 <= m < 2^31).
 __global__ void k_node_info(const int32_t *__restrict__ D, const int64_t *__restrict__ sig1,
                             const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ outdeg, int32_t n,
-                            int4 *__restrict__ info) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        info[v] = make_int4(D[v], (int)sig1[v], out_ptr[v], out_ptr[v] + outdeg[v]);
+                            int64_t hash_cap, int4 *__restrict__ info) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int ls = out_ptr[v];
+        const int2 pd = probe_desc(ls, ls + outdeg[v], hash_cap);
+        info[v] = make_int4(D[v], (int)sig1[v], pd.x, pd.y);
+    }
 }
 
 // Layout of the oriented CSR: the out-lists are stored work bin by work bin
@@ -652,8 +660,9 @@ int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
     } else if (launch_scan(s.outdeg, s.out_ptr, n, s.scan_tmp, st)) {
         return -1;
     }
-    k_node_info<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.D, s.sig1, s.out_ptr, s.outdeg, n, s.info);
-    const Orient o{ci, s.info, s.out_col, s.out_D, s.out_src, s.out_rng, nmin, nmax, n};
+    k_node_info<<<t.grid((int64_t)n, 256), 256, 0, st>>>(s.D, s.sig1, s.out_ptr, s.outdeg, n, hash_slots(m),
+                                                         s.info);
+    const Orient o{ci, s.info, s.out_col, s.out_D, s.out_src, s.out_pd, nmin, nmax, n};
     k_orient<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, n, m, t.row_thread_max, t.hub_min, o, s.out_ptr, s.omega);
     k_orient_hub<<<t.num_sms * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters, s.omega);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

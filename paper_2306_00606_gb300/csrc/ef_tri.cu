@@ -22,8 +22,10 @@
 // aligned quads); a longer one has a bucketed hash table (4 slots per
 // 16-byte bucket, load factor <= 0.5 + small rounding, built by k_out_hash)
 // and the key's bucket and the next one are loaded together, which settles
-// the test but for rare long probe runs.  The oriented CSR carries each
-// out-neighbour's own list range, so no test waits for an out_ptr load.
+// the test but for rare long probe runs.  The oriented CSR carries, for each
+// out-neighbour, the probe descriptor of its own list (which quads to load
+// and how to read them, fixed once per node by the orientation), so no test
+// waits for an out_ptr load or recomputes a table's geometry.
 //
 // Measured and left out (4M-node power-law graph): L2 eviction hints
 // (evict_last on probes, evict_first on the candidate stream) changed
@@ -52,19 +54,6 @@ constexpr int TRI_WARPS = 8;
 // blocks per SM the registers are sized for.  Measured on the 4M-node
 // power-law graph: (2, 4) 1.80 ms, (2, 3) 1.98, (2, 5) 2.06, (4, 3) 2.28,
 // (4, 4) 2.51 (register spills).  Variant 0 = (2, 4), 1 = (4, 3).
-
-// Table of the out-list [ls, le) of one node: slots [base, base + 4 nb) of
-// out_hash, base = 2 ls rounded up to a multiple of 4 and 4 nb = 2 (le - ls)
-// rounded down to one, so the tables of consecutive out-lists never overlap
-// and every bucket is 16-byte aligned.  Only lists longer than SHORT_MAX have
-// one, and only when it lies inside the array (always, for a symmetric CSR:
-// the out-lists then hold m/2 entries in all).
-__device__ __forceinline__ bool out_table(int ls, int le, int64_t hash_cap, int64_t &base, int &nb) {
-    const int p = le - ls;
-    base = ((int64_t)2 * ls + 3) & ~(int64_t)3;
-    nb = (2 * p) >> 2;
-    return p > SHORT_MAX && base + 4 * (int64_t)nb <= hash_cap;
-}
 
 __device__ __forceinline__ int bucket_of(int key, int nb) {
     const uint32_t h = (uint32_t)key * 0x9E3779B1u;
@@ -101,38 +90,33 @@ __device__ __forceinline__ unsigned match4(int4 v, int key) {
 
 __device__ __forceinline__ bool has_empty(int4 v) { return (v.x | v.y | v.z | v.w) < 0; }
 
-// Bits of the quad of entries [e0, e0 + 4) that lie in [ls, le).
-__device__ __forceinline__ unsigned range_bits(int e0, int ls, int le) {
-    const int lo = max(ls - e0, 0), hi = min(le - e0, 4);
-    return hi > lo ? ((1u << hi) - 1u) & ~((1u << lo) - 1u) : 0u;
-}
-
-// One membership test "key in the out-list [ls, le)", split so that a lane
-// issues the loads of all its tests before it waits for any: the quads p0
-// and p0 + d1, and which of their entries count (info bits 0-3 and 4-7) and
-// the kind of list (bits 8-9: 0 short, 1 hashed, 2 long without a table).
+// One membership test "key in the out-list of probe descriptor pd", split so
+// that a lane issues the loads of all its tests before it waits for any: the
+// quads p0 and p0 + d1, and which of their entries count (info bits 0-3 and
+// 4-7) and the kind of list (bits 8-9, the descriptor's kind).
 struct Probe {
     const int4 *p0;
     int d1;
     unsigned info;
 };
 
-__device__ __forceinline__ Probe probe_of(const int32_t *out_col, const int32_t *out_hash, int64_t hash_cap, int ls,
-                                          int le, int key) {
+__device__ __forceinline__ Probe probe_of(const int32_t *out_col, const int32_t *out_hash, int2 pd, int key) {
     Probe r;
-    int64_t hb;
-    int nb;
-    if (out_table(ls, le, hash_cap, hb, nb)) {
+    const unsigned kind = (unsigned)pd.y >> DESC_KIND_SHIFT;
+    if (kind == 1) {
+        const int nb = pd.y & DESC_MASK;
         const int b0 = bucket_of(key, nb);
-        r.p0 = reinterpret_cast<const int4 *>(out_hash + hb) + b0;
+        r.p0 = reinterpret_cast<const int4 *>(out_hash) + ((int64_t)pd.x + b0);
         r.d1 = b0 + 1 == nb ? -b0 : 1;
         r.info = 0xffu | 1u << 8;
-    } else {
-        const int q0 = ls >> 2;
-        r.p0 = reinterpret_cast<const int4 *>(out_col) + q0;
+    } else if (kind == 0) {
+        r.p0 = reinterpret_cast<const int4 *>(out_col) + pd.x;
         r.d1 = 1;
-        r.info = range_bits(4 * q0, ls, le) | range_bits(4 * q0 + 4, ls, le) << 4 |
-                 (le - ls > SHORT_MAX ? 2u : 0u) << 8;
+        r.info = (unsigned)pd.y & 0xffu;
+    } else {
+        r.p0 = reinterpret_cast<const int4 *>(out_col) + (pd.x >> 2);
+        r.d1 = 1;
+        r.info = 2u << 8;
     }
     return r;
 }
@@ -142,15 +126,13 @@ __device__ __forceinline__ Probe probe_of(const int32_t *out_col, const int32_t 
 // list without a table (malformed input only: binary search) -- reload what
 // they need.
 __device__ __forceinline__ bool probe_done(const Probe &r, int4 x, int4 y, const int32_t *out_col,
-                                           const int32_t *out_hash, int64_t hash_cap, int ls, int le, int key) {
+                                           const int32_t *out_hash, int2 pd, int key) {
     if ((match4(x, key) & r.info) | (match4(y, key) & (r.info >> 4) & 0xfu)) return true;
     const unsigned kind = (r.info >> 8) & 3u;
     if (kind == 0 || (kind == 1 && (has_empty(x) || has_empty(y)))) return false;
     if (kind == 1) {
-        int64_t hb;
-        int nb;
-        out_table(ls, le, hash_cap, hb, nb);
-        const int4 *t = reinterpret_cast<const int4 *>(out_hash + hb);
+        const int nb = pd.y & DESC_MASK;
+        const int4 *t = reinterpret_cast<const int4 *>(out_hash) + pd.x;
         int b = (int)(r.p0 + r.d1 - t);
         b = b + 1 == nb ? 0 : b + 1;
         for (int tries = 2; tries < nb; ++tries) {
@@ -161,6 +143,7 @@ __device__ __forceinline__ bool probe_done(const Probe &r, int4 x, int4 y, const
         }
         return false;
     }
+    const int ls = pd.x, le = pd.y & DESC_MASK;
     const int pos = ls + lower_bound_i32(out_col + ls, le - ls, key);
     return pos < le && out_col[pos] == key;
 }
@@ -173,13 +156,14 @@ __device__ __forceinline__ void credit_tri(int64_t *qacc, int64_t *tcnt, int v, 
 template <int TRI_UNIT, int TRI_BLOCKS>
 __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
     const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_D,
-    const int2 *__restrict__ out_rng, const int32_t *__restrict__ out_src, const int32_t *__restrict__ out_hash,
-    int64_t hash_cap, const int32_t *__restrict__ outdeg, const int32_t *__restrict__ D, int32_t n,
+    const int2 *__restrict__ out_pd, const int32_t *__restrict__ out_src, const int32_t *__restrict__ out_hash,
+    const int32_t *__restrict__ outdeg, const int32_t *__restrict__ D, int32_t n,
     const int32_t *__restrict__ owner_range, const int64_t *__restrict__ tq,
     int64_t *__restrict__ qacc, int64_t *__restrict__ tcnt) {
     __shared__ int s_ex[TRI_WARPS][32];   // exclusive prefix of unit counts
-    __shared__ int s_kend[TRI_WARPS][32], s_b[TRI_WARPS][32], s_Db[TRI_WARPS][32], s_bs[TRI_WARPS][32];
-    __shared__ int s_be[TRI_WARPS][32], s_Dab[TRI_WARPS][32], s_a[TRI_WARPS][32];
+    __shared__ int s_kend[TRI_WARPS][32], s_b[TRI_WARPS][32], s_Db[TRI_WARPS][32], s_Dab[TRI_WARPS][32];
+    __shared__ int s_a[TRI_WARPS][32];
+    __shared__ int2 s_bpd[TRI_WARPS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t total = out_ptr[n];
     const int64_t stride = (int64_t)gridDim.x * TRI_WARPS * 32;
@@ -195,12 +179,10 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
             if (np > 0) {
                 const int b = out_col[k];
                 const int Db = out_D[k];
-                const int2 rb = out_rng[k];
                 s_kend[w][lane] = kend;
                 s_b[w][lane] = b;
                 s_Db[w][lane] = Db;
-                s_bs[w][lane] = rb.x;
-                s_be[w][lane] = rb.y;
+                s_bpd[w][lane] = out_pd[k];
                 s_Dab[w][lane] = D[a] + Db;
                 s_a[w][lane] = a;
                 nu = (np + TRI_UNIT - 1) / TRI_UNIT;
@@ -217,7 +199,8 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
         __syncwarp();
         int cur_a = -1, hit_a = 0;
         int64_t acc_a = 0;
-        int i = -1, kend = 0, exi = 0, b = 0, Db = 0, bs = 0, be = 0, Dab = 0, ai = 0;
+        int i = -1, kend = 0, exi = 0, b = 0, Db = 0, Dab = 0, ai = 0;
+        int2 bpd = make_int2(0, 0);
         for (int t = lane; t < U; t += 32) {
             // the warp edge owning unit t: the last i with s_ex[i] <= t (s_ex is
             // non-decreasing; i + step <= 31 at every step)
@@ -231,8 +214,7 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
                 exi = s_ex[w][i];
                 b = s_b[w][i];
                 Db = s_Db[w][i];
-                bs = s_bs[w][i];
-                be = s_be[w][i];
+                bpd = s_bpd[w][i];
                 Dab = s_Dab[w][i];
                 ai = s_a[w][i];
             }
@@ -245,7 +227,7 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
                 if (q < jn) {
                     c[q] = __ldg(out_col + j0 + q);
                     Dc[q] = __ldg(out_D + j0 + q);
-                    rc[q] = __ldg(out_rng + j0 + q);
+                    rc[q] = __ldg(out_pd + j0 + q);
                 }
             }
             Probe pr[TRI_UNIT];
@@ -253,10 +235,8 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
 #pragma unroll
             for (int q = 0; q < TRI_UNIT; ++q) {
                 if (q < jn) {
-                    const int2 r = rc[q];
                     const bool b_low = rank_less(Db, b, Dc[q], c[q]);
-                    pr[q] = probe_of(out_col, out_hash, hash_cap, b_low ? bs : r.x, b_low ? be : r.y,
-                                     b_low ? c[q] : b);
+                    pr[q] = probe_of(out_col, out_hash, b_low ? bpd : rc[q], b_low ? c[q] : b);
                     pr[q].info |= (unsigned)b_low << 10;
                     x[q] = __ldg(pr[q].p0);
                     y[q] = __ldg(pr[q].p0 + pr[q].d1);
@@ -268,12 +248,7 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
             for (int q = 0; q < TRI_UNIT; ++q) {
                 if (q < jn) {
                     const bool b_low = (pr[q].info >> 10) & 1u;
-                    int ls = bs, le = be;
-                    if (!b_low) {
-                        ls = rc[q].x;
-                        le = rc[q].y;
-                    }
-                    if (probe_done(pr[q], x[q], y[q], out_col, out_hash, hash_cap, ls, le, b_low ? c[q] : b)) {
+                    if (probe_done(pr[q], x[q], y[q], out_col, out_hash, b_low ? bpd : rc[q], b_low ? c[q] : b)) {
                         const int64_t g = __ldg(tq + Dab + Dc[q]);
                         credit_tri(qacc, tcnt, c[q], g, 1);
                         gsum += g;
@@ -298,8 +273,6 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
     }
 }
 
-static inline int64_t hash_slots(int64_t m) { return m + 8; }   // slots of out_hash
-
 static inline unsigned grid_of(int64_t work, int per_block, int64_t cap) {
     int64_t g = (work + per_block - 1) / per_block;
     return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
@@ -317,12 +290,12 @@ int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cuda
                      const int32_t *owner_range) {
     const unsigned grid = grid_of(m / 2, TRI_WARPS * 32, (int64_t)t.num_sms * 16);
     if (t.tri_variant == 1)
-        k_tri_pairs<4, 3><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_rng, s.out_src,
-                                                            s.out_hash, hash_slots(m), s.outdeg, s.D, n, owner_range, s.tq, s.qacc,
+        k_tri_pairs<4, 3><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pd, s.out_src,
+                                                            s.out_hash, s.outdeg, s.D, n, owner_range, s.tq, s.qacc,
                                                             s.tcnt);
     else
-        k_tri_pairs<2, 4><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_rng, s.out_src,
-                                                            s.out_hash, hash_slots(m), s.outdeg, s.D, n, owner_range, s.tq, s.qacc,
+        k_tri_pairs<2, 4><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pd, s.out_src,
+                                                            s.out_hash, s.outdeg, s.D, n, owner_range, s.tq, s.qacc,
                                                             s.tcnt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -233,11 +233,14 @@ struct ClassEval<true> {
 
 constexpr int MID_WARPS = 4;
 
-// One warp per middle node of degree 33..MID_MAX.
+// One warp per middle node of degree 33..MID_MAX.  Warps take their nodes
+// one at a time from an atomic counter (the work of a node grows with the
+// square of its class count, which varies a hundredfold within the bin); the
+// next index is fetched while the current node is processed.
 template <bool F64>
 __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
-    const int32_t *__restrict__ list, const int32_t *__restrict__ cnt, const double *__restrict__ ftab,
+    const int32_t *__restrict__ list, int32_t *__restrict__ cnt, const double *__restrict__ ftab,
     double *__restrict__ Tacc, void *__restrict__ Ccenter) {
     using E = ClassEval<F64>;
     using Cls = typename E::Cls;
@@ -252,8 +255,12 @@ __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
     R *cq = s_q[w];
     const unsigned lt = (1u << lane) - 1u;
     const int count = cnt[BIN_MID];
-    const int64_t nwarps = (int64_t)gridDim.x * MID_WARPS;
-    for (int64_t it = (int64_t)blockIdx.x * MID_WARPS + w; it < count; it += nwarps) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(cnt + CNT_MIDITEM, 1);
+    it = __shfl_sync(FULL, it, 0);
+    while (it < count) {
+        int next = 0;
+        if (lane == 0) next = atomicAdd(cnt + CNT_MIDITEM, 1);
         const int u = list[it];
         const int start = rp[u];
         const int Du = rp[u + 1] - start;
@@ -307,6 +314,7 @@ __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
         const R ctot = warp_sum(center.get());
         if (lane == 0) reinterpret_cast<R *>(Ccenter)[u] = ctot;
         __syncwarp();
+        it = __shfl_sync(FULL, next, 0);
     }
 }
 
@@ -483,14 +491,32 @@ static size_t hub_smem_bytes() {
     return HUB_HIST * sizeof(int32_t) + HUB_SMEM_K * (sizeof(typename E::Cls) + sizeof(typename E::R));
 }
 
+// Resident blocks per SM of the class kernels ([F64][mid, hub]): their grids
+// hold exactly one wave, and their warps take work from atomic counters.
+static int g_class_blocks[2][2] = {{1, 1}, {1, 1}};
+
+template <bool F64>
+static int class_occupancy() {
+    int mid = 0, hub = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mid, k_wedge_mid<F64>, MID_WARPS * 32, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&hub, k_wedge_hub<F64>, HUB_THREADS, hub_smem_bytes<F64>()) !=
+            cudaSuccess)
+        return -1;
+    g_class_blocks[F64][0] = mid > 0 ? mid : 1;
+    g_class_blocks[F64][1] = hub > 0 ? hub : 1;
+    return 0;
+}
+
 // Opt the hub kernels in to their dynamic shared memory on the current device
-// (once per context, before any launch or stream capture).
+// and size the class kernels' grids (once per context, before any launch or
+// stream capture).
 int prepare_kernels() {
     if (cudaFuncSetAttribute(k_wedge_hub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)hub_smem_bytes<true>()) != cudaSuccess ||
         cudaFuncSetAttribute(k_wedge_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)hub_smem_bytes<false>()) != cudaSuccess)
         return -1;
+    if (class_occupancy<true>() || class_occupancy<false>()) return -1;
     return 0;
 }
 
@@ -498,10 +524,10 @@ template <bool F64>
 static int big_classes(const int32_t *rp, const int32_t *ci, const Scratch &s, int32_t n, int num_sms,
                        cudaStream_t st) {
     const int32_t *mid = s.bins + (size_t)BIN_MID * n;
-    k_wedge_mid<F64><<<(unsigned)(num_sms * 8), MID_WARPS * 32, 0, st>>>(rp, ci, s.D, mid, s.counters, s.ftab, s.Tacc,
-                                                                         s.Ccenter);
+    k_wedge_mid<F64><<<(unsigned)(num_sms * g_class_blocks[F64][0]), MID_WARPS * 32, 0, st>>>(
+        rp, ci, s.D, mid, s.counters, s.ftab, s.Tacc, s.Ccenter);
     const size_t smem = hub_smem_bytes<F64>();
-    k_wedge_hub<F64><<<(unsigned)(num_sms * 2), HUB_THREADS, smem, st>>>(
+    k_wedge_hub<F64><<<(unsigned)(num_sms * g_class_blocks[F64][1]), HUB_THREADS, smem, st>>>(
         rp, ci, s.D, s.bins, n, s.counters, s.ftab, s.Tacc, s.Ccenter, s.hub_cidx, s.hub_cls, s.hub_q);
     return 0;
 }
