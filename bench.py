@@ -40,16 +40,15 @@ WORKLOADS = {
                   "seed=20230610, one ef_compute_batched call (replayed CUDA graph)"),
 }
 BATCHED = {"ws4096"}
-PASSES = ("prep_ms", "orient_ms", "wedge_small_ms", "wedge_big_ms", "tri_hash_ms", "tri_pairs_ms", "finalize_ms")
-PASS_KERNEL = {"prep_ms": "k_degrees+k_row_stats+k_row_stats_hub+k_ftab",
-               "orient_ms": "scan+k_orient+k_orient_hub", "wedge_small_ms": "k_wedge_small<4,8,16,32>",
-               "wedge_big_ms": "k_wedge_mid+k_wedge_hub", "tri_hash_ms": "k_out_hash",
+PASSES = ("prep_ms", "orient_ms", "wedge_small_ms", "wedge_big_ms", "tri_pairs_ms", "finalize_ms")
+PASS_KERNEL = {"prep_ms": "k_degrees+k_row_stats+k_row_stats_hub",
+               "orient_ms": "k_ftab+layout+scan+k_node_info+k_orient+k_orient_hub+k_hash_rows",
+               "wedge_small_ms": "k_wedge_small<4,8,16,32>", "wedge_big_ms": "k_wedge_mid+k_wedge_hub",
                "tri_pairs_ms": "k_tri_pairs", "finalize_ms": "k_finalize"}
 PASS_NOTE = {"prep_ms": "bound by random L2 gathers of neighbour degrees",
-             "orient_ms": "bound by random L2 gathers of neighbour degrees and sigma1",
+             "orient_ms": "bound by random L2 gathers of neighbour records; also fills the out-list hash tables",
              "wedge_small_ms": "bound by MUFU lg2 and FP32 adds (one f evaluation per ordered pair)",
              "wedge_big_ms": "bound by MUFU lg2 and FP32 adds over degree classes, and L2 reductions",
-             "tri_hash_ms": "bound by L2 atomics",
              "tri_pairs_ms": "bound by dependent L2 round trips (1.1e8 membership tests), not HBM bandwidth",
              "finalize_ms": "streaming, HBM-bound"}
 
@@ -65,15 +64,14 @@ def algorithmic_bytes(g, st):
     return {
         # row_ptr + col_idx read; D, sigma1, sigma2, outdeg written
         "prep_ms": csr + 4 * n + 16 * n + 4 * n,
-        # CSR + outdeg read; out_ptr, out_col/out_D/out_src (m/2 each), omega written
-        "orient_ms": csr + 4 * n + 4 * (n + 1) + 12 * (m // 2) + 8 * n,
+        # CSR + outdeg read; out_ptr, out_col/out_D/out_src/out_pd (20 B per
+        # oriented entry), hash tables (2 slots per entry), omega written
+        "orient_ms": csr + 4 * n + 4 * (n + 1) + 28 * (m // 2) + 8 * n,
         # rows of the middle nodes read; Ccenter written, one 8-byte credit per row entry
         "wedge_small_ms": 4 * len(small) * 2 + 4 * int(small.sum()) + 8 * len(small) + 8 * int(small.sum()),
         "wedge_big_ms": 4 * len(big) * 2 + 4 * int(big.sum()) + 8 * len(big) + 8 * int(big.sum()),
-        # out_ptr + out_col read, tables written (2 slots per entry of a long list)
-        "tri_hash_ms": 4 * (n + 1) + 4 * (m // 2) + 8 * (m // 2),
-        # out_ptr, out_col, out_D, out_src read; qacc, tcnt written
-        "tri_pairs_ms": 4 * (n + 1) + 12 * (m // 2) + 16 * n,
+        # out_ptr, out_col, out_D, out_src, out_pd read; qacc, tcnt written
+        "tri_pairs_ms": 4 * (n + 1) + 20 * (m // 2) + 16 * n,
         # D and 7 eight-byte per-node arrays read, EF written
         "finalize_ms": 4 * n + 7 * 8 * n + 8 * n,
     }

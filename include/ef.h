@@ -101,11 +101,13 @@ typedef struct {
  * on the context stream between the passes). */
 typedef struct {
     int64_t calls;
-    double prep_ms;        /* validation, degrees, neighbour sums, f table */
-    double orient_ms;      /* degree orientation (scan + oriented CSR) and omega */
+    double prep_ms;        /* validation, degrees, neighbour sums */
+    double orient_ms;      /* f table, degree orientation (scan + oriented
+                              CSR + out-list hash tables) and omega */
     double wedge_small_ms; /* middle nodes of degree <= 32 */
     double wedge_big_ms;   /* middle nodes of degree > 32 */
-    double tri_hash_ms;    /* hash tables of the long out-lists */
+    double tri_hash_ms;    /* always 0: the orientation builds the hash
+                              tables of the long out-lists (orient_ms) */
     double tri_pairs_ms;   /* triangle pair tests and corrections (one kernel) */
     double finalize_ms;    /* per-node sums, S, N, EF */
     double total_ms;

@@ -92,9 +92,10 @@ thread_local char g_err[512];
 
 // Kernels one call launches (default wedge mode): part A 3 (+1 batched),
 // f table 1, orientation (layout gather, a scan of 3, layout scatter, node
-// records, 2), small wedges 4, class wedges 2, triangles 2 (hash tables,
-// pair tests), finalize 1.
-constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 8 + 4 + 2 + 2 + 1;
+// records, 2, hash tables of the longer rows 1; the short rows' tables are
+// filled by the orientation itself), small wedges 4, class wedges 2, pair
+// tests 1, finalize 1.
+constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 9 + 4 + 2 + 1 + 1;
 
 void set_err(ef_ctx *c, const char *fmt, ...) {
     char *dst = c ? c->err : g_err;
@@ -195,8 +196,8 @@ int part_a(ef_ctx *ctx, const Job &j, const ef::Scratch &s, cudaStream_t st) {
     return EF_OK;
 }
 
-// Part B; with prof, events 1..7 bracket f table + orientation, small
-// wedges, big wedges, hash tables, pair tests and finalize.
+// Part B; with prof, events 1..4, 6, 7 bracket f table + orientation (with
+// the hash tables), small wedges, big wedges, pair tests and finalize.
 int part_b(ef_ctx *ctx, const Job &j, const ef::Scratch &s, int64_t fcap, bool prof, cudaStream_t st) {
     using namespace ef;
     const Tune &t = ctx->tune;
@@ -207,8 +208,6 @@ int part_b(ef_ctx *ctx, const Job &j, const ef::Scratch &s, int64_t fcap, bool p
     if (prof) CU(cudaEventRecord(ctx->ev[3], st));
     LAUNCH(launch_wedge_big(j.rp, j.ci, s, j.o.precision, j.o.wedge_mode, j.n, j.m, t, st), "big wedge");
     if (prof) CU(cudaEventRecord(ctx->ev[4], st));
-    LAUNCH(launch_out_hash(s, j.n, j.m, t, st), "out-list hash");
-    if (prof) CU(cudaEventRecord(ctx->ev[5], st));
     LAUNCH(launch_tri_pairs(s, j.n, j.m, t, st), "triangle");
     if (prof) CU(cudaEventRecord(ctx->ev[6], st));
     LAUNCH(launch_finalize(s, j.o.precision, j.n, j.out, t, st), "finalize");
@@ -351,8 +350,7 @@ void accumulate_stats(ef_ctx *ctx, bool batched) {
     st.orient_ms += el(1, 2);
     st.wedge_small_ms += el(2, 3);
     st.wedge_big_ms += el(3, 4);
-    st.tri_hash_ms += el(4, 5);
-    st.tri_pairs_ms += el(5, 6);
+    st.tri_pairs_ms += el(4, 6);
     st.finalize_ms += el(6, 7);
     st.total_ms += el(0, 7);
     st.kernels += KERNELS_PER_CALL + (batched ? 1 : 0);
@@ -507,7 +505,8 @@ int rank_buffers(ef_ctx *ctx, int32_t n, ef::RankScratch &r) {
 
 // Features of every node into x (after prepare_graph).  with_orient: take
 // omega and the neighbour degree range from the orientation pass (which a
-// ranking needs anyway for its triangles) instead of the lighter omega pass.
+// ranking needs anyway for its triangles) instead of the lighter omega pass;
+// the orientation always builds the hash tables, since triangles follow.
 int features_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, int mode,
                     const ef::Scratch &s, ef::RankScratch r, float *x, bool with_orient = false) {
     using namespace ef;
@@ -516,10 +515,7 @@ int features_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n
         LAUNCH(launch_orient(rp, ci, n, m, s, ctx->tune, st, r.nbr_min, r.nbr_max, ctx->bins), "orientation");
     else
         LAUNCH(launch_omega_mm(rp, ci, n, m, s, r, ctx->tune, st), "omega");
-    if (mode == 1) {
-        LAUNCH(launch_out_hash(s, n, m, ctx->tune, st), "out-list hash");
-        LAUNCH(launch_tri_pairs(s, n, m, ctx->tune, st), "triangle");
-    }
+    if (mode == 1) LAUNCH(launch_tri_pairs(s, n, m, ctx->tune, st), "triangle");
     r.x = x;
     LAUNCH(launch_features(s, r, n, mode, ctx->tune, st), "features");
     return EF_OK;
@@ -539,7 +535,6 @@ int nodes_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, i
     if (global_tri && !tri_done) {
         if (!orient_done)
             LAUNCH(launch_orient(rp, ci, n, m, s, ctx->tune, st, nullptr, nullptr, ctx->bins), "orientation");
-        LAUNCH(launch_out_hash(s, n, m, ctx->tune, st), "out-list hash");
         LAUNCH(launch_tri_pairs(s, n, m, ctx->tune, st), "triangle");
     }
     if (timed) CU(cudaEventRecord(ctx->ev[8], st));
@@ -925,7 +920,6 @@ int ef_compute_shard(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, int32_t
     int32_t *rng = s.counters + CNT_RANGE;
     LAUNCH(launch_shard_range(rp, n, m, shard, num_shards, rng, st), "shard range");
     LAUNCH(launch_orient(rp, ci, n, m, s, t, st, nullptr, nullptr, ctx->bins), "orientation");
-    LAUNCH(launch_out_hash(s, n, m, t, st), "out-list hash");
     LAUNCH(launch_tri_pairs(s, n, m, t, st, rng), "triangle");
     // the out-degrees are not needed any more: they hold the marks
     LAUNCH(launch_mark_range(rng, n, s.outdeg, t, st), "shard marks");

@@ -240,6 +240,24 @@ __device__ __forceinline__ bool out_table(int ls, int le, int64_t hash_cap, int6
     return p > SHORT_MAX && base + 4 * (int64_t)nb <= hash_cap;
 }
 
+// Home bucket of key in a table of nb buckets of 4 slots.
+__device__ __forceinline__ int bucket_of(int key, int nb) {
+    const uint32_t h = (uint32_t)key * 0x9E3779B1u;
+    return (int)(((uint64_t)h * (uint32_t)nb) >> 32);
+}
+
+// Insert key into a table (cleared to -1 beforehand) shared by several
+// threads: linear probing over slots from the key's home bucket, by atomics.
+__device__ __forceinline__ void table_insert_shared(int32_t *out_hash, int64_t base, int nb, int key) {
+    const int cap = 4 * nb;
+    int sl = 4 * bucket_of(key, nb);
+    for (int tries = 0; tries < cap; ++tries) {
+        const int prev = atomicCAS(out_hash + base + sl, -1, key);
+        if (prev == -1 || prev == key) break;
+        sl = sl + 1 == cap ? 0 : sl + 1;
+    }
+}
+
 // Bits of the quad of entries [e0, e0 + 4) that lie in [ls, le).
 __device__ __forceinline__ unsigned range_bits(int e0, int ls, int le) {
     const int lo = max(ls - e0, 0), hi = min(le - e0, 4);
@@ -377,8 +395,11 @@ namespace ef {
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
                   cudaStream_t st);
 // The out-lists in degree-bin order (bins) or node order.
+// With tables, also the hash tables of the out-lists longer than SHORT_MAX
+// (cleared here, filled as the lists are written).
 int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
-                  cudaStream_t st, int32_t *nmin = nullptr, int32_t *nmax = nullptr, bool bins = true);
+                  cudaStream_t st, int32_t *nmin = nullptr, int32_t *nmax = nullptr, bool bins = true,
+                  bool tables = true);
 int launch_big_items(const Scratch &s, int32_t n, cudaStream_t st);
 int launch_batch_check(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const int64_t *goff, int32_t G,
                        const Scratch &s, const Tune &t, cudaStream_t st);
@@ -389,7 +410,6 @@ int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, i
                        const Tune &t, cudaStream_t st);
 int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int wedge_mode,
                      int32_t n, int64_t m, const Tune &t, cudaStream_t st);
-int launch_out_hash(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st);
 int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st,
                      const int32_t *owner_range = nullptr);
 int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs &out, const Tune &t,

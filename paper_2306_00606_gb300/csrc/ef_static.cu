@@ -109,7 +109,7 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     out.ef = out_ef;
     if (launch_ftab(s.ftab, s.tq, s.counters, fcap, st) || launch_orient(rp, ci, n, m, s, t, st, nullptr, nullptr, bins) ||
         launch_wedge_small(rp, ci, s, precision, n, t, st) || launch_wedge_big(rp, ci, s, precision, 0, n, m, t, st) ||
-        launch_out_hash(s, n, m, t, st) || launch_tri_pairs(s, n, m, t, st) ||
+        launch_tri_pairs(s, n, m, t, st) ||
         launch_finalize(s, precision, n, out, t, st))
         return fail(EF_ERR_CUDA, "ef_compute_static: launch failed");
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)

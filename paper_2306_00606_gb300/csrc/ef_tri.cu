@@ -20,7 +20,7 @@
 // two independent 16-byte loads, the same instructions for every lane: an
 // out-list of at most SHORT_MAX entries is read whole (it spans at most two
 // aligned quads); a longer one has a bucketed hash table (4 slots per
-// 16-byte bucket, load factor <= 0.5 + small rounding, built by k_out_hash)
+// 16-byte bucket, load factor <= 0.5 + small rounding, built by the orientation)
 // and the key's bucket and the next one are loaded together, which settles
 // the test but for rare long probe runs.  The oriented CSR carries, for each
 // out-neighbour, the probe descriptor of its own list (which quads to load
@@ -54,34 +54,6 @@ constexpr int TRI_WARPS = 8;
 // blocks per SM the registers are sized for.  Measured on the 4M-node
 // power-law graph: (2, 4) 1.80 ms, (2, 3) 1.98, (2, 5) 2.06, (4, 3) 2.28,
 // (4, 4) 2.51 (register spills).  Variant 0 = (2, 4), 1 = (4, 3).
-
-__device__ __forceinline__ int bucket_of(int key, int nb) {
-    const uint32_t h = (uint32_t)key * 0x9E3779B1u;
-    return (int)(((uint64_t)h * (uint32_t)nb) >> 32);
-}
-
-// Thread per oriented entry: insert it into its owner's table (cleared to -1
-// beforehand) by linear probing over slots from the key's bucket.
-__global__ void k_out_hash(const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ outdeg,
-                           const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_src, int32_t n,
-                           int64_t hash_cap, int32_t *__restrict__ out_hash) {
-    const int64_t total = out_ptr[n];
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int a = out_src[k];
-        int64_t hb;
-        int nb;
-        if (!out_table(out_ptr[a], out_ptr[a] + outdeg[a], hash_cap, hb, nb)) continue;
-        const int key = out_col[k];
-        const int cap = 4 * nb;
-        int sl = 4 * bucket_of(key, nb);
-        for (int tries = 0; tries < cap; ++tries) {
-            const int prev = atomicCAS(out_hash + hb + sl, -1, key);
-            if (prev == -1 || prev == key) break;
-            sl = sl + 1 == cap ? 0 : sl + 1;
-        }
-    }
-}
 
 __device__ __forceinline__ unsigned match4(int4 v, int key) {
     return (unsigned)(v.x == key) | (unsigned)(v.y == key) << 1 | (unsigned)(v.z == key) << 2 |
@@ -276,14 +248,6 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
 static inline unsigned grid_of(int64_t work, int per_block, int64_t cap) {
     int64_t g = (work + per_block - 1) / per_block;
     return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
-}
-
-int launch_out_hash(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st) {
-    const int num_sms = t.num_sms;
-    if (cudaMemsetAsync(s.out_hash, 0xff, (size_t)hash_slots(m) * sizeof(int32_t), st) != cudaSuccess) return -1;
-    k_out_hash<<<grid_of(m / 2, 256, (int64_t)num_sms * 32), 256, 0, st>>>(s.out_ptr, s.outdeg, s.out_col, s.out_src,
-                                                                          n, hash_slots(m), s.out_hash);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st,
