@@ -236,7 +236,8 @@ constexpr int MID_WARPS = 4;
 // One warp per middle node of degree 33..MID_MAX.  Warps take their nodes
 // one at a time from an atomic counter (the work of a node grows with the
 // square of its class count, which varies a hundredfold within the bin); the
-// next index is fetched while the current node is processed.
+// next node's index, id and row range are loaded while the current node is
+// processed, so only the neighbour gathers wait at the start of a node.
 template <bool F64>
 __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
@@ -258,12 +259,15 @@ __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
     int it = 0;
     if (lane == 0) it = atomicAdd(cnt + CNT_MIDITEM, 1);
     it = __shfl_sync(FULL, it, 0);
+    int u = 0, start = 0, Du = 0;
+    if (it < count) {
+        u = list[it];
+        start = rp[u];
+        Du = rp[u + 1] - start;
+    }
     while (it < count) {
         int next = 0;
         if (lane == 0) next = atomicAdd(cnt + CNT_MIDITEM, 1);
-        const int u = list[it];
-        const int start = rp[u];
-        const int Du = rp[u + 1] - start;
         const int base = Du - 4;
         for (int i = lane; i < MID_HIST; i += 32) hist[i] = 0;
         __syncwarp();
@@ -273,6 +277,8 @@ __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
             if (a < MID_HIST) atomicAdd(hist + a, 1);
         }
         __syncwarp();
+        next = __shfl_sync(FULL, next, 0);
+        const int u_next = next < count ? list[next] : 0;
         int K = 0;
         for (int i0 = 0; i0 < MID_HIST; i0 += 32) {
             const int i = i0 + lane;
@@ -302,6 +308,8 @@ __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
             K += __popc(bal);
         }
         __syncwarp();
+        const int start_next = next < count ? rp[u_next] : 0;
+        const int end_next = next < count ? rp[u_next + 1] : 0;
         SumAcc<R> center;
         for (int i = lane; i < K; i += 32) {
             const Cls c_i = cls[i];
@@ -314,7 +322,10 @@ __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
         const R ctot = warp_sum(center.get());
         if (lane == 0) reinterpret_cast<R *>(Ccenter)[u] = ctot;
         __syncwarp();
-        it = __shfl_sync(FULL, next, 0);
+        it = next;
+        u = u_next;
+        start = start_next;
+        Du = end_next - start_next;
     }
 }
 
