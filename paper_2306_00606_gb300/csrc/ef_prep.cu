@@ -161,9 +161,9 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
 }
 
 // Row order of the one-thread row passes (k_row_stats, k_orient), decided on
-// the device from the degree pass's counts: when the graph has rows of degree
-// > 32 (degrees spread out), the rows of degree 1..32 are taken in work-bin
-// order (the lists of degree classes 1-4, 5-8, 9-16, 17-32 one after the
+// the device from the degree pass's counts when the host allows it
+// (rows_in_bins_allowed): when the graph has rows of degree > 32 (degrees
+// spread out), the rows of degree 1..32 are taken in work-bin order (the lists of degree classes 1-4, 5-8, 9-16, 17-32 one after the
 // other), so that the 32 rows of a warp have similar lengths, and the rows of
 // degree 33..hub_min-1 from their list, a warp each; otherwise (lattices,
 // small-world graphs) in node order, where neighbouring rows share cache
@@ -172,8 +172,8 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
 struct RowOrder {
     int base[5];   // bin order: first position of each small class, then their total
     bool bins;
-    __device__ __forceinline__ void load(const int32_t *cnt, int32_t n) {
-        bins = cnt[BIN_BIG] > 0;
+    __device__ __forceinline__ void load(const int32_t *cnt, int32_t n, bool allowed) {
+        bins = allowed && cnt[BIN_BIG] > 0;
         int acc = 0;
         for (int q = 0; q < 4; ++q) {
             base[q] = acc;
@@ -282,9 +282,10 @@ __device__ __forceinline__ void row_stats_warp(const int32_t *__restrict__ ci, c
 // the warp for the others; hubs go to k_row_stats_hub.
 __global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
                             int tmax, int hub_min, const int32_t *__restrict__ D,
-                            const int32_t *__restrict__ bins, RowOut ro, int32_t *__restrict__ cnt) {
+                            const int32_t *__restrict__ bins, bool bins_ok, RowOut ro,
+                            int32_t *__restrict__ cnt) {
     __shared__ RowOrder s_ord;
-    if (threadIdx.x == 0) s_ord.load(cnt, n);
+    if (threadIdx.x == 0) s_ord.load(cnt, n, bins_ok);
     __syncthreads();
     const RowOrder ord = s_ord;
     const int total = ord.total();
@@ -556,11 +557,11 @@ __device__ __forceinline__ void orient_row_warp(const Orient &o, int u, int ua, 
 // the warp for the others; hubs go to k_orient_hub.
 __global__ void __launch_bounds__(256, 5) k_orient(const int32_t *__restrict__ rp, int32_t n, int64_t m, int tmax,
                                                    int hub_min, Orient o, const int32_t *__restrict__ D,
-                                                   const int32_t *__restrict__ bins,
+                                                   const int32_t *__restrict__ bins, bool bins_ok,
                                                    const int32_t *__restrict__ cnt,
                                                    const int32_t *__restrict__ out_ptr, int64_t *__restrict__ omega) {
     __shared__ RowOrder s_ord;
-    if (threadIdx.x == 0) s_ord.load(cnt, n);
+    if (threadIdx.x == 0) s_ord.load(cnt, n, bins_ok);
     __syncthreads();
     const RowOrder ord = s_ord;
     const int total = ord.total();
@@ -794,8 +795,8 @@ int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
                   cudaStream_t st) {
     k_degrees<<<grid_for(n, 1024, 1 << 30), 1024, 0, st>>>(rp, n, m, t.hub_min, s.D, s.bins, s.counters);
     const RowOut ro{s.sig1, s.sig2, s.outdeg};
-    k_row_stats<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, ci, n, m, t.row_thread_max, t.hub_min, s.D, s.bins, ro,
-                                                         s.counters);
+    k_row_stats<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, ci, n, m, t.row_thread_max, t.hub_min, s.D, s.bins,
+                                                         rows_in_bins_allowed(m), ro, s.counters);
     k_row_stats_hub<<<t.num_sms * 4, ROW_CTA, 0, st>>>(rp, ci, n, s.D, s.bins, ro, s.counters);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -819,7 +820,7 @@ int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
                                                          s.info);
     const Orient o{ci, s.info, s.out_col, s.out_D, s.out_src, s.out_pd, tables ? s.out_hash : nullptr, nmin, nmax, n};
     k_orient<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, n, m, t.row_thread_max, t.hub_min, o, s.D, s.bins,
-                                                      s.counters, s.out_ptr, s.omega);
+                                                      rows_in_bins_allowed(m), s.counters, s.out_ptr, s.omega);
     k_orient_hub<<<t.num_sms * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters, s.omega);
     if (tables)
         k_hash_rows<<<(unsigned)(t.num_sms * 8), 256, 0, st>>>(rp, n, m, t.row_thread_max, s.bins + (size_t)BIN_BIG * n,

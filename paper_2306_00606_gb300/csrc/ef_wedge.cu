@@ -518,9 +518,13 @@ static int class_occupancy() {
     return 0;
 }
 
-// Opt the hub kernels in to their dynamic shared memory on the current device
-// and size the class kernels' grids (once per context, before any launch or
-// stream capture).
+// L2 size of the current device (read by prepare_kernels).
+static int64_t g_l2_bytes = 0;
+int64_t device_l2_bytes() { return g_l2_bytes; }
+
+// Opt the hub kernels in to their dynamic shared memory on the current device,
+// size the class kernels' grids and read the L2 size (once per context,
+// before any launch or stream capture).
 int prepare_kernels() {
     if (cudaFuncSetAttribute(k_wedge_hub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)hub_smem_bytes<true>()) != cudaSuccess ||
@@ -528,6 +532,10 @@ int prepare_kernels() {
                              (int)hub_smem_bytes<false>()) != cudaSuccess)
         return -1;
     if (class_occupancy<true>() || class_occupancy<false>()) return -1;
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+        return -1;
+    g_l2_bytes = l2;
     return 0;
 }
 
