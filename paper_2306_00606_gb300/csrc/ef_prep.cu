@@ -675,6 +675,29 @@ __global__ void k_hash_rows(const int32_t *__restrict__ rp, int32_t n, int64_t m
     }
 }
 
+// The same in the degree-bin layout with tmax = SMALL_MAX: the out-lists of
+// the rows of degree > SMALL_MAX are the tail of the oriented CSR (the mid
+// and hub bins come last), so a thread per entry of that tail inserts it into
+// its owner's table.  Independent entries keep many inserts in flight, where
+// a warp per row waited on four dependent loads per row.
+__global__ void k_hash_tail(const int32_t *__restrict__ cnt, const int32_t *__restrict__ lay_ptr,
+                            const int32_t *__restrict__ out_ptr, int32_t n, const int4 *__restrict__ info,
+                            const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_src,
+                            int32_t *__restrict__ out_hash) {
+    __shared__ int s_base[LAYOUT_BINS + 1];
+    if (threadIdx.x == 0) layout_bases(cnt, s_base);
+    __syncthreads();
+    const int64_t first = lay_ptr[s_base[4]];   // layout bin 4 = BIN_MID, the first list of degree > SMALL_MAX
+    const int64_t total = out_ptr[n];
+    for (int64_t k = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int a = out_src[k];
+        const int4 ia = __ldg(info + a);
+        if (((unsigned)ia.w >> DESC_KIND_SHIFT) == 1u)
+            table_insert_shared(out_hash, 4 * (int64_t)ia.z, ia.w & DESC_MASK, out_col[k]);
+    }
+}
+
 // Work items of the big middle nodes for the direct kernel: ceil(D / BIG_ROWS)
 // each; entries past the bin count are 0 so a scan over n gives the offsets.
 __global__ void k_big_chunks(const int32_t *__restrict__ D, const int32_t *__restrict__ big_list,
@@ -822,7 +845,10 @@ int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
     k_orient<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, n, m, t.row_thread_max, t.hub_min, o, s.D, s.bins,
                                                       rows_in_bins_allowed(m), s.counters, s.out_ptr, s.omega);
     k_orient_hub<<<t.num_sms * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters, s.omega);
-    if (tables)
+    if (tables && bins && t.row_thread_max >= SMALL_MAX)
+        k_hash_tail<<<(unsigned)(t.num_sms * 16), 256, 0, st>>>(s.counters, s.lay_ptr, s.out_ptr, n, s.info,
+                                                               s.out_col, s.out_src, s.out_hash);
+    else if (tables)
         k_hash_rows<<<(unsigned)(t.num_sms * 8), 256, 0, st>>>(rp, n, m, t.row_thread_max, s.bins + (size_t)BIN_BIG * n,
                                                                s.counters, s.info, s.out_ptr, s.outdeg, s.out_col,
                                                                s.out_hash);
