@@ -280,14 +280,14 @@ __device__ __forceinline__ void row_stats_warp(const int32_t *__restrict__ ci, c
 
 // Rows of degree < hub_min (RowOrder): a thread per row of degree <= tmax,
 // the warp for the others; hubs go to k_row_stats_hub.
-__global__ void k_row_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
+__global__ void __launch_bounds__(256, 6) k_row_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
                             int tmax, int hub_min, const int32_t *__restrict__ D,
                             const int32_t *__restrict__ bins, bool bins_ok, RowOut ro,
                             int32_t *__restrict__ cnt) {
     __shared__ RowOrder s_ord;
     if (threadIdx.x == 0) s_ord.load(cnt, n, bins_ok);
     __syncthreads();
-    const RowOrder ord = s_ord;
+    const RowOrder &ord = s_ord;
     const int total = ord.total();
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(256, 5) k_orient(const int32_t *__restrict__ r
     __shared__ RowOrder s_ord;
     if (threadIdx.x == 0) s_ord.load(cnt, n, bins_ok);
     __syncthreads();
-    const RowOrder ord = s_ord;
+    const RowOrder &ord = s_ord;
     const int total = ord.total();
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
