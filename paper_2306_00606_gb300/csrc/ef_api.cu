@@ -92,10 +92,11 @@ thread_local char g_err[512];
 
 // Kernels one call launches (default wedge mode): part A 3 (+1 batched),
 // f table 1, orientation (layout gather, a scan of 3, layout scatter, node
-// records, 2, hash tables of the longer rows 1; the short rows' tables are
-// filled by the orientation itself), small wedges 4, class wedges 2, pair
-// tests 1, finalize 1.
-constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 9 + 4 + 2 + 1 + 1;
+// records, the row kernel in two forms of which one returns at once, the hub
+// rows, hash tables of the longer rows; the short rows' tables are filled by
+// the row kernel itself), small wedges 4, class wedges 2, pair tests 1,
+// finalize 1.
+constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 10 + 4 + 2 + 1 + 1;
 
 void set_err(ef_ctx *c, const char *fmt, ...) {
     char *dst = c ? c->err : g_err;
