@@ -12,7 +12,7 @@
 // Pair tests: b and c are adjacent iff the higher-ranked of the two is in the
 // lower-ranked one's out-list.  That is sum_a C(|N+(a)|, 2) independent tests
 // -- 1.1e8 on the 4M-node power-law workload, against 1.15e9 dependent steps
-// for merging the two out-lists of every edge.  A warp takes 32 consecutive
+// for merging the two out-lists of every edge.  A warp takes 64 consecutive
 // oriented edges, cuts each edge's candidates c into units of TRI_UNIT and
 // spreads the units evenly over its lanes.
 //
@@ -50,10 +50,13 @@
 namespace ef {
 
 constexpr int TRI_WARPS = 8;
-// Kernel variants: candidate pairs per lane step (TRI_UNIT) and resident
-// blocks per SM the registers are sized for.  Measured on the 4M-node
-// power-law graph: (2, 4) 1.80 ms, (2, 3) 1.98, (2, 5) 2.06, (4, 3) 2.28,
-// (4, 4) 2.51 (register spills).  Variant 0 = (2, 4), 1 = (4, 3).
+// Kernel variants: candidate pairs per lane step (TRI_UNIT), resident blocks
+// per SM the registers are sized for, and oriented edges per warp step (EW).
+// Measured on the 4M-node power-law graph with EW = 32: (2, 4) 1.80 ms,
+// (2, 3) 1.98, (2, 5) 2.06, (4, 3) 2.28, (4, 4) 2.51 (register spills).
+// EW = 64 fills the last round of a step better where out-lists are short:
+// WS batch 6.13 -> 5.65 ms, BA 1M 0.174 -> 0.154, power-law 1.665 -> 1.653.
+// Variant 0 = (2, 4, 64), 1 = (4, 3, 32).
 
 __device__ __forceinline__ unsigned match4(int4 v, int key) {
     return (unsigned)(v.x == key) | (unsigned)(v.y == key) << 1 | (unsigned)(v.z == key) << 2 |
@@ -125,49 +128,55 @@ __device__ __forceinline__ void credit_tri(int64_t *qacc, int64_t *tcnt, int v, 
     atomicAdd((unsigned long long *)(tcnt + v), (unsigned long long)cnt);
 }
 
-template <int TRI_UNIT, int TRI_BLOCKS>
+template <int TRI_UNIT, int TRI_BLOCKS, int EW>
 __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
     const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_D,
     const int2 *__restrict__ out_pd, const int32_t *__restrict__ out_src, const int32_t *__restrict__ out_hash,
     const int32_t *__restrict__ outdeg, const int32_t *__restrict__ D, int32_t n,
     const int32_t *__restrict__ owner_range, const int64_t *__restrict__ tq,
     int64_t *__restrict__ qacc, int64_t *__restrict__ tcnt) {
-    __shared__ int s_ex[TRI_WARPS][32];   // exclusive prefix of unit counts
-    __shared__ int s_kend[TRI_WARPS][32], s_b[TRI_WARPS][32], s_Db[TRI_WARPS][32], s_Dab[TRI_WARPS][32];
-    __shared__ int s_a[TRI_WARPS][32];
-    __shared__ int2 s_bpd[TRI_WARPS][32];
+    static_assert(EW == 32 || EW == 64, "a warp step takes 32 or 64 edges");
+    __shared__ int s_ex[TRI_WARPS][EW];   // exclusive prefix of unit counts
+    __shared__ int s_kend[TRI_WARPS][EW], s_b[TRI_WARPS][EW], s_Db[TRI_WARPS][EW], s_Dab[TRI_WARPS][EW];
+    __shared__ int s_a[TRI_WARPS][EW];
+    __shared__ int2 s_bpd[TRI_WARPS][EW];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t total = out_ptr[n];
-    const int64_t stride = (int64_t)gridDim.x * TRI_WARPS * 32;
+    const int64_t stride = (int64_t)gridDim.x * TRI_WARPS * EW;
     // owners a in [a_lo, a_hi) open their pairs (all nodes, or one shard's range)
     const int a_lo = owner_range ? owner_range[0] : 0, a_hi = owner_range ? owner_range[1] : n;
-    for (int64_t K0 = ((int64_t)blockIdx.x * TRI_WARPS + w) * 32; K0 < total; K0 += stride) {
-        const int64_t k = K0 + lane;
-        int nu = 0;
-        if (k < total) {
-            const int a = out_src[k];
-            const int kend = out_ptr[a] + outdeg[a];
-            const int np = a >= a_lo && a < a_hi ? kend - (int)k - 1 : 0;
-            if (np > 0) {
-                const int b = out_col[k];
-                const int Db = out_D[k];
-                s_kend[w][lane] = kend;
-                s_b[w][lane] = b;
-                s_Db[w][lane] = Db;
-                s_bpd[w][lane] = out_pd[k];
-                s_Dab[w][lane] = D[a] + Db;
-                s_a[w][lane] = a;
-                nu = (np + TRI_UNIT - 1) / TRI_UNIT;
-            }
-        }
-        int inc = nu;
+    for (int64_t K0 = ((int64_t)blockIdx.x * TRI_WARPS + w) * EW; K0 < total; K0 += stride) {
+        int U = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, inc, o);
-            if (lane >= o) inc += y;
+        for (int h = 0; h < EW / 32; ++h) {
+            const int e = h * 32 + lane;
+            const int64_t k = K0 + e;
+            int nu = 0;
+            if (k < total) {
+                const int a = out_src[k];
+                const int kend = out_ptr[a] + outdeg[a];
+                const int np = a >= a_lo && a < a_hi ? kend - (int)k - 1 : 0;
+                if (np > 0) {
+                    const int b = out_col[k];
+                    const int Db = out_D[k];
+                    s_kend[w][e] = kend;
+                    s_b[w][e] = b;
+                    s_Db[w][e] = Db;
+                    s_bpd[w][e] = out_pd[k];
+                    s_Dab[w][e] = D[a] + Db;
+                    s_a[w][e] = a;
+                    nu = (np + TRI_UNIT - 1) / TRI_UNIT;
+                }
+            }
+            int inc = nu;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += y;
+            }
+            s_ex[w][e] = U + inc - nu;
+            U += __shfl_sync(FULL, inc, 31);
         }
-        s_ex[w][lane] = inc - nu;
-        const int U = __shfl_sync(FULL, inc, 31);
         __syncwarp();
         int cur_a = -1, hit_a = 0;
         int64_t acc_a = 0;
@@ -175,10 +184,10 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
         int2 bpd = make_int2(0, 0);
         for (int t = lane; t < U; t += 32) {
             // the warp edge owning unit t: the last i with s_ex[i] <= t (s_ex is
-            // non-decreasing; i + step <= 31 at every step)
+            // non-decreasing; i + step <= EW - 1 at every step)
             int ni = 0;
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
+            for (int step = EW / 2; step > 0; step >>= 1)
                 if (s_ex[w][ni + step] <= t) ni += step;
             if (ni != i) {
                 i = ni;
@@ -254,11 +263,11 @@ int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cuda
                      const int32_t *owner_range) {
     const unsigned grid = grid_of(m / 2, TRI_WARPS * 32, (int64_t)t.num_sms * 16);
     if (t.tri_variant == 1)
-        k_tri_pairs<4, 3><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pd, s.out_src,
+        k_tri_pairs<4, 3, 32><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pd, s.out_src,
                                                             s.out_hash, s.outdeg, s.D, n, owner_range, s.tq, s.qacc,
                                                             s.tcnt);
     else
-        k_tri_pairs<2, 4><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pd, s.out_src,
+        k_tri_pairs<2, 4, 64><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pd, s.out_src,
                                                             s.out_hash, s.outdeg, s.D, n, owner_range, s.tq, s.qacc,
                                                             s.tcnt);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
