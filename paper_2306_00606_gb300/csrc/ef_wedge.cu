@@ -43,13 +43,22 @@ __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__
         const int ak = own ? D[x] : 0;
         const int b0 = Du - 4 + ak;
         Acc acc = 0;
-#pragma unroll
-        for (int j = 0; j < G; ++j) {
-            const int aj = __shfl_sync(FULL, ak, j, G);
-            if (own && j < Du && j != k) {
-                const int d = b0 + aj;  // >= 0 for D_u >= 2
-                if constexpr (F64) acc += __ldg(ftab + d);
-                else acc += dlog2d(fmaxf((float)d, 1.0f));
+        // the warp's largest row bounds the loop (rows of a bin are often
+        // much shorter than G); degrees travel as floats (exact below 2^24),
+        // so no conversion sits in the loop
+        const int jmax = __reduce_max_sync(FULL, Du);
+        if constexpr (F64) {
+#pragma unroll 4
+            for (int j = 0; j < jmax; ++j) {
+                const int aj = __shfl_sync(FULL, ak, j, G);
+                if (own && j < Du && j != k) acc += __ldg(ftab + (b0 + aj));   // b0 + aj >= 0 for D_u >= 2
+            }
+        } else {
+            const float akf = (float)ak, b0f = (float)b0;
+#pragma unroll 4
+            for (int j = 0; j < jmax; ++j) {
+                const float t = dlog2d(fmaxf(b0f + __shfl_sync(FULL, akf, j, G), 1.0f));
+                if (own && j < Du && j != k) acc += t;
             }
         }
         const Acc r = own ? (F64 ? acc : acc * (Acc)LN2) : (Acc)0;
