@@ -83,6 +83,22 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int *total = nullptr)
 }
 
 // --------------------------------------------------------- degrees + bins
+// A slot in bin b (b < 0: none) of the block's counts s_cnt: the lanes of a
+// warp with the same bin take consecutive slots from one atomic.
+__device__ __forceinline__ int warp_bin_slot(int *s_cnt, int b) {
+    const unsigned want = __ballot_sync(FULL, b >= 0);
+    int p = 0;
+    if (b >= 0) {
+        const unsigned peers = __match_any_sync(want, b);
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        int first = 0;
+        if (lane == leader) first = atomicAdd(&s_cnt[b], __popc(peers));
+        first = __shfl_sync(peers, first, leader);
+        p = first + __popc(peers & ((1u << lane) - 1u));
+    }
+    return p;
+}
+
 // Thread per node: D, max degree, row_ptr checks, and the wedge bins (they
 // depend on D only): small sub-warp bins, or "big" plus the mid list or a
 // hub bucket.  Block-level counting in shared memory, one global atomic per
@@ -117,8 +133,10 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
         }
     }
     if (v == 0 && (rp[0] != 0 || (int64_t)rp[n] != m)) err |= ERRB_ROWPTR;
-    if (b0 >= 0) p0 = atomicAdd(&s_cnt[b0], 1);
-    if (b1 >= 0) p1 = atomicAdd(&s_cnt[b1], 1);
+    // positions in the block's bins: one shared atomic per bin and warp
+    // (lattices put a whole block in one or two bins)
+    p0 = warp_bin_slot(s_cnt, b0);
+    p1 = warp_bin_slot(s_cnt, b1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mx = max(mx, __shfl_xor_sync(FULL, mx, o));
@@ -869,15 +887,29 @@ int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
 // pass, so the first and last entries decide.
 __global__ void k_batch_check(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
                               const int64_t *__restrict__ goff, int32_t G, int32_t *__restrict__ cnt) {
+    // a warp takes 32 consecutive rows: one binary search for the graph of the
+    // first (by lane 0), then each lane steps forward to its own graph
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     int err = 0;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        int lo = 0, hi = G - 1;   // last g with goff[g] <= v
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (goff[mid] <= v) lo = mid; else hi = mid - 1;
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+         base += nwarps * 32) {
+        int g0 = 0;
+        if (lane == 0) {
+            int lo = 0, hi = G - 1;   // last g with goff[g] <= base
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (goff[mid] <= base) lo = mid; else hi = mid - 1;
+            }
+            g0 = lo;
         }
-        const int a = rp[v], b = rp[v + 1];   // bad row pointers are reported by k_degrees
-        if (a >= 0 && a < b && (int64_t)b <= m && (ci[a] < goff[lo] || ci[b - 1] >= goff[lo + 1])) err |= ERRB_CROSS;
+        int g = __shfl_sync(FULL, g0, 0);
+        const int64_t v = base + lane;
+        if (v < n) {
+            while (g + 1 < G && goff[g + 1] <= v) ++g;
+            const int a = rp[v], b = rp[v + 1];   // bad row pointers are reported by k_degrees
+            if (a >= 0 && a < b && (int64_t)b <= m && (ci[a] < goff[g] || ci[b - 1] >= goff[g + 1])) err |= ERRB_CROSS;
+        }
     }
     err = __reduce_or_sync(FULL, err);
     if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
