@@ -54,11 +54,15 @@ __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__
                 if (own && j < Du && j != k) acc += __ldg(ftab + (b0 + aj));   // b0 + aj >= 0 for D_u >= 2
             }
         } else {
+            // d = D_u - 4 + D_x + D_j >= 3 once D_u > 4 (G >= 8): only the
+            // smallest bin needs the guard that keeps d = 0 from 0 * log2(0)
             const float akf = (float)ak, b0f = (float)b0;
+            const int lim = own ? Du : 0;
 #pragma unroll 4
             for (int j = 0; j < jmax; ++j) {
-                const float t = dlog2d(fmaxf(b0f + __shfl_sync(FULL, akf, j, G), 1.0f));
-                if (own && j < Du && j != k) acc += t;
+                const float d = b0f + __shfl_sync(FULL, akf, j, G);
+                const float t = dlog2d(G == 4 ? fmaxf(d, 1.0f) : d);
+                if (j < lim && j != k) acc += t;
             }
         }
         const Acc r = own ? (F64 ? acc : acc * (Acc)LN2) : (Acc)0;

@@ -189,6 +189,28 @@ TUNINGS = [dict(row_thread_max=8, hub_min=513, tri_variant=0, grid_per_sm=64, la
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
+def test_tunings_on_a_graph_without_rows_above_32(ctx, tuning):
+    """No node of degree > 32: the row passes keep node order and the
+    orientation's one-thread rows gather eight records at a time; with
+    row_thread_max below the degrees, rows go to the warp path instead."""
+    import paper_2306_00606_gb300 as ef
+    g = synth.disjoint_union([synth.watts_strogatz(6000, 12, 0.1, 23), synth.erdos_renyi(3000, 0.004, 24)])
+    assert g.degrees.max() <= 32
+    ef.ef_set_tuning(ctx.handle, None)
+    base = run_one(ctx, g.row_ptr, g.col_idx, "fp64")
+    ref = oracle.alg1(g)
+    np.testing.assert_array_equal(base["n_clusters"], ref["N"])
+    np.testing.assert_array_equal(base["s"], ref["S"])
+    np.testing.assert_array_equal(base["triangles"], oracle.triangles(g))
+    np.testing.assert_allclose(base["ef"], ref["EF"], rtol=EF_RTOL64, atol=1e-12)
+    ef.ef_set_tuning(ctx.handle, tuning)
+    try:
+        _same(run_one(ctx, g.row_ptr, g.col_idx, "fp64"), base, "fp64")
+    finally:
+        ef.ef_set_tuning(ctx.handle, None)
+
+
+@pytest.mark.parametrize("tuning", TUNINGS)
 def test_tunings_give_the_same_results(ctx, tuning):
     import paper_2306_00606_gb300 as ef
     g = synth.powerlaw_cm(20000, 2.1, 2, 3000, 22)
