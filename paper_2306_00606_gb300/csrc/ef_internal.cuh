@@ -279,7 +279,8 @@ constexpr int DESC_MASK = (1 << DESC_KIND_SHIFT) - 1;
 __device__ __forceinline__ int2 probe_desc(int ls, int le, int64_t hash_cap) {
     int64_t hb;
     int nb;
-    if (out_table(ls, le, hash_cap, hb, nb)) return make_int2((int)(hb >> 2), (int)((unsigned)nb | 1u << DESC_KIND_SHIFT));
+    if (out_table(ls, le, hash_cap, hb, nb))
+        return make_int2((int)(hb >> 2), (int)((unsigned)nb | 1u << DESC_KIND_SHIFT));
     if (le - ls > SHORT_MAX) return make_int2(ls, (int)((unsigned)le | 2u << DESC_KIND_SHIFT));
     const int q0 = ls >> 2;
     return make_int2(q0, (int)(range_bits(4 * q0, ls, le) | range_bits(4 * q0 + 4, ls, le) << 4));

@@ -180,13 +180,14 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
 
 // Row order of the one-thread row passes (k_row_stats, k_orient), decided on
 // the device from the degree pass's counts when the host allows it
-// (rows_in_bins_allowed): when the graph has rows of degree > 32 (degrees
-// spread out), the rows of degree 1..32 are taken in work-bin order (the lists of degree classes 1-4, 5-8, 9-16, 17-32 one after the
-// other), so that the 32 rows of a warp have similar lengths, and the rows of
-// degree 33..hub_min-1 from their list, a warp each; otherwise (lattices,
-// small-world graphs) in node order, where neighbouring rows share cache
-// lines.  Measured: BA n = 1M orientation 0.36 -> 0.25 ms in bin order; the
-// 4096-graph WS batch 4.7 -> 5.7 ms, so it keeps node order.
+// (rows_in_bins_allowed).  When the graph has rows of degree > 32 (degrees
+// spread out), the rows of degree 1..32 are taken in work-bin order (the
+// lists of degree classes 1-4, 5-8, 9-16 and 17-32 one after the other), so
+// that the 32 rows of a warp have similar lengths, and the rows of degree
+// 33..hub_min-1 from their list, a warp each.  Otherwise (lattices,
+// small-world graphs) they go in node order, where neighbouring rows share
+// cache lines.  Measured: BA n = 1M orientation 0.36 -> 0.25 ms in bin
+// order; the 4096-graph WS batch 4.7 -> 5.7 ms, so it keeps node order.
 struct RowOrder {
     int base[5];   // bin order: first position of each small class, then their total
     bool bins;
@@ -298,10 +299,10 @@ __device__ __forceinline__ void row_stats_warp(const int32_t *__restrict__ ci, c
 
 // Rows of degree < hub_min (RowOrder): a thread per row of degree <= tmax,
 // the warp for the others; hubs go to k_row_stats_hub.
-__global__ void __launch_bounds__(256, 6) k_row_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
-                            int tmax, int hub_min, const int32_t *__restrict__ D,
-                            const int32_t *__restrict__ bins, bool bins_ok, RowOut ro,
-                            int32_t *__restrict__ cnt) {
+__global__ void __launch_bounds__(256, 6) k_row_stats(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                                      int32_t n, int64_t m, int tmax, int hub_min,
+                                                      const int32_t *__restrict__ D, const int32_t *__restrict__ bins,
+                                                      bool bins_ok, RowOut ro, int32_t *__restrict__ cnt) {
     __shared__ RowOrder s_ord;
     if (threadIdx.x == 0) s_ord.load(cnt, n, bins_ok);
     __syncthreads();
