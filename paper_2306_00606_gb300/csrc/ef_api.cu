@@ -90,13 +90,16 @@ namespace {
 
 thread_local char g_err[512];
 
-// Kernels one call launches (default wedge mode): part A 3 (+1 batched),
-// f table 1, orientation (layout gather, a scan of 3, layout scatter, node
-// records, the row kernel in two forms of which one returns at once, the hub
-// rows, hash tables of the longer rows; the short rows' tables are filled by
-// the row kernel itself), small wedges 4, class wedges 2, pair tests 1,
-// finalize 1.
-constexpr int64_t KERNELS_PER_CALL = 3 + 1 + 10 + 4 + 2 + 1 + 1;
+// Kernels one call launches: part A 3 (+1 batched), f table 1, orientation
+// (degree-bin layout: layout gather, a scan of 3, layout scatter; node
+// layout: a scan of 3; then node records, the row kernel in two forms of
+// which one returns at once, the hub rows, hash tables of the longer rows;
+// the short rows' tables are filled by the row kernel itself), small wedges
+// 4, big wedges (class kernels 2; direct mode: item counts, a scan of 3,
+// direct kernel, reduction), pair tests 1, finalize 1.
+int64_t kernels_per_call(bool batched, bool bins, int wedge_mode) {
+    return 3 + (batched ? 1 : 0) + 1 + (bins ? 5 : 3) + 5 + 4 + (wedge_mode == 1 ? 6 : 2) + 1 + 1;
+}
 
 void set_err(ef_ctx *c, const char *fmt, ...) {
     char *dst = c ? c->err : g_err;
@@ -340,7 +343,7 @@ int check_args(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_opti
 
 // Events: 0 start, 1 part B start (after the validation readback), 2..6
 // after orientation, small wedges, big wedges, hash tables, pair tests, 7 end.
-void accumulate_stats(ef_ctx *ctx, bool batched) {
+void accumulate_stats(ef_ctx *ctx, bool batched, int wedge_mode) {
     auto el = [&](int a, int b) {
         float t = 0.f;
         return cudaEventElapsedTime(&t, ctx->ev[a], ctx->ev[b]) == cudaSuccess ? (double)t : 0.0;
@@ -354,7 +357,7 @@ void accumulate_stats(ef_ctx *ctx, bool batched) {
     st.tri_pairs_ms += el(4, 6);
     st.finalize_ms += el(6, 7);
     st.total_ms += el(0, 7);
-    st.kernels += KERNELS_PER_CALL + (batched ? 1 : 0);
+    st.kernels += kernels_per_call(batched, ctx->bins, wedge_mode);
 }
 
 // Host I/O and synchronisation around compute_device.
@@ -398,7 +401,7 @@ int run_job(ef_ctx *ctx, Job j, const ef_outputs *host_out) {
     if (rc) return rc;
     if (!j.o.async) {
         CU(cudaStreamSynchronize(ctx->stream));
-        if (j.o.profile) accumulate_stats(ctx, j.goff_dev != nullptr);
+        if (j.o.profile) accumulate_stats(ctx, j.goff_dev != nullptr, j.o.wedge_mode);
     }
     CU(cudaGetLastError());
     return EF_OK;
