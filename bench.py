@@ -10,9 +10,13 @@ wedge pass, triangle pass, finalize), FP32-compensated path, inputs resident
 in HBM.  The metric is clusters/s = W / step time with W = sum_v C(D_v, 2),
 the number of clusters Algorithm 1 enumerates.
 
-Prints one JSON line.  `--impl reference` times the CPU oracle instead (the
-vertex-centric formulation, OpenMP over the host cores) on a bounded random
-sample of the same graph.
+Prints one JSON line.  Beside the headline it carries the other workloads
+(`workloads`: ER 2000 and BA 1M in both precisions, the power-law graph in
+FP64, its minimum-degree-6 variant with 4.4e7 undirected edges, the 4096-graph
+Watts-Strogatz batch with its per-graph time distribution, BA 16M).
+`--impl reference` times the CPU oracle instead (the vertex-centric
+formulation, OpenMP over the host cores) on bounded random node samples of
+the same graph, the same samples the `cpu_baseline` key reports.
 """
 from __future__ import annotations
 
@@ -38,6 +42,9 @@ WORKLOADS = {
     "er2000": (1, "Erdos-Renyi G(n=2000, p=0.004) seed=20230607"),
     "ws4096": (4, "batch of 4096 Watts-Strogatz graphs, n ~ U[200,20000], k ~ U{4,...,12} even, p=0.1, "
                   "seed=20230610, one ef_compute_batched call (replayed CUDA graph)"),
+    "plcm4m_d6": ("3b", "power-law configuration model n=4000000 gamma=2.3 degrees in [6,20000] seed=20230612 "
+                        "(4.4e7 undirected edges)"),
+    "ba16m": (5, "Barabasi-Albert n=16000000 m=4 seed=20230611"),
 }
 BATCHED = {"ws4096"}
 PASSES = ("prep_ms", "orient_ms", "wedge_small_ms", "wedge_big_ms", "tri_pairs_ms", "finalize_ms")
@@ -107,6 +114,7 @@ def parse():
     p.add_argument("--no-surrogate", action="store_true", help="skip the learned ranking leg")
     p.add_argument("--surrogate-steps", type=int, default=3000)
     p.add_argument("--no-shards", action="store_true", help="skip the sharded-decomposition leg")
+    p.add_argument("--no-workloads", action="store_true", help="skip the other workloads' leg")
     p.add_argument("--sir", action="store_true", help="run the SIR validation leg (Figs. 6-8 protocols, BA 1M)")
     p.add_argument("--sir-batch", type=int, default=0, metavar="B",
                    help="only time one ef_sir_run of B simulations from the highest-degree node of BA 1M "
@@ -220,33 +228,65 @@ def graph_stats(g):
                 small_evals=int((d[d <= 32] * (d[d <= 32] - 1)).sum()), maxdeg=int(d.max()) if g.n else 0)
 
 
-def cpu_baseline(g, seconds: float, seed: int = 0):
-    """The oracle (vertex-centric, OpenMP on all host cores) on a random node
-    sample sized for about `seconds` of CPU work.  Returns clusters/s, where a
-    sample's cluster count is the sum of its nodes' credited clusters / 4
-    (every cluster carries 4 credits), so the rate is comparable with W/t."""
+def _closed_credits(g):
+    """Credited clusters per node, N_v = D_v (D_v - 2) + sigma1(v) (the oracle's work per node)."""
+    d = g.degrees.astype(np.int64)
+    src = np.repeat(np.arange(g.n), d)
+    return d * (d - 2) + np.bincount(src, weights=d[g.col_idx], minlength=g.n).astype(np.int64)
+
+
+def oracle_steps(g, steps: int, seconds: float, seed0: int = 0):
+    """Time the oracle (vertex-centric, OpenMP dynamic over all host cores) on
+    `steps` random node samples of about `seconds` each; yields one dict per
+    step.  A sample draws uniformly from the nodes whose own work (N_v
+    credits) is at most 1/(2 x cores) of the step's, so that no single node
+    keeps one core busy after the others finish, sorted largest first.  The
+    step size comes from a short calibration run; seeds seed0, seed0 + 1, ...
+    make the samples the same in every run."""
     import oracle
-    rng = np.random.default_rng(seed)
     cores = oracle.num_threads()
-    k = 2000
-    t_used = 0.0
-    credits = 0
-    nodes_done = 0
+    N = _closed_credits(g)
+    # calibration: random nodes of at most 50x the median work, doubling
+    # until a run takes 0.25 s (or covers the graph)
+    rng = np.random.default_rng(12345)
+    pool = rng.permutation(np.nonzero(N <= max(int(np.median(N)) * 50, 1))[0]).astype(np.int32)
+    k = min(2000, len(pool))
     while True:
-        nodes = rng.choice(g.n, size=min(k, g.n), replace=False).astype(np.int32)
         t0 = time.perf_counter()
-        r = oracle.vertex(g, nodes, threads=cores)
+        oracle.vertex(g, pool[:k], threads=cores)
         dt = time.perf_counter() - t0
-        t_used += dt
-        credits += int(r["N"].sum())
-        nodes_done += len(nodes)
-        if t_used >= seconds or len(nodes) == g.n:
+        if dt >= 0.25 or k >= len(pool):
             break
-        k = int(min(g.n, max(2000, k * max(1.5, min(8.0, (seconds - t_used) / max(dt, 1e-3))))))
-    rate = credits / 4 / t_used
-    return {"value": rate, "unit": "clusters/s", "cores": cores, "kind": "oracle",
-            "sample": f"{nodes_done} uniformly random nodes (vertex-centric oracle, OpenMP dynamic,2), "
-                      f"{credits / 4:.3g} clusters = credited/4, {t_used:.1f} s"}
+        k = min(len(pool), 2 * k)
+    rate = max(int(N[pool[:k]].sum()), 1) / max(dt, 1e-4)   # credits/s
+    target = rate * seconds
+    cap = max(target / (2 * cores), float(np.percentile(N, 50)))
+    eligible = np.nonzero(N <= cap)[0]
+    for i in range(steps):
+        r = np.random.default_rng(seed0 + i)
+        perm = r.permutation(eligible)
+        k = int(np.searchsorted(np.cumsum(N[perm]), target)) + 1
+        nodes = perm[:min(k, len(perm))]
+        nodes = nodes[np.argsort(-N[nodes], kind="stable")].astype(np.int32)
+        t0 = time.perf_counter()
+        res = oracle.vertex(g, nodes, threads=cores)
+        dt = time.perf_counter() - t0
+        yield {"nodes": len(nodes), "clusters": int(res["N"].sum()) / 4, "s": dt, "cores": cores,
+               "eligible": len(eligible), "cap": cap}
+
+
+def cpu_baseline(g, seconds: float, steps: int = 3, seed0: int = 0):
+    """The oracle's clusters/s on `steps` samples of `seconds` / `steps` each
+    (oracle_steps; a sample's cluster count is its nodes' credited clusters
+    / 4, as every cluster carries 4 credits, so the rate compares with W/t)."""
+    rows = list(oracle_steps(g, steps, seconds / steps, seed0))
+    clusters = sum(r["clusters"] for r in rows)
+    t = sum(r["s"] for r in rows)
+    return {"value": clusters / t, "unit": "clusters/s", "cores": rows[0]["cores"], "kind": "oracle",
+            "sample": f"{steps} samples (seeds {seed0}..{seed0 + steps - 1}) of {sum(r['nodes'] for r in rows)} "
+                      f"uniformly random nodes in all, drawn from the {rows[0]['eligible']} nodes with at most "
+                      f"{rows[0]['cap']:.3g} credited clusters; vertex-centric oracle, OpenMP dynamic,2, "
+                      f"{clusters:.3g} clusters = credited/4, {t:.1f} s"}
 
 
 def rmat_sweep(ctx, args, dev) -> list:
@@ -275,7 +315,7 @@ def rmat_sweep(ctx, args, dev) -> list:
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / 10
         W = graph_stats(g)["W"]
-        cpu = cpu_baseline(g, 2.0, seed=M)
+        cpu = cpu_baseline(g, 2.0, steps=1, seed0=M)
         rows.append({"M": M, "nodes": g.n, "nnz": g.nnz, "avg_degree": g.nnz / g.n, "clusters": W, "ms": ms,
                      "clusters_per_ms": W / ms, "oracle_clusters_per_ms": cpu["value"] / 1e3,
                      "oracle_cores": cpu["cores"], "gpu_over_oracle": (W / ms) / (cpu["value"] / 1e3)})
@@ -513,31 +553,140 @@ def surrogate_leg(args, dev) -> dict:
             "network": "16-64-64-1 ReLU, BF16 mma.sync, FP32 accumulate"}
 
 
+def workload_config(desc, g, st, batched: bool, gpus: int) -> dict:
+    """The `config` of a bench line: the workload and its sizes (both arms print the same)."""
+    n = g.n
+    return {"workload": desc, "nodes": n, "nnz": g.nnz, "edges": g.nnz // 2, "clusters": st["W"],
+            "graphs": len(g.graph_off) - 1 if batched else 1, "max_degree": st["maxdeg"],
+            "l2": f"inputs larger than L2 (CSR {(4 * (n + 1) + 4 * g.nnz) / 2**20:.0f} MiB), no flush",
+            "parallelism": f"replicas x{gpus}"}
+
+
 def run_reference(args):
+    """The oracle as the reference arm: each step times the oracle on one
+    bounded random node sample of the workload (oracle_steps: the samples of
+    seeds 0, 1, ... are the ones `cpu_baseline` times in the GPU arm), about
+    cpu_seconds / 3 per step, shortened so that warm-up and steps stay
+    within about 150 s."""
     rank, world, local = dist_env()
     if rank != 0:
         return 0
     idx, desc = WORKLOADS[args.workload]
     g = synth.workload(idx)
     st = graph_stats(g)
-    rates = []
-    for _ in range(args.warmup):
-        cpu_baseline(g, min(2.0, args.cpu_seconds / 4), seed=99)
-    t_total = 0.0
-    for i in range(args.steps):
-        r = cpu_baseline(g, args.cpu_seconds / max(args.steps, 1) * 2, seed=i)
-        rates.append(r["value"])
-        t_total += st["W"] / r["value"]
-    v = float(statistics.median(rates))
+    batched = args.workload in BATCHED
+    per_step = min(args.cpu_seconds / 3, 150.0 / max(args.steps + args.warmup, 1))
+    for _ in oracle_steps(g, args.warmup, per_step, seed0=1000):
+        pass
+    rows = list(oracle_steps(g, args.steps, per_step, seed0=0))
+    clusters = sum(r["clusters"] for r in rows)
+    t = sum(r["s"] for r in rows)
+    v = clusters / t
     line = {"impl": "reference", "metric": "clusters/s", "value": v, "unit": "clusters/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": st["W"] / v * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": desc, "nodes": st["n"], "nnz": st["nnz"],
-                                            "clusters": st["W"]},
-            "cpu_baseline": dict(r, value=v),
+            "data": "synthetic", "config": workload_config(desc, g, st, batched, args.gpus),
+            "cpu_baseline": {"value": v, "unit": "clusters/s", "cores": rows[0]["cores"], "kind": "oracle",
+                             "sample": f"each step: uniformly random nodes sized for {per_step:.1f} s by a calibration run, "
+                                       f"among those with at most {rows[0]['cap']:.3g} credited clusters (seeds "
+                                       f"0..{args.steps - 1}; {args.warmup} warm-up samples of seeds 1000..), "
+                                       f"{sum(r['nodes'] for r in rows)} nodes and {clusters:.3g} clusters in "
+                                       f"all, {t:.1f} s measured"},
             "e2e": {"value": v, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def _time_events(fn, stream, dev, reps: int, warm: int = 3) -> float:
+    """Mean ms per call of fn over `reps` calls (CUDA events on `stream`) after `warm` untimed calls."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / reps
+
+
+def workloads_leg(args, dev, hbm: float) -> dict:
+    """Every workload besides the headline one, one ef_compute_ex (or
+    ef_compute_batched) per step, inputs in HBM, 3 warm-up and 10 timed
+    calls (CUDA events): ms per graph, clusters/s, the per-pass breakdown
+    (a profiled call) and the path's algorithmic bytes (CSR read once, EF
+    written once) against HBM.  The batch adds each graph's own time as a
+    call of its own (host wall clock around the synchronous call)."""
+    import torch
+    import paper_2306_00606_gb300 as ef
+    stream = torch.cuda.current_stream(dev)
+    ctx = ef.Context(dev.index, stream)
+    plan = [("er2000", ("fp32c", "fp64")), ("ba1m", ("fp32c", "fp64")), ("plcm4m", ("fp64",)),
+            ("plcm4m_d6", ("fp32c", "fp64")), ("ws4096", ("fp32c", "fp64")), ("ba16m", ("fp32c", "fp64"))]
+    res = {}
+    for name, precs in plan:
+        idx, desc = WORKLOADS[name]
+        g = synth.workload(idx)
+        gs = graph_stats(g)
+        batched = name in BATCHED
+        G = len(g.graph_off) - 1 if batched else 1
+        rp = torch.from_numpy(g.row_ptr).to(dev)
+        ci = torch.from_numpy(g.col_idx).to(dev)
+        out = torch.empty(g.n, dtype=torch.float64, device=dev)
+        path_bytes = 4 * (g.n + 1) + 4 * g.nnz + 8 * g.n
+        entry = {"workload": desc, "nodes": g.n, "nnz": g.nnz, "edges": g.nnz // 2, "clusters": gs["W"],
+                 "graphs": G, "max_degree": gs["maxdeg"]}
+        for prec in precs:
+            if batched:
+                def call(profile=False):
+                    ef.ef_compute_batched(ctx.handle, rp, ci, g.graph_off, precision=prec, ef=out,
+                                          graph=not profile, profile=profile)
+            else:
+                def call(profile=False):
+                    ef.ef_compute_ex(ctx.handle, rp, ci, precision=prec, ef=out, profile=profile)
+            ms = _time_events(call, stream, dev, reps=10)
+            ctx.stats(reset=True)
+            call(profile=True)
+            pst = ctx.stats(reset=True)
+            entry[prec] = {"ms_per_step": ms, "ms_per_graph": ms / G, "clusters_per_s": gs["W"] / (ms / 1e3),
+                           "passes_ms": {k: pst[k] for k in PASSES},
+                           "roofline_path": {"bound": "hbm", "algorithmic_bytes": path_bytes,
+                                             "achieved": path_bytes / (ms / 1e3) / 1e9, "peak": hbm,
+                                             "unit": "GB/s", "frac": path_bytes / (ms / 1e3) / 1e9 / hbm}}
+        if batched:
+            # each graph alone: its rows relabelled to 0.., one synchronous call each
+            off = g.graph_off
+            walls, works = [], []
+            for k in range(G):
+                a, b = int(off[k]), int(off[k + 1])
+                e0, e1 = int(g.row_ptr[a]), int(g.row_ptr[b])
+                srp = (rp[a:b + 1] - e0).contiguous()
+                sci = (ci[e0:e1] - a).contiguous()
+                sout = out[a:b]
+                if k < 8:
+                    for _ in range(2):
+                        ef.ef_compute_ex(ctx.handle, srp, sci, precision="fp32c", ef=sout)
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                ef.ef_compute_ex(ctx.handle, srp, sci, precision="fp32c", ef=sout)
+                walls.append((time.perf_counter() - t0) * 1e3)
+                d = np.diff(g.row_ptr[a:b + 1]).astype(np.int64)
+                works.append(int((d * (d - 1) // 2).sum()))
+            w = np.array(walls)
+            entry["per_graph_alone_fp32c"] = {
+                "calls": G, "ms_p10": float(np.percentile(w, 10)), "ms_p50": float(np.percentile(w, 50)),
+                "ms_p90": float(np.percentile(w, 90)), "ms_p99": float(np.percentile(w, 99)),
+                "ms_max": float(w.max()), "ms_sum": float(w.sum()),
+                "clusters_per_graph_p10_p50_p90": [float(np.percentile(works, q)) for q in (10, 50, 90)],
+                "note": "each graph as a separate synchronous ef_compute_ex call (host wall clock, validation "
+                        "readback included); the batched call above runs all of them in one pass"}
+        res[name] = entry
+        del rp, ci, out
+        torch.cuda.empty_cache()
+    ctx.close()
+    return res
 
 
 def run_ours(args):
@@ -650,8 +799,8 @@ def run_ours(args):
     roofline = {"kernel": PASS_KERNEL[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": committed_traffic(PASS_KERNEL[dom], args.workload),
                 "algorithmic_bytes": alg[dom], "launch_ms": per[dom], "peak_source": src,
-                "note": "bytes = each input read once and each output written once (per-pass formulas "
-                        "in DESIGN.md); " + PASS_NOTE[dom]}
+                "note": "bytes = each input read once and each output written once (bench.py "
+                        "algorithmic_bytes); " + PASS_NOTE[dom]}
     # the wedge passes against the MUFU issue bound: one lg2 per f evaluation,
     # 16 special-function results per SM per clock
     evals = st["small_evals"] + class_evals(g)
@@ -673,12 +822,8 @@ def run_ours(args):
         "metric": "clusters/s", "value": value, "unit": "clusters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32c" else "f64", "data": "synthetic",
-        "config": {"workload": desc, "nodes": n, "nnz": g.nnz, "edges": g.nnz // 2, "clusters": st["W"],
-                   "graphs": len(g.graph_off) - 1 if batched else 1,
-                   "tuning": ef.ef_get_tuning(ctx.handle), "autotuned": bool(args.autotune),
-                   "max_degree": st["maxdeg"], "precision": args.precision,
-                   "l2": f"inputs larger than L2 (CSR {(4 * (n + 1) + 4 * g.nnz) / 2**20:.0f} MiB), no flush",
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(desc, g, st, batched, world),
+        "precision": args.precision, "tuning": ef.ef_get_tuning(ctx.handle), "autotuned": bool(args.autotune),
         "ef_wall_ms_per_graph": ms_step / (len(g.graph_off) - 1 if batched else 1),
         "graph_replays_in_timed_region": replays,
         "passes_ms": per,
@@ -699,14 +844,21 @@ def run_ours(args):
         line["sir"] = sir_leg(args, dev)
     if rank == 0 and args.rmat_sweep:
         line["rmat_sweep"] = rmat_sweep(ctx, args, dev)
-    if rank == 0 and world == 1 and not args.no_surrogate and args.scale == 1.0:
+    extra = rank == 0 and world == 1 and args.scale == 1.0 and args.workload == "plcm4m"
+    if extra and not (args.no_workloads and args.no_surrogate):
         del rp, ci, out
         ctx.close()
         torch.cuda.empty_cache()
-        try:
-            line["surrogate"] = surrogate_leg(args, dev)
-        except Exception as e:   # reported, the main line stands
-            line["surrogate"] = {"error": f"{type(e).__name__}: {e}"}
+        if not args.no_workloads:
+            try:
+                line["workloads"] = workloads_leg(args, dev, hbm)
+            except Exception as e:   # reported, the main line stands
+                line["workloads"] = {"error": f"{type(e).__name__}: {e}"}
+        if not args.no_surrogate:
+            try:
+                line["surrogate"] = surrogate_leg(args, dev)
+            except Exception as e:   # reported, the main line stands
+                line["surrogate"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

@@ -45,7 +45,9 @@ enum ef_status {
     EF_ERR_GRAPH = 2,       /* not a symmetric simple sorted CSR (checked on device) */
     EF_ERR_OOM = 3,         /* device or pinned allocation failed */
     EF_ERR_CUDA = 4,        /* a CUDA runtime call failed */
-    EF_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    EF_ERR_TIMEOUT = 5,     /* reserved: no call returns it (no kernel of
+                               this library waits on a flag or on another
+                               device, so there is no watchdog) */
     EF_ERR_MODEL = 6,       /* surrogate model malformed or mismatched */
     EF_ERR_UNSUPPORTED = 7  /* option combination not provided */
 };
@@ -138,6 +140,14 @@ typedef struct {
 /* Create a context on CUDA device `device` issuing work on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  0 on success. */
 int ef_ctx_create(int device, void *stream, ef_ctx **out);
+/* Cap the device memory the context may hold for its working buffers
+ * (scratch, f tables, staging copies, batch offsets, learned-path and SIR
+ * buffers; models are separate), in bytes; 0 = no cap (the default).  A call
+ * that would need more returns EF_ERR_OOM with a message naming both sizes,
+ * before it frees or allocates anything, and leaves the context usable (a
+ * later call with a higher cap, or on a smaller graph, runs normally).
+ * Lowering the cap frees nothing already held. */
+int ef_ctx_set_memory_limit(ef_ctx *ctx, uint64_t bytes);
 /* Free the context and its scratch.  Safe on NULL. */
 int ef_ctx_destroy(ef_ctx *ctx);
 /* Message of the last failure on this context ("" if none); ctx may be
@@ -445,8 +455,14 @@ int ef_surrogate_rank(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const 
  * would exceed it (about 172 n + 44 m + 48 min(n, m) bytes) are rejected with
  * EF_ERR_ARG and a message naming the limit; nothing runs on the GPU then.
  * The first call on a device looks up the array's address (make it before
- * any stream capture).  All calls share the array: calls that overlap on the
- * GPU race and must be serialised by the caller.  Errors: ef_last_error(NULL).
+ * any stream capture).  Under CUDA's lazy module loading that first call is
+ * also when the device's 32 MiB are reserved, so make it before a memory pool
+ * takes the device; a call with n = 0 does only this set-up (a failure to
+ * reserve gives EF_ERR_OOM).  The address is cached until the process exits:
+ * it is not valid across a cudaDeviceReset of the device.  All calls share
+ * the array, which keeps the previous call's contents (each call clears what
+ * must start at zero): calls that overlap on the GPU race and must be
+ * serialised by the caller.  Errors: ef_last_error(NULL).
  */
 int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t precision,
                       double *out_ef, void *stream);

@@ -16,6 +16,10 @@ definition:
   matrix products;
 * ``adam``       -- one Adam step (Kingma and Ba, "Adam: a method for
   stochastic optimization", Algorithm 1);
+* ``bf16`` and ``operands="bf16"`` of ``forward`` / ``loss_and_grads`` --
+  the same network with the operands of every matrix product rounded to
+  BF16 (the network's stated precision: BF16 operands, sums kept wide),
+  and ``grad_term_sums``, the size of the terms each gradient element sums;
 * ``spearman`` and ``topk_recall`` -- the quality measures.
 
 Parameters are a dict of float64 arrays: W1 (16, 64), b1 (64), W2 (64, 64),
@@ -119,33 +123,94 @@ def standardize(p: dict, X) -> np.ndarray:
     return (np.asarray(X, dtype=np.float64) - p["mean"]) / p["std"]
 
 
-def forward(p: dict, X) -> tuple[np.ndarray, dict]:
-    """Prediction for each row of X (raw features) and the activations."""
+def bf16(a) -> np.ndarray:
+    """Round to the nearest BF16 value, ties to even, returned as float64.
+
+    BF16 keeps the sign, the 8-bit exponent and the 7 leading stored
+    significand bits of an IEEE binary32 number.  In binary64 that is the
+    top 8 bits of the 53-bit significand, so the rounding drops the low 45
+    stored bits (normal values; the network's values stay far from BF16's
+    range limits).
+    """
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    u = a.view(np.uint64)
+    low = np.uint64((1 << 45) - 1)
+    odd = (u >> np.uint64(45)) & np.uint64(1)
+    r = (u + (low >> np.uint64(1)) + odd) & ~low
+    return r.view(np.float64)
+
+
+def _op(a, operands):
+    return bf16(a) if operands == "bf16" else a
+
+
+def forward(p: dict, X, operands: str = "fp64") -> tuple[np.ndarray, dict]:
+    """Prediction for each row of X (raw features) and the activations.
+
+    operands="bf16" rounds both operands of the two hidden-layer matrix
+    products to BF16 (standardised features, hidden activations, weights);
+    sums, biases, ReLU and the output layer stay in FP64.
+    """
     Z = standardize(p, X)
-    A1 = Z @ p["W1"] + p["b1"]
+    A1 = _op(Z, operands) @ _op(p["W1"], operands) + p["b1"]
     H1 = np.maximum(A1, 0.0)
-    A2 = H1 @ p["W2"] + p["b2"]
+    A2 = _op(H1, operands) @ _op(p["W2"], operands) + p["b2"]
     H2 = np.maximum(A2, 0.0)
     out = H2 @ p["w3"] + p["b3"]
     return out, dict(Z=Z, A1=A1, H1=H1, A2=A2, H2=H2)
 
 
-def loss_and_grads(p: dict, X, y) -> tuple[float, dict]:
-    """L = mean over rows of (prediction - y)^2 and its gradient (chain rule)."""
+def loss_and_grads(p: dict, X, y, operands: str = "fp64") -> tuple[float, dict]:
+    """L = mean over rows of (prediction - y)^2 and its gradient (chain rule).
+
+    operands="bf16" also rounds to BF16 the operands of the backward matrix
+    products: the layer-2 errors and W2 for the layer-1 errors, and the
+    activations and errors whose products form the weight gradients of W1
+    and W2.  Bias gradients and the output layer's stay in FP64.
+    """
     y = np.asarray(y, dtype=np.float64)
-    out, a = forward(p, X)
+    out, a = forward(p, X, operands)
     B = out.shape[0]
     r = out - y
     L = float(np.mean(r * r))
     d_out = 2.0 * r / B
     g = {"b3": float(d_out.sum()), "w3": a["H2"].T @ d_out}
     d_A2 = np.outer(d_out, p["w3"]) * (a["A2"] > 0)
-    g["W2"] = a["H1"].T @ d_A2
+    g["W2"] = _op(a["H1"], operands).T @ _op(d_A2, operands)
     g["b2"] = d_A2.sum(axis=0)
-    d_A1 = (d_A2 @ p["W2"].T) * (a["A1"] > 0)
-    g["W1"] = a["Z"].T @ d_A1
+    d_A1 = (_op(d_A2, operands) @ _op(p["W2"], operands).T) * (a["A1"] > 0)
+    g["W1"] = _op(a["Z"], operands).T @ _op(d_A1, operands)
     g["b1"] = d_A1.sum(axis=0)
     return L, g
+
+
+def grad_term_sums(p: dict, X, y, operands: str = "fp64") -> tuple[dict, dict]:
+    """For every gradient element, the sum and the largest of the absolute
+    values of the per-row terms it adds up (same products as
+    ``loss_and_grads``): the scale against which rounding in those terms is
+    measured.  Returns (sums, maxima), keyed like the gradient."""
+    y = np.asarray(y, dtype=np.float64)
+    out, a = forward(p, X, operands)
+    B = out.shape[0]
+    d_out = 2.0 * (out - y) / B
+    d_A2 = np.outer(d_out, p["w3"]) * (a["A2"] > 0)
+    d_A1 = (_op(d_A2, operands) @ _op(p["W2"], operands).T) * (a["A1"] > 0)
+    pairs = {"w3": (a["H2"], d_out[:, None]), "b3": (np.ones((B, 1)), d_out[:, None]),
+             "W2": (_op(a["H1"], operands), _op(d_A2, operands)), "b2": (np.ones((B, 1)), d_A2),
+             "W1": (_op(a["Z"], operands), _op(d_A1, operands)), "b1": (np.ones((B, 1)), d_A1)}
+    sums, maxima = {}, {}
+    for k, (u, v) in pairs.items():
+        au, av = np.abs(u), np.abs(v)
+        s = au.T @ av
+        mx = np.max(au[:, :, None] * av[:, None, :], axis=0)
+        if k in ("w3",):
+            s, mx = s[:, 0], mx[:, 0]
+        elif k in ("b3",):
+            s, mx = float(s[0, 0]), float(mx[0, 0])
+        elif k in ("b1", "b2"):
+            s, mx = s[0], mx[0]
+        sums[k], maxima[k] = s, mx
+    return sums, maxima
 
 
 def adam(p: dict, g: dict, m: dict, v: dict, step: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8) -> None:

@@ -24,7 +24,7 @@ EF_PREC_FP64, EF_PREC_FP32C = 0, 1
 PRECISIONS = {"fp64": EF_PREC_FP64, "fp32c": EF_PREC_FP32C}
 
 # Every symbol include/ef.h declares (checked by the CPU test of the ABI).
-EXPORTED = ("ef_ctx_create", "ef_ctx_destroy", "ef_last_error", "ef_sync", "ef_get_stats",
+EXPORTED = ("ef_ctx_create", "ef_ctx_set_memory_limit", "ef_ctx_destroy", "ef_last_error", "ef_sync", "ef_get_stats",
             "ef_compute", "ef_compute_ex", "ef_compute_batched", "ef_get_tuning", "ef_set_tuning", "ef_autotune",
             "ef_compute_nodes", "ef_features", "ef_model_create", "ef_model_destroy", "ef_model_get", "ef_model_set",
             "ef_model_feature_mode", "ef_model_save", "ef_model_load", "ef_mlp_forward", "ef_mlp_grad",
@@ -131,6 +131,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     lib.ef_ctx_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
     lib.ef_ctx_destroy.argtypes = [vp]
+    lib.ef_ctx_set_memory_limit.argtypes = [vp, ctypes.c_uint64]
     lib.ef_last_error.argtypes = [vp]
     lib.ef_last_error.restype = ctypes.c_char_p
     lib.ef_sync.argtypes = [vp]
@@ -197,6 +198,11 @@ def ef_ctx_create(device: int = 0, stream: int | None = None) -> int:
     h = ctypes.c_void_p()
     _check(load_library().ef_ctx_create(device, stream or None, ctypes.byref(h)))
     return h.value
+
+
+def ef_ctx_set_memory_limit(ctx: int, nbytes: int) -> None:
+    """Cap the device bytes the context's working buffers may hold (0 = no cap)."""
+    _check(load_library().ef_ctx_set_memory_limit(ctx, int(nbytes)), ctx)
 
 
 def ef_ctx_destroy(ctx: int) -> None:
@@ -563,6 +569,9 @@ class Context:
 
     def stats(self, reset: bool = False) -> dict:
         return ef_get_stats(self.handle, reset)
+
+    def set_memory_limit(self, nbytes: int) -> None:
+        ef_ctx_set_memory_limit(self.handle, nbytes)
 
     def sir(self, row_ptr, col_idx, index_cases, *, outputs=("final_size", "length", "peak_infected", "peak_step"),
             depth: int = 4, **kw) -> dict:

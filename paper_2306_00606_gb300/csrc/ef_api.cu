@@ -77,6 +77,7 @@ struct ef_ctx {
     bool bins = true;                // out-lists of the current graph in degree-bin order (bin_layout)
     void *sir = nullptr;             // SIR simulation state
     size_t sir_bytes = 0;
+    uint64_t mem_limit = 0;          // cap on the working buffers (0: none)
 };
 
 struct ef_model {
@@ -136,8 +137,25 @@ void drop_graph(ef_ctx *ctx) {
     memset(&ctx->gkey, 0, sizeof ctx->gkey);
 }
 
+// Device bytes held in the context's working buffers.
+uint64_t held_bytes(const ef_ctx *ctx) {
+    return (uint64_t)ctx->scratch_bytes + (uint64_t)ctx->ftab_cap * 2 * sizeof(double) + ctx->io_bytes +
+           ctx->goff_bytes + ctx->rank_bytes + ctx->acts_bytes + ctx->sir_bytes + (ctx->dtmp ? 64 * sizeof(double) : 0);
+}
+
 int ensure_buffer(ef_ctx *ctx, void **buf, size_t *have, size_t need, size_t slack) {
     if (*have >= need) return EF_OK;
+    if (ctx->mem_limit) {
+        // the buffer grows to need + slack, or to need alone when only that fits
+        const uint64_t rest = held_bytes(ctx) - *have;
+        if (rest + need > ctx->mem_limit) {
+            set_err(ctx, "a buffer of %llu bytes would take the context to %llu bytes, above its memory limit "
+                         "of %llu bytes", (unsigned long long)need, (unsigned long long)(rest + need),
+                    (unsigned long long)ctx->mem_limit);
+            return EF_ERR_OOM;
+        }
+        if (rest + need + slack > ctx->mem_limit) slack = 0;
+    }
     if (*buf) {
         drop_graph(ctx);   // it may refer to the old buffer
         CU(cudaStreamSynchronize(ctx->stream));
@@ -693,6 +711,12 @@ int ef_ctx_create(int device, void *stream, ef_ctx **out) {
         return e == cudaErrorMemoryAllocation ? EF_ERR_OOM : EF_ERR_CUDA;
     }
     *out = ctx;
+    return EF_OK;
+}
+
+int ef_ctx_set_memory_limit(ef_ctx *ctx, uint64_t bytes) {
+    if (!ctx) { set_err(nullptr, "null context"); return EF_ERR_ARG; }
+    ctx->mem_limit = bytes;
     return EF_OK;
 }
 

@@ -11,10 +11,15 @@
 //
 // Set-up: the first call on a device looks up the array's device address with
 // cudaGetSymbolAddress (with that device current) and caches it; make that
-// first call before any stream capture.  Afterwards a call only launches
-// kernels, memsets and one small device-to-host copy of the validation word
-// into a stack variable.  It calls no cudaMalloc, cudaFree, cudaMallocHost or
-// any other allocating routine.
+// first call before any stream capture.  With CUDA's lazy module loading this
+// lookup is also when the driver loads the module holding the array and
+// reserves its 32 MiB on the device, so make the first call before a memory
+// pool takes the rest of the device (a call with n = 0 does the set-up and
+// nothing else).  The cached address stays valid until the device's context
+// is destroyed (cudaDeviceReset); do not call this after a reset.
+// Afterwards a call only launches kernels, memsets and one small
+// device-to-host copy of the validation word into a stack variable.  It calls
+// no cudaMalloc, cudaFree, cudaMallocHost or any other allocating routine.
 //
 // All calls share the one array and it keeps the previous call's contents;
 // everything that must start at zero is cleared by each call.  Two calls
@@ -54,6 +59,27 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
     if (n < 0 || m < 0 || m >= ((int64_t)1 << 31)) return fail(EF_ERR_ARG, "ef_compute_static: bad sizes");
     if (precision != EF_PREC_FP64 && precision != EF_PREC_FP32C)
         return fail(EF_ERR_ARG, "ef_compute_static: bad precision");
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return fail(EF_ERR_CUDA, "ef_compute_static: no current CUDA device");
+    void *base;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_addr[dev]) {
+            cudaError_t e = cudaGetSymbolAddress(&g_static_addr[dev], g_static_scratch);
+            if (e != cudaSuccess) {
+                g_static_addr[dev] = nullptr;
+                cudaGetLastError();
+                return fail(e == cudaErrorMemoryAllocation ? EF_ERR_OOM : EF_ERR_CUDA,
+                            e == cudaErrorMemoryAllocation
+                                ? "ef_compute_static: no device memory left for the fixed scratch array "
+                                  "(make the first call before a memory pool takes the device)"
+                                : "ef_compute_static: cudaGetSymbolAddress failed");
+            }
+        }
+        base = g_static_addr[dev];
+    }
     if (n == 0) return EF_OK;
     if (!g->row_ptr || (m > 0 && !g->col_idx)) return fail(EF_ERR_ARG, "ef_compute_static: null CSR array");
 
@@ -71,21 +97,6 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
         return fail(EF_ERR_ARG, msg);
     }
 
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-        return fail(EF_ERR_CUDA, "ef_compute_static: no current CUDA device");
-    void *base;
-    {
-        std::lock_guard<std::mutex> lk(g_static_mu);
-        if (!g_static_addr[dev]) {
-            cudaError_t e = cudaGetSymbolAddress(&g_static_addr[dev], g_static_scratch);
-            if (e != cudaSuccess) {
-                g_static_addr[dev] = nullptr;
-                return fail(EF_ERR_CUDA, "ef_compute_static: cudaGetSymbolAddress failed");
-            }
-        }
-        base = g_static_addr[dev];
-    }
     s.ftab = (double *)((char *)base + carve_scratch((char *)base, n, m, s));
     s.tq = reinterpret_cast<int64_t *>(s.ftab + fcap);
     Tune t;

@@ -515,25 +515,38 @@ static size_t hub_smem_bytes() {
     return HUB_HIST * sizeof(int32_t) + HUB_SMEM_K * (sizeof(typename E::Cls) + sizeof(typename E::R));
 }
 
-// Resident blocks per SM of the class kernels ([F64][mid, hub]): their grids
-// hold exactly one wave, and their warps take work from atomic counters.
-static int g_class_blocks[2][2] = {{1, 1}, {1, 1}};
+// Per device (kept per device id, so that a process using several devices
+// of different kinds sizes each one's grids from its own properties):
+// resident blocks per SM of the class kernels ([F64][mid, hub]), whose grids
+// hold exactly one wave while their warps take work from atomic counters,
+// and the L2 size.
+constexpr int MAX_DEVICES = 64;
+struct DeviceProps {
+    int class_blocks[2][2] = {{1, 1}, {1, 1}};
+    int64_t l2_bytes = 0;
+};
+static DeviceProps g_dev_props[MAX_DEVICES];
+
+static DeviceProps &dev_props() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) dev = 0;
+    return g_dev_props[dev];
+}
 
 template <bool F64>
-static int class_occupancy() {
+static int class_occupancy(DeviceProps &p) {
     int mid = 0, hub = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mid, k_wedge_mid<F64>, MID_WARPS * 32, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&hub, k_wedge_hub<F64>, HUB_THREADS, hub_smem_bytes<F64>()) !=
             cudaSuccess)
         return -1;
-    g_class_blocks[F64][0] = mid > 0 ? mid : 1;
-    g_class_blocks[F64][1] = hub > 0 ? hub : 1;
+    p.class_blocks[F64][0] = mid > 0 ? mid : 1;
+    p.class_blocks[F64][1] = hub > 0 ? hub : 1;
     return 0;
 }
 
 // L2 size of the current device (read by prepare_kernels).
-static int64_t g_l2_bytes = 0;
-int64_t device_l2_bytes() { return g_l2_bytes; }
+int64_t device_l2_bytes() { return dev_props().l2_bytes; }
 
 // Opt the hub kernels in to their dynamic shared memory on the current device,
 // size the class kernels' grids and read the L2 size (once per context,
@@ -544,11 +557,13 @@ int prepare_kernels() {
         cudaFuncSetAttribute(k_wedge_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)hub_smem_bytes<false>()) != cudaSuccess)
         return -1;
-    if (class_occupancy<true>() || class_occupancy<false>()) return -1;
     int dev = 0, l2 = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES ||
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
         return -1;
-    g_l2_bytes = l2;
+    DeviceProps &p = g_dev_props[dev];
+    if (class_occupancy<true>(p) || class_occupancy<false>(p)) return -1;
+    p.l2_bytes = l2;
     return 0;
 }
 
@@ -556,10 +571,11 @@ template <bool F64>
 static int big_classes(const int32_t *rp, const int32_t *ci, const Scratch &s, int32_t n, int num_sms,
                        cudaStream_t st) {
     const int32_t *mid = s.bins + (size_t)BIN_MID * n;
-    k_wedge_mid<F64><<<(unsigned)(num_sms * g_class_blocks[F64][0]), MID_WARPS * 32, 0, st>>>(
+    const DeviceProps &p = dev_props();
+    k_wedge_mid<F64><<<(unsigned)(num_sms * p.class_blocks[F64][0]), MID_WARPS * 32, 0, st>>>(
         rp, ci, s.D, mid, s.counters, s.ftab, s.Tacc, s.Ccenter);
     const size_t smem = hub_smem_bytes<F64>();
-    k_wedge_hub<F64><<<(unsigned)(num_sms * g_class_blocks[F64][1]), HUB_THREADS, smem, st>>>(
+    k_wedge_hub<F64><<<(unsigned)(num_sms * p.class_blocks[F64][1]), HUB_THREADS, smem, st>>>(
         rp, ci, s.D, s.bins, n, s.counters, s.ftab, s.Tacc, s.Ccenter, s.hub_cidx, s.hub_cls, s.hub_q);
     return 0;
 }

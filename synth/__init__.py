@@ -234,9 +234,14 @@ def disjoint_union(gs) -> Graph:
 # The five workloads: (1) ER G(2000, 0.004); (2) BA n=1e6, m=5; (3) power-law
 # configuration model n=4e6, gamma=2.3, degrees in [3, 20000]; (4) 4096 WS
 # graphs, n in [200, 20000], k even in [4, 12], p=0.1; (5) BA n=1.6e7, m=4.
+# "3b" is workload 3 with minimum degree 6: about 4.4e7 undirected edges
+# (8.7e7 CSR entries), the 44M-edge graph read as undirected edges.
 
-def workload(idx: int, scale: float = 1.0) -> Graph:
-    """Standard workload `idx` (1..5); `scale` < 1 shrinks node counts for tests."""
+def workload(idx, scale: float = 1.0) -> Graph:
+    """Standard workload `idx` (1..5, or "3b"); `scale` < 1 shrinks node counts for tests."""
+    if idx == "3b":
+        return powerlaw_cm(max(10, int(4_000_000 * scale)), 2.3, 6, 20000 if scale >= 1 else
+                           max(7, int(20000 * scale ** 0.5)), SEED_BASE + 6)
     seed = SEED_BASE + idx
     if idx == 1:
         return erdos_renyi(max(3, int(2000 * scale)), 0.004, seed)

@@ -5,10 +5,16 @@
 - exact EF of chosen nodes: N, S and t exactly, EF within the parity bars,
   against the vertex-centric oracle;
 - the network: forward pass and gradients (BF16 operands, FP32
-  accumulation) against the FP64 oracle.  The bars come from BF16's 8-bit
-  significand: relative error per product about 2^-9, so a few 1e-3 on a
-  64-term sum, and 3e-2 relative on the gradient of each weight block,
-  far below the O(1) error of a transposed or misplaced operand;
+  accumulation), element by element:
+  * on a network and inputs of few-bit dyadic values, where every operand is
+    a BF16 number and every sum is exact in FP32, the GPU must equal the
+    FP64 oracle exactly (any transposed, misplaced or dropped term shows);
+  * on realistic features, against the oracle with the same BF16 operand
+    rounding: each gradient element within 2^-6 of the absolute sum of its
+    own terms (one BF16 step on every operand, and the FP32 sums), rows
+    whose ReLU masks FP32 sums could decide differently allowed their full
+    terms; each prediction within 2^-7 of the absolute sum it is made of;
+    and against the unrounded FP64 oracle block by block;
 - training lowers the loss, and save/load round-trips;
 - ranking: the trained network's top set reaches 0.95 recall of the exact
   top 1% while computing exact EF for a few percent of the nodes, and it
@@ -22,6 +28,7 @@ import pytest
 import oracle
 import synth
 from oracle import surrogate as sg
+from netcases import dyadic_network
 
 pytestmark = pytest.mark.gpu
 
@@ -120,6 +127,78 @@ def test_network_forward_matches_oracle(ctx):
     ref, _ = sg.forward(p, X)
     scale = np.abs(ref).mean() + np.abs(ref).std()
     assert np.abs(got - ref).max() <= 2e-2 * scale, (np.abs(got - ref).max(), scale)
+    # element by element against the oracle with the same BF16 operands: a
+    # rounding that FP32 sums decide the other way moves one operand by one
+    # BF16 step (at most 2^-7 of it), so a prediction stays within 2^-7 of
+    # the absolute sum it is made of
+    ref16, a = sg.forward(p, X, operands="bf16")
+    err = np.abs(got - ref16)
+    tol = 2.0 ** -7 * _abs_forward(p, a)
+    assert np.all(err <= tol), (int(np.argmax(err / tol)), float(np.max(err / tol)))
+
+
+def test_network_exact_on_dyadic_values(ctx):
+    import torch
+    import paper_2306_00606_gb300 as ef
+    rows = 64   # four 16-row tiles; 1/batch is a power of two
+    p, X, y = dyadic_network(7, rows)
+    m = ef.Model(ctx.handle)
+    m.set(np.concatenate([sg.flatten(p), p["mean"], p["std"]]).astype(np.float32))
+    assert np.array_equal(m.get().astype(np.float64), np.concatenate([sg.flatten(p), p["mean"], p["std"]]))
+    x = _dev(X.astype(np.float32))
+    out = torch.empty(rows, dtype=torch.float32, device="cuda")
+    m.forward(x, out)
+    ref, _ = sg.forward(p, X)
+    np.testing.assert_array_equal(out.cpu().numpy().astype(np.float64), ref)
+    loss, grad = m.grad(x, _dev(y.astype(np.float32)))
+    ref_loss, ref_g = sg.loss_and_grads(p, X, y)
+    assert loss == ref_loss
+    gf = sg.flatten(ref_g)
+    o = 0
+    for k in sg.TRAINED:
+        size = int(np.prod(sg.SHAPES[k]))
+        a, b = grad[o:o + size].astype(np.float64), gf[o:o + size]
+        assert np.count_nonzero(b) > size // 4, k   # the check covers mostly non-zero elements
+        np.testing.assert_array_equal(a, b, err_msg=k)
+        o += size
+
+
+def _abs_forward(p, a):
+    """Per row, the absolute sum the prediction is made of, propagated through both layers."""
+    z = sg.bf16(a["Z"])
+    h1 = np.abs(z) @ np.abs(sg.bf16(p["W1"])) + np.abs(p["b1"])
+    h2 = h1 @ np.abs(sg.bf16(p["W2"])) + np.abs(p["b2"])
+    return h2 @ np.abs(p["w3"]) + abs(p["b3"])
+
+
+def _near_midpoint(v, window):
+    """Values within `window` of a BF16 rounding midpoint (the FP32 value the
+    GPU rounds may lie on the other side of it)."""
+    v = np.asarray(v, dtype=np.float64)
+    r = sg.bf16(v)
+    _, e = np.frexp(r)
+    step = np.ldexp(1.0, e - 8)   # BF16 spacing above |r| (8 significant bits)
+    d = np.minimum(np.abs(np.abs(v) - (np.abs(r) + step / 2)), np.abs(np.abs(v) - (np.abs(r) - step / 4)))
+    d = np.minimum(d, np.abs(np.abs(v) - (np.abs(r) - step / 2)))
+    return (d <= window) & (v != 0)
+
+
+def _mask_unsure_rows(p, a):
+    """Rows with a ReLU pre-activation closer to 0 than the GPU's FP32 sums
+    and its BF16 roundings could move it: 2^-18 of the pre-activation's
+    absolute sum, plus one BF16 step (2^-7) of every operand whose rounding
+    could go either way."""
+    z, w1, w2 = a["Z"], sg.bf16(p["W1"]), sg.bf16(p["W2"])
+    zb = sg.bf16(z)
+    s1 = np.abs(zb) @ np.abs(w1) + np.abs(p["b1"])
+    zc = _near_midpoint(z, 2.0 ** -20 * np.abs(z))
+    d1 = 2.0 ** -7 * (np.abs(zb) * zc) @ np.abs(w1) + 2.0 ** -18 * s1
+    h1 = a["H1"]
+    h1b = sg.bf16(h1)
+    s2 = np.abs(h1b) @ np.abs(w2) + np.abs(p["b2"])
+    hc = _near_midpoint(h1, d1)
+    d2 = 2.0 ** -7 * (np.abs(h1b) * hc) @ np.abs(w2) + d1 @ np.abs(w2) + 2.0 ** -18 * s2
+    return np.any(np.abs(a["A1"]) <= d1, axis=1) | np.any(np.abs(a["A2"]) <= d2, axis=1)
 
 
 def test_network_gradients_match_oracle(ctx):
@@ -139,6 +218,40 @@ def test_network_gradients_match_oracle(ctx):
         err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
         assert err <= 3e-2, (k, err)
         o += size
+    # element by element against the oracle with the same BF16 operands: each
+    # element within 2^-6 of the absolute sum of its own terms (every term's
+    # operands one BF16 step away, and the FP32 sums); rows whose ReLU masks
+    # the GPU could decide differently may change their terms completely
+    _, g16 = sg.loss_and_grads(p, X, y, operands="bf16")
+    out, a = sg.forward(p, X, operands="bf16")
+    unsure = _mask_unsure_rows(p, a)
+    assert unsure.sum() <= 0.05 * len(y), unsure.sum()
+    sums, _ = sg.grad_term_sums(p, X, y, operands="bf16")
+    au = {k: v[unsure] for k, v in a.items()}
+    d_abs = np.abs(2.0 * (out - y) / len(y))[unsure]
+    open_sums = _open_term_sums(p, au, d_abs * 1.01)
+    o = 0
+    for k in sg.TRAINED:
+        size = int(np.prod(sg.SHAPES[k]))
+        a_k = grad[o:o + size].astype(np.float64)
+        b_k = np.ravel(g16[k])
+        tol = 2.0 ** -6 * np.ravel(sums[k]) + 2.0 * np.ravel(open_sums[k]) + 1e-12
+        ratio = np.abs(a_k - b_k) / tol
+        assert np.all(ratio <= 1.0), (k, int(np.sum(ratio > 1)), float(ratio.max()))
+        o += size
+
+
+def _open_term_sums(p, a, d_abs):
+    """Absolute term sums of the rows in `a`, with every ReLU mask open and
+    |dL/dprediction| = d_abs: a bound on what those rows add to each
+    gradient element, whichever way their masks go."""
+    z = np.abs(sg.bf16(a["Z"]))
+    h1 = np.abs(sg.bf16(a["H1"]))
+    h2 = np.abs(a["H2"])
+    e2 = np.outer(d_abs, np.abs(p["w3"]))
+    e1 = np.abs(sg.bf16(e2)) @ np.abs(sg.bf16(p["W2"])).T
+    return {"W1": z.T @ np.abs(sg.bf16(e1)), "b1": e1.sum(axis=0), "W2": h1.T @ np.abs(sg.bf16(e2)),
+            "b2": e2.sum(axis=0), "w3": h2.T @ d_abs, "b3": float(d_abs.sum())}
 
 
 def _training_set(ctx):

@@ -8,7 +8,11 @@ None of these compares the oracle with itself:
 - the forward pass in its linear regime against one composed affine map;
 - Adam's first step against its closed form;
 - Spearman's rho against SciPy;
-- recall on hand-made cases.
+- recall on hand-made cases;
+- BF16 rounding against PyTorch's float32 -> bfloat16 conversion and hand
+  ties; the BF16-operand network against the FP64 one on a network whose
+  operands are all BF16 numbers with exact sums (they must agree exactly);
+- the gradient term sums against |gradient| where every term is >= 0.
 """
 import math
 
@@ -18,6 +22,7 @@ import pytest
 import oracle
 import synth
 from oracle import surrogate as sg
+from netcases import dyadic_network
 
 
 def test_feature_count_and_names():
@@ -138,3 +143,60 @@ def test_topk_recall_hand_cases():
     pred[1] = -10   # the second-best node is predicted worst
     assert sg.topk_recall(pred, exact, 0.2) == 0.5
     assert list(sg.top_set(np.zeros(5), 0.4)) == [0, 1]   # ties go to the smaller index
+
+
+def test_bf16_rounding_matches_torch_and_hand_ties():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.normal(size=20000) * 10.0 ** rng.integers(-6, 6, size=20000),
+                        [1.0, -1.0, 0.0, 3.0, 1e-3]]).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(sg.bf16(x.astype(np.float64)), ref)
+    # 8 significant bits: 1 + 2^-8 is halfway between 1 and 1 + 2^-7 (ties to
+    # the even 1); 1 + 3 * 2^-8 is halfway between 1 + 2^-7 and 1 + 2^-6
+    # (ties to the even 1 + 2^-6); anything above a midpoint rounds up; 96.5
+    # has 8 significant bits, 96.25 and 96.75 are ties (to 96 and 97)
+    hand = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -8 + 2.0 ** -30, -(1 + 2.0 ** -7), 96.5,
+                     96.25, 96.75])
+    np.testing.assert_array_equal(sg.bf16(hand), [1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7, -(1 + 2.0 ** -7), 96.5,
+                                                  96.0, 97.0])
+
+
+@pytest.mark.parametrize("seed", [7, 8])
+def test_bf16_network_equals_fp64_when_operands_are_bf16_exact(seed):
+    p, X, y = dyadic_network(seed, 64)
+    for k in ("W1", "W2"):
+        assert np.array_equal(sg.bf16(p[k]), p[k])
+    out64, a64 = sg.forward(p, X)
+    out16, a16 = sg.forward(p, X, operands="bf16")
+    np.testing.assert_array_equal(out16, out64)
+    L64, g64 = sg.loss_and_grads(p, X, y)
+    L16, g16 = sg.loss_and_grads(p, X, y, operands="bf16")
+    assert L16 == L64
+    np.testing.assert_array_equal(sg.flatten(g16), sg.flatten(g64))
+    # and the bf16 mode does round: on generic values it differs from FP64
+    q, Xq, yq = _data(seed)
+    assert not np.array_equal(sg.forward(q, Xq, operands="bf16")[0], sg.forward(q, Xq)[0])
+
+
+def test_grad_term_sums_equal_gradient_when_terms_are_nonnegative():
+    rng = np.random.default_rng(12)
+    p = sg.init_params(12)
+    for k in ("W1", "W2", "w3"):
+        p[k] = np.abs(p[k])
+    p["b1"] = np.full(64, 0.1)
+    p["b2"] = np.full(64, 0.1)
+    X = np.abs(rng.normal(size=(30, 16)))     # mean 0, std 1: every activation > 0
+    out, _ = sg.forward(p, X)
+    y = out - rng.uniform(0.5, 1.0, size=30)   # every error > 0: every term >= 0
+    _, g = sg.loss_and_grads(p, X, y)
+    sums, maxima = sg.grad_term_sums(p, X, y)
+    for k in sg.TRAINED:
+        np.testing.assert_allclose(np.ravel(sums[k]), np.ravel(np.abs(g[k])), rtol=1e-12)
+        assert np.all(np.ravel(maxima[k]) <= np.ravel(sums[k]) * (1 + 1e-12))
+    # with mixed signs the sums bound the gradient
+    q, Xq, yq = _data(2)
+    _, gq = sg.loss_and_grads(q, Xq, yq)
+    sq, _ = sg.grad_term_sums(q, Xq, yq)
+    for k in sg.TRAINED:
+        assert np.all(np.abs(np.ravel(gq[k])) <= np.ravel(sq[k]) * (1 + 1e-12))

@@ -5,8 +5,11 @@ forbid cudaMalloc/cudaFree, or loops that must not touch an allocator, get EF
 from a fixed scratch array inside the library.  These tests call it through
 the C ABI and check it against ef_compute_ex on two calls in a row (the array
 keeps the previous call's contents, so the second call shows that everything
-that must start at zero is cleared), and that an oversized graph is refused
-before any GPU work.  This file is collected last on purpose.
+that must start at zero is cleared), that once a first call has set it up
+(a call with n = 0 does that and nothing else) further calls leave the
+device's free memory unchanged, also on a stream of the caller's, and that an
+oversized graph is refused before any GPU work.  This file is collected last
+on purpose.
 """
 import ctypes
 
@@ -18,9 +21,10 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def _static(lib, ef_mod, rp, ci, out, precision):
+def _static(lib, ef_mod, rp, ci, out, precision, stream=None):
     g = ef_mod.ef_csr(rp.data_ptr(), ci.data_ptr())
-    return lib.ef_compute_static(ctypes.byref(g), rp.shape[0] - 1, ci.shape[0], precision, out.data_ptr(), None)
+    return lib.ef_compute_static(ctypes.byref(g), rp.shape[0] - 1, ci.shape[0], precision, out.data_ptr(),
+                                 ctypes.c_void_p(stream) if stream else None)
 
 
 def test_static_entry_matches_ef_compute_ex_twice():
@@ -54,3 +58,31 @@ def test_static_entry_rejects_oversized_graph():
     rc = _static(lib, ef, rp, ci, out, 0)
     assert rc == ef.EF_ERR_ARG
     assert "maximum" in ef.ef_last_error(None)
+
+
+def test_static_entry_leaves_free_memory_unchanged_on_a_side_stream():
+    import torch
+    import paper_2306_00606_gb300 as ef
+    lib = ef.load_library()
+    # set-up only: an empty graph (the array's address, and with lazy module
+    # loading its reservation on the device)
+    z = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert _static(lib, ef, z, z[:0], torch.empty(1, dtype=torch.float64, device="cuda"), 0) == ef.EF_OK
+    g = synth.barabasi_albert(20000, 5, 33)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    with ef.Context(0) as ctx:
+        ref = ctx.compute(rp, ci, precision="fp64")["ef"].cpu().numpy()
+    side = torch.cuda.Stream()
+    outs = [torch.full((g.n,), -1.0, dtype=torch.float64, device="cuda") for _ in range(3)]
+    # one call first, so that the driver has loaded every kernel this entry point launches
+    assert _static(lib, ef, rp, ci, outs[0], 0, side.cuda_stream) == ef.EF_OK, ef.ef_last_error(None)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for out in outs[1:]:
+        assert _static(lib, ef, rp, ci, out, 0, side.cuda_stream) == ef.EF_OK, ef.ef_last_error(None)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    for out in outs:
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-9, atol=1e-12)
