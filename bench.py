@@ -566,8 +566,8 @@ def run_reference(args):
     """The oracle as the reference arm: each step times the oracle on one
     bounded random node sample of the workload (oracle_steps: the samples of
     seeds 0, 1, ... are the ones `cpu_baseline` times in the GPU arm), about
-    cpu_seconds / 3 per step, shortened so that warm-up and steps stay
-    within about 150 s."""
+    cpu_seconds / 3 per step, shortened so that the steps stay within about
+    150 s (warm-up samples take at most 0.5 s each)."""
     rank, world, local = dist_env()
     if rank != 0:
         return 0
@@ -575,8 +575,8 @@ def run_reference(args):
     g = synth.workload(idx)
     st = graph_stats(g)
     batched = args.workload in BATCHED
-    per_step = min(args.cpu_seconds / 3, 150.0 / max(args.steps + args.warmup, 1))
-    for _ in oracle_steps(g, args.warmup, per_step, seed0=1000):
+    per_step = min(args.cpu_seconds / 3, 150.0 / max(args.steps, 1))
+    for _ in oracle_steps(g, args.warmup, min(per_step, 0.5), seed0=1000):   # short untimed warm-up samples
         pass
     rows = list(oracle_steps(g, args.steps, per_step, seed0=0))
     clusters = sum(r["clusters"] for r in rows)
@@ -589,7 +589,7 @@ def run_reference(args):
             "cpu_baseline": {"value": v, "unit": "clusters/s", "cores": rows[0]["cores"], "kind": "oracle",
                              "sample": f"each step: uniformly random nodes sized for {per_step:.1f} s by a calibration run, "
                                        f"among those with at most {rows[0]['cap']:.3g} credited clusters (seeds "
-                                       f"0..{args.steps - 1}; {args.warmup} warm-up samples of seeds 1000..), "
+                                       f"0..{args.steps - 1}; {args.warmup} warm-up samples of seeds 1000.., 0.5 s each), "
                                        f"{sum(r['nodes'] for r in rows)} nodes and {clusters:.3g} clusters in "
                                        f"all, {t:.1f} s measured"},
             "e2e": {"value": v, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
