@@ -124,9 +124,7 @@ typedef struct {
     int32_t hub_min;        /* rows and middle nodes of degree >= this take a
                                whole CTA (33..513; 513) */
     int32_t tri_variant;    /* pair-test kernel: 0 two candidates per lane
-                               step, 1 four; 2 and 3 the same with each
-                               warp step's candidates staged in shared
-                               memory (0) */
+                               step, 1 four (0) */
     int32_t grid_per_sm;    /* blocks per SM of the grid-stride row passes
                                (1..256; 64) */
     int32_t layout;         /* order of the oriented out-lists: 1 node order

@@ -351,26 +351,73 @@ def allreduce_partials(parts: dict, group=None) -> None:
         dist.all_reduce(parts[k], op=dist.ReduceOp.SUM, group=group)
 
 
-def compute_sharded(ctx: int, row_ptr, col_idx, rank: int, world: int, *, group=None, precision: str = "fp64",
-                    outputs=("ef",), trust_input: bool = False) -> dict:
-    """EF of every node with the cluster loop split over ``world`` ranks.
+def shard_ranges(node_range, group=None) -> list:
+    """Every rank's node range [lo, hi), from each rank's own (as ef_compute_shard
+    reported it): one all-gather of two integers per rank."""
+    import torch
+    import torch.distributed as dist
+    mine = torch.tensor(list(node_range), dtype=torch.int64)
+    allr = [torch.zeros(2, dtype=torch.int64) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(allr, mine, group=group)
+    return [tuple(int(x) for x in r) for r in allr]
 
-    Each rank holds the whole CSR (device tensors), computes shard ``rank``,
-    takes part in ``allreduce_partials`` (skipped when world == 1) and
-    finalizes; every rank ends with the full outputs.
+
+def reduce_scatter_partials(parts: dict, ranges: list, group=None) -> None:
+    """The exchange by node range: rank r receives, in place in its own
+    ``parts``, the sums over all ranks of the partials of its nodes
+    ranges[r] = [lo, hi) (the other slices of ``parts`` are left undefined).
+    Each node's sums reach only the rank that finalizes it: (R - 1) / R of
+    the 40 bytes per node leave each rank, half of what an all-reduce moves."""
+    import torch.distributed as dist
+    ranks = dist.get_process_group_ranks(group) if group is not None else list(range(dist.get_world_size()))
+    for r, (lo, hi) in enumerate(ranges):
+        if hi <= lo:
+            continue
+        for k in PARTIALS:
+            dist.reduce(parts[k][lo:hi], dst=ranks[r], op=dist.ReduceOp.SUM, group=group)
+
+
+def partials_slice(parts: dict, lo: int, hi: int) -> dict:
+    """The partials of nodes [lo, hi) (views, no copy)."""
+    return {k: v[lo:hi] for k, v in parts.items()}
+
+
+def compute_sharded(ctx: int, row_ptr, col_idx, rank: int, world: int, *, group=None, precision: str = "fp64",
+                    outputs=("ef",), trust_input: bool = False, exchange: str = "allreduce") -> dict:
+    """EF with the cluster loop split over ``world`` ranks.
+
+    Each rank holds the whole CSR (device tensors) and computes shard
+    ``rank``.  exchange="allreduce": ``allreduce_partials`` (skipped when
+    world == 1), then every rank finalizes every node and returns the full
+    outputs.  exchange="reduce_scatter": ``reduce_scatter_partials``, then
+    each rank finalizes only its own node range and returns those outputs
+    (length hi - lo) with the key "range" = (lo, hi).  The exchange runs on
+    the partials' device (the process group's backend must support it).
     """
     import torch
     n = int(row_ptr.shape[0]) - 1
     dev = row_ptr.device
     parts = empty_partials(n, dev)
-    frac, _ = ef_compute_shard(ctx, row_ptr, col_idx, rank, world, parts, precision=precision,
-                               trust_input=trust_input)
-    if world > 1:
-        allreduce_partials(parts, group)
+    frac, rng = ef_compute_shard(ctx, row_ptr, col_idx, rank, world, parts, precision=precision,
+                                 trust_input=trust_input)
     dt = dict(ef=torch.float64, n_clusters=torch.int64, s=torch.int64, t=torch.float64, triangles=torch.int64,
               flag=torch.uint8)
-    res = {k: torch.empty(n, dtype=dt[k], device=dev) for k in outputs}
-    ef_finalize_partials(ctx, parts, frac, precision=precision, **res)
+    if exchange == "allreduce":
+        if world > 1:
+            allreduce_partials(parts, group)
+        res = {k: torch.empty(n, dtype=dt[k], device=dev) for k in outputs}
+        ef_finalize_partials(ctx, parts, frac, precision=precision, **res)
+        return res
+    if exchange != "reduce_scatter":
+        raise ValueError(f"exchange must be 'allreduce' or 'reduce_scatter', not {exchange!r}")
+    ranges = shard_ranges(rng, group) if world > 1 else [rng]
+    if world > 1:
+        reduce_scatter_partials(parts, ranges, group)
+    lo, hi = rng
+    res = {k: torch.empty(hi - lo, dtype=dt[k], device=dev) for k in outputs}
+    if hi > lo:
+        ef_finalize_partials(ctx, partials_slice(parts, lo, hi), frac, precision=precision, **res)
+    res["range"] = (lo, hi)
     return res
 
 

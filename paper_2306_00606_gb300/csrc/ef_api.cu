@@ -427,9 +427,9 @@ int run_job(ef_ctx *ctx, Job j, const ef_outputs *host_out) {
 
 int check_tuning(ef_ctx *ctx, const ef_tuning &t) {
     if (t.row_thread_max < 1 || t.row_thread_max > ef::SMALL_MAX || t.hub_min < ef::SMALL_MAX + 1 ||
-        t.hub_min > ef::MID_MAX + 1 || t.tri_variant < 0 || t.tri_variant > 3 || t.grid_per_sm < 1 ||
+        t.hub_min > ef::MID_MAX + 1 || t.tri_variant < 0 || t.tri_variant > 1 || t.grid_per_sm < 1 ||
         t.grid_per_sm > 256 || t.layout < 0 || t.layout > 2) {
-        set_err(ctx, "tuning out of range: row_thread_max %d (1..%d), hub_min %d (%d..%d), tri_variant %d (0..3), "
+        set_err(ctx, "tuning out of range: row_thread_max %d (1..%d), hub_min %d (%d..%d), tri_variant %d (0..1), "
                      "grid_per_sm %d (1..256), layout %d (0..2)",
                 t.row_thread_max, ef::SMALL_MAX, t.hub_min, ef::SMALL_MAX + 1, ef::MID_MAX + 1, t.tri_variant,
                 t.grid_per_sm, t.layout);
@@ -853,7 +853,7 @@ int ef_autotune(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_opt
         return EF_OK;
     };
     // coordinate descent, two sweeps over the knobs
-    static const int rows[] = {8, 16, 32}, hubs[] = {129, 257, 513}, tris[] = {0, 1, 2, 3}, grids[] = {16, 32, 64, 128},
+    static const int rows[] = {8, 16, 32}, hubs[] = {129, 257, 513}, tris[] = {0, 1}, grids[] = {16, 32, 64, 128},
                      layouts[] = {1, 2};
     ef::Tune cur = ctx->tune;
     double cur_ms;
@@ -862,7 +862,7 @@ int ef_autotune(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_opt
     for (int sweep = 0; sweep < 2; ++sweep) {
         for (int knob = 0; knob < 5; ++knob) {
             const int *vals = knob == 0 ? rows : knob == 1 ? hubs : knob == 2 ? tris : knob == 3 ? grids : layouts;
-            const int nv = knob == 0 ? 3 : knob == 1 ? 3 : knob == 2 ? 4 : knob == 3 ? 4 : 2;
+            const int nv = knob == 0 ? 3 : knob == 1 ? 3 : knob == 2 ? 2 : knob == 3 ? 4 : 2;
             for (int i = 0; i < nv; ++i) {
                 ef::Tune cand = cur;
                 int &field = knob == 0 ? cand.row_thread_max : knob == 1 ? cand.hub_min

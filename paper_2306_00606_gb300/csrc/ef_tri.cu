@@ -30,7 +30,15 @@
 // Measured and left out (4M-node power-law graph): L2 eviction hints
 // (evict_last on probes, evict_first on the candidate stream) changed
 // nothing; staging each tile's candidates in shared memory was slower
-// (2.00 against 1.84 ms).  The pass reads about 1.8 GB from DRAM per launch,
+// (2.00 against 1.84 ms, and again 1.74 against 1.65 ms with a warp step's
+// 128 entries staged by coalesced loads); loading each test's correction
+// tq[sum] with its probes, to save the second round trip of a hit, was
+// slower too (1.85 against 1.65 ms; the per-unit binary search replaced by
+// a shared-memory unit map changed nothing).  Under ncu (half-size graph)
+// the kernel issues in 46% of cycles, waits on long-scoreboard loads (7.2
+// cycles per issue) with 39% of the warp slots filled (64 registers), and
+// uses 31% of L2 and 8% of DRAM throughput: bound by the latency of its
+// probes at the concurrency its registers allow.  The pass reads about 1.5 GB from DRAM per launch,
 // mostly misses of the long tail of membership probes (10% of the tests spread
 // over about 100 MB of tables and lists).
 //
@@ -254,148 +262,6 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
     }
 }
 
-// Staged form of the pair tests: a warp step first copies the ids, degrees
-// and probe descriptors of SW consecutive oriented entries (its EW edges and
-// the SW - EW entries after them) into shared memory with coalesced loads, so
-// that a unit finds its candidates there instead of waiting for a global load
-// before its probes; candidates beyond the staged range (long out-lists that
-// run past it) are loaded from global memory as before.  A lane then waits on
-// one round of global loads per unit, its membership probes.
-template <int TRI_UNIT, int TRI_BLOCKS, int EW, int SW>
-__global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_staged(
-    const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_D,
-    const int2 *__restrict__ out_pd, const int32_t *__restrict__ out_src, const int32_t *__restrict__ out_hash,
-    const int32_t *__restrict__ outdeg, const int32_t *__restrict__ D, int32_t n,
-    const int32_t *__restrict__ owner_range, const int64_t *__restrict__ tq,
-    int64_t *__restrict__ qacc, int64_t *__restrict__ tcnt) {
-    static_assert((EW == 32 || EW == 64) && SW >= EW && SW % 32 == 0, "warp step shapes");
-    __shared__ int4 s_ent[TRI_WARPS][SW];   // {id, degree, descriptor x, descriptor y}
-    __shared__ int s_ex[TRI_WARPS][EW];     // exclusive prefix of unit counts
-    __shared__ int s_kend[TRI_WARPS][EW], s_Dab[TRI_WARPS][EW], s_a[TRI_WARPS][EW];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t total = out_ptr[n];
-    const int64_t stride = (int64_t)gridDim.x * TRI_WARPS * EW;
-    const int a_lo = owner_range ? owner_range[0] : 0, a_hi = owner_range ? owner_range[1] : n;
-    for (int64_t K0 = ((int64_t)blockIdx.x * TRI_WARPS + w) * EW; K0 < total; K0 += stride) {
-        const int64_t lim = min(total, K0 + SW);   // entries [K0, lim) are staged
-#pragma unroll
-        for (int h = 0; h < SW / 32; ++h) {
-            const int64_t k = K0 + h * 32 + lane;
-            if (k < lim) {
-                const int2 pd = __ldg(out_pd + k);
-                s_ent[w][h * 32 + lane] = make_int4(__ldg(out_col + k), __ldg(out_D + k), pd.x, pd.y);
-            }
-        }
-        int U = 0;
-#pragma unroll
-        for (int h = 0; h < EW / 32; ++h) {
-            const int e = h * 32 + lane;
-            const int64_t k = K0 + e;
-            int nu = 0;
-            if (k < total) {
-                const int a = __ldg(out_src + k);
-                const int kend = __ldg(out_ptr + a) + __ldg(outdeg + a);
-                const int np = a >= a_lo && a < a_hi ? kend - (int)k - 1 : 0;
-                if (np > 0) {
-                    s_kend[w][e] = kend;
-                    s_Dab[w][e] = __ldg(D + a) + __ldg(out_D + k);
-                    s_a[w][e] = a;
-                    nu = (np + TRI_UNIT - 1) / TRI_UNIT;
-                }
-            }
-            int inc = nu;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(FULL, inc, o);
-                if (lane >= o) inc += y;
-            }
-            s_ex[w][e] = U + inc - nu;
-            U += __shfl_sync(FULL, inc, 31);
-        }
-        __syncwarp();
-        int cur_a = -1, hit_a = 0;
-        int64_t acc_a = 0;
-        int i = -1, kend = 0, exi = 0, b = 0, Db = 0, Dab = 0, ai = 0;
-        int2 bpd = make_int2(0, 0);
-        for (int t = lane; t < U; t += 32) {
-            int ni = 0;
-#pragma unroll
-            for (int step = EW / 2; step > 0; step >>= 1)
-                if (s_ex[w][ni + step] <= t) ni += step;
-            if (ni != i) {
-                i = ni;
-                kend = s_kend[w][i];
-                exi = s_ex[w][i];
-                const int4 be = s_ent[w][i];
-                b = be.x;
-                Db = be.y;
-                bpd = make_int2(be.z, be.w);
-                Dab = s_Dab[w][i];
-                ai = s_a[w][i];
-            }
-            const int64_t j0 = K0 + i + 1 + TRI_UNIT * (t - exi);
-            const int jn = (int)min((int64_t)TRI_UNIT, kend - j0);
-            int c[TRI_UNIT], Dc[TRI_UNIT];
-            int2 rc[TRI_UNIT];
-#pragma unroll
-            for (int q = 0; q < TRI_UNIT; ++q) {
-                if (q < jn) {
-                    const int64_t j = j0 + q;
-                    if (j < lim) {
-                        const int4 ce = s_ent[w][j - K0];
-                        c[q] = ce.x;
-                        Dc[q] = ce.y;
-                        rc[q] = make_int2(ce.z, ce.w);
-                    } else {
-                        c[q] = __ldg(out_col + j);
-                        Dc[q] = __ldg(out_D + j);
-                        rc[q] = __ldg(out_pd + j);
-                    }
-                }
-            }
-            Probe pr[TRI_UNIT];
-            int4 x[TRI_UNIT], y[TRI_UNIT];
-#pragma unroll
-            for (int q = 0; q < TRI_UNIT; ++q) {
-                if (q < jn) {
-                    const bool b_low = rank_less(Db, b, Dc[q], c[q]);
-                    pr[q] = probe_of(out_col, out_hash, b_low ? bpd : rc[q], b_low ? c[q] : b);
-                    pr[q].info |= (unsigned)b_low << 10;
-                    x[q] = __ldg(pr[q].p0);
-                    y[q] = __ldg(pr[q].p0 + pr[q].d1);
-                }
-            }
-            int hits = 0;
-            int64_t gsum = 0;
-#pragma unroll
-            for (int q = 0; q < TRI_UNIT; ++q) {
-                if (q < jn) {
-                    const bool b_low = (pr[q].info >> 10) & 1u;
-                    if (probe_done(pr[q], x[q], y[q], out_col, out_hash, b_low ? bpd : rc[q], b_low ? c[q] : b)) {
-                        const int64_t g = __ldg(tq + Dab + Dc[q]);
-                        credit_tri(qacc, tcnt, c[q], g, 1);
-                        gsum += g;
-                        ++hits;
-                    }
-                }
-            }
-            if (hits) {
-                credit_tri(qacc, tcnt, b, gsum, hits);
-                if (ai != cur_a) {
-                    if (hit_a) credit_tri(qacc, tcnt, cur_a, acc_a, hit_a);
-                    cur_a = ai;
-                    acc_a = 0;
-                    hit_a = 0;
-                }
-                acc_a += gsum;
-                hit_a += hits;
-            }
-        }
-        if (hit_a) credit_tri(qacc, tcnt, cur_a, acc_a, hit_a);
-        __syncwarp();
-    }
-}
-
 static inline unsigned grid_of(int64_t work, int per_block, int64_t cap) {
     int64_t g = (work + per_block - 1) / per_block;
     return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
@@ -404,15 +270,7 @@ static inline unsigned grid_of(int64_t work, int per_block, int64_t cap) {
 int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cudaStream_t st,
                      const int32_t *owner_range) {
     const unsigned grid = grid_of(m / 2, TRI_WARPS * 32, (int64_t)t.num_sms * 16);
-    if (t.tri_variant == 2)
-        k_tri_staged<2, 4, 64, 128><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pd,
-                                                                    s.out_src, s.out_hash, s.outdeg, s.D, n,
-                                                                    owner_range, s.tq, s.qacc, s.tcnt);
-    else if (t.tri_variant == 3)
-        k_tri_staged<4, 3, 64, 128><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pd,
-                                                                    s.out_src, s.out_hash, s.outdeg, s.D, n,
-                                                                    owner_range, s.tq, s.qacc, s.tcnt);
-    else if (t.tri_variant == 1)
+    if (t.tri_variant == 1)
         k_tri_pairs<4, 3, 32><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pd, s.out_src,
                                                             s.out_hash, s.outdeg, s.D, n, owner_range, s.tq, s.qacc,
                                                             s.tcnt);

@@ -341,9 +341,9 @@ def test_profile_stats(ctx):
     assert st["calls"] == 1 and st["total_ms"] > 0 and st["wedge_big_ms"] > 0 and st["tri_pairs_ms"] > 0
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1])
 def test_pair_test_variants_agree(ctx, variant):
-    """Every pair-test kernel variant lists the same triangles: exact per-node
+    """The other pair-test kernel variant lists the same triangles: exact per-node
     counts against the oracle and the same N, S and EF as variant 0, on
     graphs whose out-lists run far past a warp step's staged entries (K_600:
     out-degrees up to 599; dense ER; power-law hubs; R-MAT)."""
