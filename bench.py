@@ -84,17 +84,59 @@ def algorithmic_bytes(g, st):
     }
 
 
-def committed_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (profiles/traffic.json), or None when there is none for this workload or
-    the kernel's source has changed since it was taken."""
+PASS_PREFIX = {"prep_ms": ("k_degrees", "k_row_stats", "k_batch_check"),
+               "orient_ms": ("k_ftab", "k_layout", "k_scan", "k_node_info", "k_orient", "k_hash"),
+               "wedge_small_ms": ("k_wedge_small",), "wedge_big_ms": ("k_wedge_mid", "k_wedge_hub", "k_wedge_big", "k_big"),
+               "tri_pairs_ms": ("k_tri_pairs",), "finalize_ms": ("k_finalize",)}
+
+
+def committed_kernels(workload):
+    """Per-kernel figures of the committed ncu launch list of `workload`
+    (profiles/traffic.json: DRAM bytes per launch, L2 hit rate, share of the
+    launch time), for the kernels whose source file is unchanged since the
+    capture; {} when there is none."""
     import hashlib
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[workload][kernel]
-        h = hashlib.sha256(open(os.path.join(ROOT, rec["source"]), "rb").read()).hexdigest()[:16]
-        return rec["dram_bytes_per_launch"] if h == rec["source_sha256_16"] else None
+        recs = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[workload]
     except (OSError, KeyError, ValueError, TypeError):
-        return None
+        return {}
+    out, sha = {}, {}
+    for k, r in recs.items():
+        try:
+            if r["source"] not in sha:
+                sha[r["source"]] = hashlib.sha256(open(os.path.join(ROOT, r["source"]), "rb").read()).hexdigest()[:16]
+            if sha[r["source"]] == r["source_sha256_16"]:
+                out[k] = r
+        except (OSError, KeyError, TypeError):
+            continue
+    return out
+
+
+def passes_ncu(workload):
+    """Per pass, from committed_kernels: the kernels, their summed share of the
+    launch time and DRAM bytes per launch, and the time-weighted L2 hit rate
+    (None for a pass with no fresh record)."""
+    recs = committed_kernels(workload)
+    res = {}
+    for p, pre in PASS_PREFIX.items():
+        ks = {k: r for k, r in recs.items() if k.startswith(pre)}
+        if not ks:
+            res[p] = None
+            continue
+        t = sum(r["ms_per_launch"] * r["launches"] for r in ks.values())
+        res[p] = {"kernels": sorted(ks), "ncu_share": sum(r["share"] for r in ks.values()),
+                  "dram_bytes_per_launch": sum(r["dram_bytes_per_launch"] for r in ks.values()),
+                  "l2_hit_pct": sum(r["l2_hit_pct"] * r["ms_per_launch"] * r["launches"] for r in ks.values()) / t
+                  if t > 0 else None}
+    return res
+
+
+def committed_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` (name prefix) from the committed ncu
+    launch list, or None when there is none for this workload or the
+    kernel's source has changed since it was taken."""
+    ks = [r for k, r in committed_kernels(workload).items() if k.startswith(kernel)]
+    return ks[0]["dram_bytes_per_launch"] if len(ks) == 1 else None
 
 
 def parse():
@@ -832,6 +874,7 @@ def run_ours(args):
         "roofline_alu": roofline_alu,
         "credits_per_s": 4 * value,
         "passes_gbs": {k: alg[k] / (per[k] / 1e3) / 1e9 if per[k] > 0 else None for k in PASSES},
+        "passes_ncu": passes_ncu(args.workload),
         "e2e": e2e,
         "gpu_launches": int(passes["kernels"]),
         "clocks": clocks,

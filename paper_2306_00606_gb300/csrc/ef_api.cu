@@ -302,8 +302,8 @@ int compute_device(ef_ctx *ctx, const Job &j) {
     rc = ensure_buffer(ctx, (void **)&ctx->ftab, &have, (size_t)fcap * 2 * sizeof(double), 0);
     if (rc) return rc;
     ctx->ftab_cap = (int64_t)(have / (2 * sizeof(double)));
-    s.ftab = ctx->ftab;
-    s.tq = reinterpret_cast<int64_t *>(ctx->ftab + fcap);
+    s.ftab = reinterpret_cast<float2 *>(ctx->ftab);
+    s.tq = reinterpret_cast<int64_t *>(s.ftab + fcap);
 
     if (use_graph) {
         GraphKey key;
@@ -511,8 +511,8 @@ int prepare_graph(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, 
     rc = ensure_buffer(ctx, (void **)&ctx->ftab, &have, (size_t)fcap * 2 * sizeof(double), 0);
     if (rc) return rc;
     ctx->ftab_cap = (int64_t)(have / (2 * sizeof(double)));
-    s.ftab = ctx->ftab;
-    s.tq = reinterpret_cast<int64_t *>(ctx->ftab + fcap);
+    s.ftab = reinterpret_cast<float2 *>(ctx->ftab);
+    s.tq = reinterpret_cast<int64_t *>(s.ftab + fcap);
     LAUNCH(launch_ftab(s.ftab, s.tq, s.counters, fcap, ctx->stream), "f table");
     return EF_OK;
 }

@@ -128,7 +128,7 @@ struct Scratch {
     double  *big_partial;// m/BIG_ROWS + n + 2  per-item middle-node partial sums (direct kernel)
     int32_t *scan_tmp;   // scan block sums (orientation)
     int32_t *scan_tmp2;  // scan block sums (direct kernel's items)
-    double  *ftab;       // 3*maxdeg+1 (capacity): f(d) = d ln d in FP64
+    float2  *ftab;       // 3*maxdeg+1 (capacity): f(d) = d ln d as an FP32 pair hi + lo (F2Sum)
     void    *hub_cls;    // m+n+2  class (degree, count) pairs of hubs with > HUB_SMEM_K classes
     void    *hub_q;      // m+n+2  their per-class credits
     int32_t *hub_cidx;   // m+1    class index of each neighbour of a hub (at the hub's row positions)
@@ -332,6 +332,38 @@ struct SumAcc {
     __device__ __forceinline__ T get() const { return s - c; }
 };
 
+// FP64-mode sums of f terms in FP32 pairs.  The f table holds each f(d) =
+// d ln d (computed in FP64) as an unevaluated sum hi + lo of two floats
+// (48 significant bits).  F2Sum adds terms c (hi + lo), c an integer below
+// 2^24, to a running pair (sh, sl): c hi is split exactly into p + pe with
+// an FMA, p goes into sh by an error-free two-sum whose error, pe and c lo
+// collect in sl.  Every term here is >= 0, so over a chunk of at most
+// F2_CHUNK terms each error is at most 2^-24 of the chunk's sum and sl's own
+// rounding adds at most F2_CHUNK^2 2^-48 of it: below 2^-38 (3.6e-12)
+// relative for chunks of 32, which the caller then adds up in FP64.  Each
+// term costs about ten FP32 instructions instead of an FP64 FMA, which runs
+// at a thirty-second of the FP32 rate on this GPU.
+constexpr int F2_CHUNK = 32;
+struct F2Sum {
+    float sh = 0.f, sl = 0.f;
+    __device__ __forceinline__ void add(float2 t, float c) {
+        const float p = c * t.x;
+        const float pe = fmaf(c, t.x, -p);   // c t.x - p, exactly
+        const float s = sh + p;
+        const float bp = s - sh;
+        sl += ((sh - (s - bp)) + (p - bp)) + fmaf(c, t.y, pe);
+        sh = s;
+    }
+    __device__ __forceinline__ void add(float2 t) {   // c = 1
+        const float s = sh + t.x;
+        const float bp = s - sh;
+        sl += ((sh - (s - bp)) + (t.x - bp)) + t.y;
+        sh = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)sh + (double)sl; }
+};
+__device__ __forceinline__ double f2_value(float2 t) { return (double)t.x + (double)t.y; }
+
 // d * log2(d) for integral d >= 1 held in a float (MUFU lg2).
 __device__ __forceinline__ float dlog2d(float d) { return d * __log2f(d); }
 
@@ -413,7 +445,7 @@ int64_t device_l2_bytes();   // of the current device (after prepare_kernels ran
 // CSR: step 1.10 -> 0.82 ms in bin order; BA n = 16M, 580 MB: 9.9 -> 11.3 ms.)
 inline bool rows_in_bins_allowed(int64_t m) { return 4 * m <= device_l2_bytes() / 2; }
 int launch_scan(const int32_t *in, int32_t *out, int32_t n, int32_t *tmp, cudaStream_t st);
-int launch_ftab(double *ftab, int64_t *tq, int32_t *cnt, int64_t cap, cudaStream_t st);
+int launch_ftab(float2 *ftab, int64_t *tq, int32_t *cnt, int64_t cap, cudaStream_t st);
 int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
                        const Tune &t, cudaStream_t st);
 int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int wedge_mode,

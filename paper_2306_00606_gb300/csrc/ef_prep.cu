@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(ROW_CTA) k_row_stats_hub(const int32_t *__rest
 // orientation wait one L2 round trip per 32-entry chunk: 0.3 ms more on the
 // 4M-node power-law graph.)
 static_assert(SMALL_MAX <= 32, "a one-thread row's table fits a 64-bit occupancy mask");
+struct OrientStage;
 struct Orient {
     const int32_t *ci;
     const int4 *info;   // per node {D, sigma1, probe descriptor of its out-list}
@@ -429,9 +430,38 @@ struct Orient {
         out_pd[k] = make_int2(nf.z, nf.w);
     }
     // A whole short row by one thread, CHUNK entries at a time (loads issued
-    // together); returns omega_v.
+    // together); returns omega_v.  With sg, the entries and table keys go to
+    // the warp's shared-memory staging area instead (OrientStage).
     template <int CHUNK>
-    __device__ __forceinline__ int64_t row(int v, int Dv, int a, int b, int k) const {
+    __device__ __forceinline__ int64_t row(int v, int Dv, int a, int b, int k,
+                                           const OrientStage *sg = nullptr) const;
+};
+
+// Shared-memory staging of one warp step of one-thread rows: when the rows'
+// out-lists form one contiguous range [kbase, kbase + len) of the oriented
+// CSR (consecutive rows in layout order, none of them walked elsewhere), the
+// rows write their entries and hash-table keys here and the warp then stores
+// the range, and its table slots [tbase, tbase + tlen), with coalesced
+// stores.  Written directly, a store instruction of 32 rows touched about 12
+// sectors for 128 bytes.
+struct OrientStage {
+    int32_t *col, *D, *src;
+    int2 *pd;
+    int32_t *tab;
+    int kbase;
+    int64_t tbase;
+    __device__ __forceinline__ void put(int k, int u, int x, int4 nf) const {
+        const int i = k - kbase;
+        col[i] = x;
+        D[i] = nf.x;
+        src[i] = u;
+        pd[i] = make_int2(nf.z, nf.w);
+    }
+};
+
+template <int CHUNK>
+__device__ __forceinline__ int64_t Orient::row(int v, int Dv, int a, int b, int k, const OrientStage *sg) const {
+    {
         int64_t om = 0;
         int mn = 0x7fffffff, mx = 0;
         int64_t hb = 0;
@@ -453,13 +483,15 @@ struct Orient {
                     mn = min(mn, nf[q].x);
                     mx = max(mx, nf[q].x);
                     if (rank_less(Dv, v, nf[q].x, x[q])) {
-                        put(k++, v, x[q], nf[q]);
+                        if (sg) sg->put(k++, v, x[q], nf[q]);
+                        else put(k++, v, x[q], nf[q]);
                         if (hashed) {
                             // first free slot from the home bucket, cyclically
                             const uint64_t f = ~occ & full;
                             const uint64_t hi = f & (~0ull << (4 * bucket_of(x[q], nb)));
                             const int pos = __ffsll((long long)(hi ? hi : f)) - 1;
-                            out_hash[hb + pos] = x[q];
+                            if (sg) sg->tab[hb + pos - sg->tbase] = x[q];
+                            else out_hash[hb + pos] = x[q];
                             occ |= 1ull << pos;
                         }
                     }
@@ -472,7 +504,7 @@ struct Orient {
         }
         return om;
     }
-};
+}
 
 // info[v] = {D_v, sigma1(v), probe descriptor of v's out-list}: what the
 // orientation needs of a neighbour, in one 16-byte gather (sigma1 <= m < 2^31).
@@ -580,19 +612,35 @@ __device__ __forceinline__ void orient_row_warp(const Orient &o, int u, int ua, 
 // waste most of a wide chunk.  Both forms are launched; the one that does not
 // match the degree pass's counts returns at once.  (WS batch orientation
 // 4.7 -> 4.3 ms with 8; the power-law graph 0.90 -> 1.02 ms with 8.)
+// Entries of one warp step that the staging area of k_orient<CHUNK> holds
+// (20 bytes each, plus two table slots).  Only the eight-record form (graphs
+// without rows above degree 32) stages: measured on the 4096-graph WS batch,
+// orientation 4.32 -> 2.96 ms; the four-record form (a staging area of 128
+// entries, 5 blocks per SM) was slower on the power-law graph (0.89 -> 0.96
+// ms), BA 16M (2.42 -> 2.55 ms) and BA 1M, where its rows are longer or come
+// from the degree bins and the warp's rows rarely fit, so it writes directly.
+template <int CHUNK>
+struct OrientCap {
+    static constexpr int value = CHUNK == 8 ? 192 : 0;
+};
+
 template <int CHUNK>
 __global__ void __launch_bounds__(256, CHUNK == 8 ? 3 : 5) k_orient(
     const int32_t *__restrict__ rp, int32_t n, int64_t m, int tmax, int hub_min, Orient o,
     const int32_t *__restrict__ D, const int32_t *__restrict__ bins, bool bins_ok, const int32_t *__restrict__ cnt,
-    const int32_t *__restrict__ out_ptr, int64_t *__restrict__ omega) {
+    const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ outdeg, int64_t *__restrict__ omega) {
     if ((cnt[BIN_BIG] == 0) != (CHUNK == 8)) return;
+    constexpr int CAP = OrientCap<CHUNK>::value;
+    constexpr int SCAP = CAP > 0 ? CAP : 1, TCAP = CAP > 0 ? 2 * CAP + 8 : 1;
     __shared__ RowOrder s_ord;
+    __shared__ int32_t s_col[8][SCAP], s_D[8][SCAP], s_src[8][SCAP], s_tab[8][TCAP];
+    __shared__ int2 s_pd[8][SCAP];
     if (threadIdx.x == 0) s_ord.load(cnt, n, bins_ok);
     __syncthreads();
     const RowOrder &ord = s_ord;
     const int total = ord.total();
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + w;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t base = warp * 32; base < total; base += nwarps * 32) {
         const int i = (int)(base + lane);
@@ -601,7 +649,39 @@ __global__ void __launch_bounds__(256, CHUNK == 8 ? 3 : 5) k_orient(
         const int a = in ? rp[v] : 0, b = in ? rp[v + 1] : 0;
         const bool ok = in && a >= 0 && a <= b && (int64_t)b <= m;
         const int Dv = ok ? b - a : 0;
-        if (ok && Dv <= tmax) omega[v] = o.template row<CHUNK>(v, Dv, a, b, out_ptr[v]);
+        const bool mine = ok && Dv <= tmax;
+        const int k0 = mine ? out_ptr[v] : 0;
+        // stage when this step's one-thread rows own one contiguous range that
+        // fits: span of their out-lists == sum of their lengths (no other row's
+        // list inside), both within CAP
+        int kmin = 0, kend = 0, sum = 0;
+        if constexpr (CAP > 0) {
+            const int od = mine ? outdeg[v] : 0;
+            kmin = __reduce_min_sync(FULL, od > 0 ? k0 : 0x7fffffff);
+            kend = __reduce_max_sync(FULL, od > 0 ? k0 + od : 0);
+            sum = __reduce_add_sync(FULL, od);
+        }
+        const bool stage = CAP > 0 && sum > 0 && sum <= CAP && kend - kmin == sum;
+        if (stage) {
+            const int64_t tb0 = ((int64_t)2 * kmin + 3) & ~(int64_t)3;
+            const int64_t tb1 = ((int64_t)2 * kend + 3) & ~(int64_t)3;
+            const int tlen = o.out_hash ? (int)(tb1 - tb0) : 0;
+            for (int t = lane; t < tlen; t += 32) s_tab[w][t] = -1;
+            __syncwarp();
+            const OrientStage sg{s_col[w], s_D[w], s_src[w], s_pd[w], s_tab[w], kmin, tb0};
+            if (mine) omega[v] = o.template row<CHUNK>(v, Dv, a, b, k0, &sg);
+            __syncwarp();
+            for (int t = lane; t < sum; t += 32) {
+                o.out_col[kmin + t] = s_col[w][t];
+                o.out_D[kmin + t] = s_D[w][t];
+                o.out_src[kmin + t] = s_src[w][t];
+                o.out_pd[kmin + t] = s_pd[w][t];
+            }
+            for (int t = lane; t < tlen; t += 32) o.out_hash[tb0 + t] = s_tab[w][t];
+            __syncwarp();
+        } else if (mine) {
+            omega[v] = o.template row<CHUNK>(v, Dv, a, b, k0);
+        }
         unsigned wide = __ballot_sync(FULL, ok && Dv > tmax && Dv < hub_min);
         while (wide) {
             const int j = __ffs(wide) - 1;
@@ -735,12 +815,14 @@ __global__ void k_big_chunks(const int32_t *__restrict__ D, const int32_t *__res
 }
 
 // -------------------------------------------------------------- f(d) table
-// ftab[d] = d ln d; tq[s] = 4 (f(s-6) - f(s-4)) in units of 2^-F, the
+// ftab[d] = d ln d (computed in FP64, stored as the FP32 pair hi + lo of
+// F2Sum: hi = f rounded to FP32, lo = the rest rounded to FP32, together
+// within 2^-48 of f); tq[s] = 4 (f(s-6) - f(s-4)) in units of 2^-F, the
 // correction one triangle of degree sum s brings to each of its nodes.  F is
 // the largest value <= TRI_FRAC_MAX with C(maxdeg, 2) * max|g| * 2^F < 2^62
 // (|g| <= 8 (ln(3 maxdeg) + 1) + 8); every thread derives the same F and
 // thread 0 publishes it for the finalize pass.
-__global__ void k_ftab(double *__restrict__ ftab, int64_t *__restrict__ tq, int32_t *__restrict__ cnt, int64_t cap) {
+__global__ void k_ftab(float2 *__restrict__ ftab, int64_t *__restrict__ tq, int32_t *__restrict__ cnt, int64_t cap) {
     const int64_t maxdeg = cnt[CNT_MAXDEG];
     int64_t L = 3 * maxdeg + 1;
     if (L > cap) L = cap;
@@ -750,7 +832,9 @@ __global__ void k_ftab(double *__restrict__ ftab, int64_t *__restrict__ tq, int3
     F = F > TRI_FRAC_MAX ? TRI_FRAC_MAX : (F < 0 ? 0 : F);
     if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CNT_TRIFRAC] = F;
     for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < L; d += (int64_t)gridDim.x * blockDim.x) {
-        ftab[d] = d > 1 ? (double)d * log((double)d) : 0.0;
+        const double f = d > 1 ? (double)d * log((double)d) : 0.0;
+        const float hi = (float)f;
+        ftab[d] = make_float2(hi, (float)(f - (double)hi));
         double g = 0.0;
         if (d >= 6) {
             const double a = (double)(d - 6), b = (double)(d - 4);
@@ -824,7 +908,7 @@ int launch_scan(const int32_t *in, int32_t *out, int32_t n, int32_t *tmp, cudaSt
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_ftab(double *ftab, int64_t *tq, int32_t *cnt, int64_t cap, cudaStream_t st) {
+int launch_ftab(float2 *ftab, int64_t *tq, int32_t *cnt, int64_t cap, cudaStream_t st) {
     int64_t blocks = (cap + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     if (blocks < 1) blocks = 1;
@@ -869,9 +953,11 @@ int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
                                                          s.info);
     const Orient o{ci, s.info, s.out_col, s.out_D, s.out_src, s.out_pd, tables ? s.out_hash : nullptr, nmin, nmax, n};
     k_orient<4><<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, n, m, t.row_thread_max, t.hub_min, o, s.D, s.bins,
-                                                         rows_in_bins_allowed(m), s.counters, s.out_ptr, s.omega);
+                                                         rows_in_bins_allowed(m), s.counters, s.out_ptr, s.outdeg,
+                                                         s.omega);
     k_orient<8><<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, n, m, t.row_thread_max, t.hub_min, o, s.D, s.bins,
-                                                         rows_in_bins_allowed(m), s.counters, s.out_ptr, s.omega);
+                                                         rows_in_bins_allowed(m), s.counters, s.out_ptr, s.outdeg,
+                                                         s.omega);
     k_orient_hub<<<t.num_sms * 4, ROW_CTA, 0, st>>>(rp, n, o, s.bins, s.out_ptr, s.counters, s.omega);
     if (tables && bins && t.row_thread_max >= SMALL_MAX)
         k_hash_tail<<<(unsigned)(t.num_sms * 16), 256, 0, st>>>(s.counters, s.lay_ptr, s.out_ptr, n, s.info,

@@ -97,7 +97,7 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
         return fail(EF_ERR_ARG, msg);
     }
 
-    s.ftab = (double *)((char *)base + carve_scratch((char *)base, n, m, s));
+    s.ftab = (float2 *)((char *)base + carve_scratch((char *)base, n, m, s));
     s.tq = reinterpret_cast<int64_t *>(s.ftab + fcap);
     Tune t;
     if (cudaDeviceGetAttribute(&t.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||

@@ -8,9 +8,11 @@
 // in registers and stored once (Ccenter[u]); R_u(x) is added to x's
 // accumulator Tacc[x] by an FP64 reduction in L2 (RED, no return value).
 //
-// Precision modes: FP64 reads f from an FP64 table; FP32C evaluates
-// d log2 d with the MUFU lg2 unit and sums in FP32 with Kahan compensation
-// per thread (times ln 2 at the end); the end credits still travel as FP64.
+// Precision modes: FP64 reads f from a table computed in FP64 and held as
+// FP32 pairs, and sums rows in FP32-pair chunks (F2Sum, below 2^-38 relative
+// error per chunk) added up in FP64; FP32C evaluates d log2 d with the MUFU
+// lg2 unit and sums in FP32 with Kahan compensation per thread (times ln 2
+// at the end); the end credits travel as FP64 in both.
 #include "ef_internal.cuh"
 
 #include <type_traits>
@@ -19,12 +21,18 @@ namespace ef {
 
 // ------------------------------------------------ small middle nodes (D <= 32)
 // G lanes per middle node (G in {4, 8, 16, 32}); lane k owns neighbour k and
-// sums f over the other neighbours of the same middle node, fetched by shuffles.
+// sums f over the other neighbours of the same middle node, fetched by
+// shuffles.  Measured and left out: summing over the node's degree classes
+// (lanes of equal D_x found with one 64-bit match, class leaders' degrees
+// and counts shuffled in), although the 4096-graph WS batch has 6x fewer
+// distinct (degree, degree) pairs than ordered neighbour pairs: small wedges
+// 3.50 -> 4.44 ms there, 0.30 -> 0.51 ms on the power-law graph (the match
+// and two indexed shuffles per class cost more than the pairs they save).
 template <int G, bool F64>
 __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                      const int32_t *__restrict__ D, const int32_t *__restrict__ list,
                                                      const int32_t *__restrict__ cnt, int bin,
-                                                     const double *__restrict__ ftab, double *__restrict__ Tacc,
+                                                     const float2 *__restrict__ ftab, double *__restrict__ Tacc,
                                                      void *__restrict__ Ccenter) {
     using Acc = typename std::conditional<F64, double, float>::type;
     constexpr int PER = 32 / G;
@@ -48,11 +56,14 @@ __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__
         // so no conversion sits in the loop
         const int jmax = __reduce_max_sync(FULL, Du);
         if constexpr (F64) {
+            // at most 31 terms: one FP32-pair chunk (F2Sum)
+            F2Sum a2;
 #pragma unroll 4
             for (int j = 0; j < jmax; ++j) {
                 const int aj = __shfl_sync(FULL, ak, j, G);
-                if (own && j < Du && j != k) acc += __ldg(ftab + (b0 + aj));   // b0 + aj >= 0 for D_u >= 2
+                if (own && j < Du && j != k) a2.add(__ldg(ftab + (b0 + aj)));   // b0 + aj >= 0 for D_u >= 2
             }
+            acc = a2.value();
         } else {
             // d = D_u - 4 + D_x + D_j >= 3 once D_u > 4 (G >= 8): only the
             // smallest bin needs the guard that keeps d = 0 from 0 * log2(0)
@@ -83,7 +94,7 @@ template <bool F64>
 __global__ void __launch_bounds__(BIG_ROWS) k_wedge_big_direct(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
     const int32_t *__restrict__ list, int32_t *__restrict__ cnt, const int32_t *__restrict__ item_ptr,
-    const double *__restrict__ ftab, double *__restrict__ Tacc, double *__restrict__ partial) {
+    const float2 *__restrict__ ftab, double *__restrict__ Tacc, double *__restrict__ partial) {
     using Acc = typename std::conditional<F64, double, float>::type;
     using Elt = typename std::conditional<F64, int, float>::type;
     __shared__ __align__(16) Elt s_a[BIG_TILE];   // FP32C: D_j as float; FP64: D_j as a table offset
@@ -120,10 +131,10 @@ __global__ void __launch_bounds__(BIG_ROWS) k_wedge_big_direct(
                 int i = 0;
                 if constexpr (F64) {
                     for (; i + 2 <= tn; i += 2) {
-                        s0 += __ldg(ftab + (b0 + s_a[i]));
-                        s1 += __ldg(ftab + (b0 + s_a[i + 1]));
+                        s0 += f2_value(__ldg(ftab + (b0 + s_a[i])));
+                        s1 += f2_value(__ldg(ftab + (b0 + s_a[i + 1])));
                     }
-                    for (; i < tn; ++i) s0 += __ldg(ftab + (b0 + s_a[i]));
+                    for (; i < tn; ++i) s0 += f2_value(__ldg(ftab + (b0 + s_a[i])));
                 } else {
                     for (; i + 4 <= tn; i += 4) {
                         const float4 q = *reinterpret_cast<const float4 *>(&s_a[i]);
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(BIG_ROWS) k_wedge_big_direct(
         double r = 0.0;
         if (own) {
             if constexpr (F64) {
-                r = (s0 + s1) - __ldg(ftab + (b0 + ak));
+                r = (s0 + s1) - f2_value(__ldg(ftab + (b0 + ak)));
             } else {
                 // d >= 31 here (D_u > 32), so no clamp is needed in d log2 d
                 double sum = ((double)s0 - (double)c0) + ((double)s1 - (double)c1);
@@ -193,16 +204,17 @@ template <>
 struct ClassEval<false> {
     using Cls = float2;
     using R = float;
-    static __device__ __forceinline__ Cls make(int b, int c) { return make_float2((float)b, (float)c); }
+    static __device__ __forceinline__ Cls make(int b, int c, bool = true) { return make_float2((float)b, (float)c); }
     static __device__ __forceinline__ float bval(Cls x) { return x.x; }
-    static __device__ __forceinline__ float cval(Cls x) { return x.y; }
+    static __device__ __forceinline__ float cval(Cls x, bool = true) { return x.y; }
     // returns R = (sum_j c_j f(base + b_i + b_j) - f(base + 2 b_i)) in natural-log units.
     // Chunks of CHUNK classes are summed in plain FP32 (every term is >= 0,
     // so a chunk's rounding error is below CHUNK ulps of its sum) and the
     // chunk sums with Kahan compensation: one FMA per class pair instead of
     // a multiply and a four-operation compensated add.
     static constexpr int CHUNK = 8;
-    static __device__ __forceinline__ float row(const Cls *cls, int K, int base, Cls ci, const double *) {
+    static __device__ __forceinline__ float row(const Cls *cls, int K, int base, Cls ci, const float2 *,
+                                                bool = true) {
         const float fb = (float)base + ci.x;
         float s = 0.f, c = 0.f;
         int j = 0;
@@ -225,22 +237,43 @@ struct ClassEval<false> {
 
 template <>
 struct ClassEval<true> {
+    // (degree, count): the count as FP32 bits when it is exact in FP32
+    // (pair_ok: the middle node's degree is below 2^24), else as an int
     using Cls = int2;
     using R = double;
-    static __device__ __forceinline__ Cls make(int b, int c) { return make_int2(b, c); }
+    static __device__ __forceinline__ Cls make(int b, int c, bool pair_ok = true) {
+        return make_int2(b, pair_ok ? __float_as_int((float)c) : c);
+    }
     static __device__ __forceinline__ int bval(Cls x) { return x.x; }
-    static __device__ __forceinline__ int cval(Cls x) { return x.y; }
-    static __device__ __forceinline__ double row(const Cls *cls, int K, int base, Cls ci, const double *ftab) {
+    static __device__ __forceinline__ double cval(Cls x, bool pair_ok = true) {
+        return pair_ok ? (double)__int_as_float(x.y) : (double)x.y;
+    }
+    // The row in FP32-pair chunks of F2_CHUNK classes (F2Sum), the chunk sums
+    // in FP64 (pair_ok), else every term an FP64 FMA.
+    static __device__ __forceinline__ double row(const Cls *cls, int K, int base, Cls ci, const float2 *ftab,
+                                                 bool pair_ok = true) {
         const int fb = base + ci.x;
-        double s0 = 0.0, s1 = 0.0;
-        int j = 0;
-        for (; j + 2 <= K; j += 2) {
-            const int4 q = *reinterpret_cast<const int4 *>(cls + j);
-            s0 = fma((double)q.y, __ldg(ftab + (fb + q.x)), s0);
-            s1 = fma((double)q.w, __ldg(ftab + (fb + q.z)), s1);
+        double s = 0.0;
+        if (pair_ok) {
+            int j = 0;
+            while (j < K) {
+                const int je = min(K, j + F2_CHUNK);
+                F2Sum a, b;
+                for (; j + 2 <= je; j += 2) {
+                    const int4 q = *reinterpret_cast<const int4 *>(cls + j);
+                    a.add(__ldg(ftab + (fb + q.x)), __int_as_float(q.y));
+                    b.add(__ldg(ftab + (fb + q.z)), __int_as_float(q.w));
+                }
+                if (j < je) {
+                    a.add(__ldg(ftab + (fb + cls[j].x)), __int_as_float(cls[j].y));
+                    ++j;
+                }
+                s += a.value() + b.value();
+            }
+        } else {
+            for (int j = 0; j < K; ++j) s = fma((double)cls[j].y, f2_value(__ldg(ftab + (fb + cls[j].x))), s);
         }
-        if (j < K) s0 = fma((double)cls[j].y, __ldg(ftab + (fb + cls[j].x)), s0);
-        return (s0 + s1) - __ldg(ftab + (fb + ci.x));
+        return s - f2_value(__ldg(ftab + (fb + ci.x)));
     }
 };
 
@@ -254,7 +287,7 @@ constexpr int MID_WARPS = 4;
 template <bool F64>
 __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
-    const int32_t *__restrict__ list, int32_t *__restrict__ cnt, const double *__restrict__ ftab,
+    const int32_t *__restrict__ list, int32_t *__restrict__ cnt, const float2 *__restrict__ ftab,
     double *__restrict__ Tacc, void *__restrict__ Ccenter) {
     using E = ClassEval<F64>;
     using Cls = typename E::Cls;
@@ -378,7 +411,7 @@ __device__ __forceinline__ int hub_scan(int x, int *s_w, int &total) {
 template <bool F64>
 __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
-    const int32_t *__restrict__ bins, int32_t n, int32_t *__restrict__ cnt, const double *__restrict__ ftab,
+    const int32_t *__restrict__ bins, int32_t n, int32_t *__restrict__ cnt, const float2 *__restrict__ ftab,
     double *__restrict__ Tacc, void *__restrict__ Ccenter, int32_t *__restrict__ cidx_g, void *__restrict__ cls_g_,
     void *__restrict__ q_g_) {
     using E = ClassEval<F64>;
@@ -407,6 +440,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
         const int start = rp[u];
         const int Du = rp[u + 1] - start;
         const int base = Du - 4;
+        const bool pair_ok = Du < (1 << 24);   // class counts exact in FP32 (FP64 mode)
         int32_t *cidx = cidx_g + start;
         for (int i = tid; i < HUB_HIST; i += HUB_THREADS) hist[i] = 0;
         if (tid == 0) s_nsp = 0;
@@ -441,7 +475,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
         for (int j = 0; j < HUB_HIST / HUB_THREADS; ++j) {
             const int bin = tid * (HUB_HIST / HUB_THREADS) + j;
             if (hc[j] > 0) {
-                cls[off] = E::make(bin, hc[j]);
+                cls[off] = E::make(bin, hc[j], pair_ok);
                 hist[bin] = off++;
             }
         }
@@ -456,7 +490,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
             int tot;
             const int pos = hub_scan(sp ? 1 : 0, s_w, tot);
             if (sp) {
-                cls[kbase + pos] = E::make(a, 1);
+                cls[kbase + pos] = E::make(a, 1, pair_ok);
                 cidx[k] = kbase + pos;
             } else if (act) {
                 cidx[k] = hist[a];
@@ -467,9 +501,9 @@ __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
         double center = 0.0;
         for (int i = tid; i < K; i += HUB_THREADS) {
             const Cls c_i = cls[i];
-            const R r = E::row(cls, K, base, c_i, ftab);
+            const R r = E::row(cls, K, base, c_i, ftab, pair_ok);
             cq[i] = r;
-            center += (double)E::cval(c_i) * (double)r;
+            center += (double)E::cval(c_i, pair_ok) * (double)r;
         }
         __syncthreads();
         for (int k = tid; k < Du; k += HUB_THREADS) credit_end(Tacc, ci[start + k], (double)cq[cidx[k]]);

@@ -327,7 +327,7 @@ def test_ranking_recall_and_what_the_network_gains(ctx, trained):
     top_deg = cand_deg[np.lexsort((cand_deg, -exact[cand_deg]))][:len(truth)]
     recall_deg = len(truth & set(top_deg.tolist())) / len(truth)
     print(f"top-1% recall: trained {recall:.4f}, untrained {recall_raw:.4f}, degree {recall_deg:.4f}")
-    assert recall > recall_raw and recall >= recall_deg - 0.01, (recall, recall_raw, recall_deg)
+    assert recall > recall_raw and recall > recall_deg, (recall, recall_raw, recall_deg)
 
 
 def test_full_size_ranking_ba16m(ctx, trained):
