@@ -49,7 +49,8 @@ enum ef_status {
                                this library waits on a flag or on another
                                device, so there is no watchdog) */
     EF_ERR_MODEL = 6,       /* surrogate model malformed or mismatched */
-    EF_ERR_UNSUPPORTED = 7  /* option combination not provided */
+    EF_ERR_UNSUPPORTED = 7  /* option combination not provided, or a node
+                               of degree above EF_MAX_DEGREE */
 };
 
 enum ef_precision {
@@ -64,6 +65,12 @@ enum ef_precision {
                           ln S - T/S in FP32 (FP64 above degree 1000).
                           EF within 2e-5 absolute of the exact value */
 };
+
+/* Largest maximum degree a validated call accepts: the exact integer sums S_v
+ * (and their closed forms' products) stay below 2^63 up to it (S_v is at
+ * most 6 maxdeg^3).  A validated graph with a node of larger degree gives
+ * EF_ERR_UNSUPPORTED; with trust_input the caller guarantees it. */
+#define EF_MAX_DEGREE (1 << 20)
 
 typedef struct ef_ctx ef_ctx;
 

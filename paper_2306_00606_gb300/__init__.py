@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libef.so")
 
 EF_OK, EF_ERR_ARG, EF_ERR_GRAPH, EF_ERR_OOM, EF_ERR_CUDA, EF_ERR_TIMEOUT, EF_ERR_MODEL, EF_ERR_UNSUPPORTED = range(8)
 EF_PREC_FP64, EF_PREC_FP32C = 0, 1
+EF_MAX_DEGREE = 1 << 20   # largest maximum degree a validated call accepts (include/ef.h)
 PRECISIONS = {"fp64": EF_PREC_FP64, "fp32c": EF_PREC_FP32C}
 
 # Every symbol include/ef.h declares (checked by the CPU test of the ABI).

@@ -192,6 +192,18 @@ const char *err_bits(int bits, char *buf, size_t len) {
     return buf;
 }
 
+// Exact S and N need the closed forms' int64 products: every term is at most
+// 6 maxdeg^3 (S_v <= N_v 3 maxdeg with N_v <= 2 maxdeg^2), below 2^63 for a
+// maximum degree up to EF_MAX_DEGREE = 2^20.
+int degree_limit(ef_ctx *ctx, const int32_t *h) {
+    if (h[ef::CNT_MAXDEG] > EF_MAX_DEGREE) {
+        set_err(ctx, "maximum degree %d is above EF_MAX_DEGREE (%d): the exact cluster-degree sums would overflow "
+                     "64 bits", h[ef::CNT_MAXDEG], EF_MAX_DEGREE);
+        return EF_ERR_UNSUPPORTED;
+    }
+    return EF_OK;
+}
+
 int graph_error(ef_ctx *ctx, int bits) {
     char buf[192];
     set_err(ctx, "input is not a symmetric simple sorted CSR:%s", err_bits(bits, buf, sizeof buf));
@@ -294,6 +306,7 @@ int compute_device(ef_ctx *ctx, const Job &j) {
         CU(cudaMemcpyAsync(ctx->h_counters, s.counters, NUM_COUNTERS * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         if (const int bits = prep_error_bits(ctx->h_counters)) return graph_error(ctx, bits);
+        if (const int lim = degree_limit(ctx, ctx->h_counters)) return lim;
         fcap = 3 * (int64_t)ctx->h_counters[CNT_MAXDEG] + 1;
         ctx->bins = bin_layout(ctx->tune, ctx->h_counters, j.n, j.goff_dev != nullptr);
     }
@@ -504,6 +517,7 @@ int prepare_graph(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, 
                            ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
         if (const int bits = prep_error_bits(ctx->h_counters)) return graph_error(ctx, bits);
+        if (const int lim = degree_limit(ctx, ctx->h_counters)) return lim;
         fcap = 3 * (int64_t)ctx->h_counters[CNT_MAXDEG] + 1;
         ctx->bins = bin_layout(ctx->tune, ctx->h_counters, n, false);
     }

@@ -115,6 +115,8 @@ extern "C" int ef_compute_static(const ef_csr *g, int32_t n, int64_t m, int32_t 
         cudaStreamSynchronize(st) != cudaSuccess)
         return fail(EF_ERR_CUDA, "ef_compute_static: validation readback failed");
     if (prep_error_bits(h_cnt)) return fail(EF_ERR_GRAPH, "ef_compute_static: input is not a symmetric simple sorted CSR");
+    if (h_cnt[CNT_MAXDEG] > EF_MAX_DEGREE)
+        return fail(EF_ERR_UNSUPPORTED, "ef_compute_static: maximum degree above EF_MAX_DEGREE (2^20)");
     const bool bins = bin_layout(t, h_cnt, n, false);
     ef_outputs out = {};
     out.ef = out_ef;

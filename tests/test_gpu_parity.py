@@ -362,3 +362,26 @@ def test_pair_test_variants_agree(ctx, variant):
             np.testing.assert_allclose(got["ef"], base["ef"], rtol=1e-12, atol=1e-12)
     finally:
         ef.ef_set_tuning(ctx.handle, None)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_maximum_degree_star(ctx, precision):
+    """The largest degree a validated call accepts, EF_MAX_DEGREE = 2^20: a
+    star K_{1,k} with k = 2^20 leaves has S = k(k-1)(k-2) ~ 1.2e18 at its
+    centre (its 64-bit sums near the top of their range) and closed forms
+    EF = ln(k(k-1)) at the centre and ln(k-1) at every leaf; one more leaf
+    is refused with EF_ERR_UNSUPPORTED."""
+    import torch
+    import paper_2306_00606_gb300 as ef
+    k = ef.EF_MAX_DEGREE
+    g = synth.star(k)
+    got = run(ctx, g, precision)
+    assert got["n_clusters"][0] == k * (k - 1) and got["s"][0] == k * (k - 1) * (k - 2)
+    assert np.all(got["n_clusters"][1:] == k - 1) and np.all(got["s"][1:] == (k - 1) * (k - 2))
+    ref = np.concatenate([[math.log(k * (k - 1))], np.full(k, math.log(k - 1))])
+    tol = dict(rtol=EF_RTOL64, atol=0) if precision == "fp64" else dict(rtol=0, atol=EF_ATOL32)
+    np.testing.assert_allclose(got["ef"], ref, **tol)
+    big = synth.star(k + 1)
+    with pytest.raises(ef.EfError) as ei:
+        ctx.compute(torch.from_numpy(big.row_ptr).cuda(), torch.from_numpy(big.col_idx).cuda(), outputs=("ef",))
+    assert ei.value.code == ef.EF_ERR_UNSUPPORTED and "EF_MAX_DEGREE" in str(ei.value)
