@@ -385,3 +385,35 @@ def test_maximum_degree_star(ctx, precision):
     with pytest.raises(ef.EfError) as ei:
         ctx.compute(torch.from_numpy(big.row_ptr).cuda(), torch.from_numpy(big.col_idx).cuda(), outputs=("ef",))
     assert ei.value.code == ef.EF_ERR_UNSUPPORTED and "EF_MAX_DEGREE" in str(ei.value)
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_full_size_relabel_invariance(ctx, precision):
+    """Relabelling the nodes of the 4M-node power-law graph by a random
+    permutation permutes every output: N, S, triangles and flags exactly, EF
+    within the precision's bar.  The relabelled graph moves the hubs to other
+    ids, so the out-list layout, the work bins' order and every kernel's
+    schedule change, while Algorithm 1's result may not."""
+    g, _, _ = _full_size_ref(3)
+    perm = np.random.default_rng(99).permutation(g.n)
+    h = synth.relabel(g, perm)
+    a = run(ctx, g, precision)
+    b = run(ctx, h, precision)
+    for k in ("n_clusters", "s", "triangles", "flag"):
+        np.testing.assert_array_equal(b[k][perm], a[k])
+    tol = dict(rtol=2 * EF_RTOL64, atol=1e-12) if precision == "fp64" else dict(rtol=0, atol=2 * EF_ATOL32)
+    np.testing.assert_allclose(b["ef"][perm], a["ef"], **tol)
+
+
+@pytest.mark.parametrize("precision", ["fp32c", "fp64"])
+def test_rmat_sweep_graph_sampled(ctx, precision):
+    """The densest graph of the R-MAT sweep (2^16 nodes, 32 edges per node,
+    a, b, c = .57, .19, .19): sampled nodes, the 20 largest hubs included,
+    against the vertex-centric oracle; every node's N in closed form."""
+    g = synth.rmat(16, 32, synth.SEED_BASE + 132)
+    got = run(ctx, g, precision)
+    np.testing.assert_array_equal(got["n_clusters"], _closed_counts(g))
+    nodes = _sample(g, 60, 6, np.random.default_rng(5))
+    ref = oracle.vertex(g, nodes)
+    ref["tri"] = ref["t"]
+    assert_parity(got, ref, precision, nodes=nodes)
