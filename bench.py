@@ -280,7 +280,7 @@ def _closed_credits(g):
     return d * (d - 2) + np.bincount(src, weights=d[g.col_idx], minlength=g.n).astype(np.int64)
 
 
-def oracle_steps(g, steps: int, seconds: float, seed0: int = 0):
+def oracle_steps(g, steps: int, seconds: float, seed0: int = 0, threads: int = 0):
     """Time the oracle (vertex-centric, OpenMP dynamic over all host cores) on
     `steps` random node samples of about `seconds` each; yields one dict per
     step.  A sample draws uniformly from the nodes whose own work (N_v
@@ -289,7 +289,7 @@ def oracle_steps(g, steps: int, seconds: float, seed0: int = 0):
     step size comes from a short calibration run; seeds seed0, seed0 + 1, ...
     make the samples the same in every run."""
     import oracle
-    cores = oracle.num_threads()
+    cores = threads if threads > 0 else oracle.num_threads()
     N = _closed_credits(g)
     # calibration: random nodes of at most 50x the median work, doubling
     # until a run takes 0.25 s (or covers the graph)
@@ -700,6 +700,13 @@ def workloads_leg(args, dev, hbm: float) -> dict:
                            "roofline_path": {"bound": "hbm", "algorithmic_bytes": path_bytes,
                                              "achieved": path_bytes / (ms / 1e3) / 1e9, "peak": hbm,
                                              "unit": "GB/s", "frac": path_bytes / (ms / 1e3) / 1e9 / hbm}}
+        if name in ("er2000", "ba1m"):
+            # the oracle beside it, on all host cores and on one (bounded samples)
+            entry["oracle"] = {}
+            for thr, label in ((0, "all_cores"), (1, "one_core")):
+                rows = list(oracle_steps(g, 1, 2.0, seed0=0, threads=thr))
+                entry["oracle"][label] = {"clusters_per_s": rows[0]["clusters"] / rows[0]["s"],
+                                          "cores": rows[0]["cores"], "nodes": rows[0]["nodes"], "s": rows[0]["s"]}
         if batched:
             # each graph alone: its rows relabelled to 0.., one synchronous call each
             off = g.graph_off
