@@ -57,8 +57,10 @@ enum ef_precision {
     EF_PREC_FP64 = 0,  /* d ln d computed in FP64 (a table held as FP32
                           pairs, within 2^-48); row sums in FP32-pair
                           chunks of at most 32 terms (below 3.6e-12
-                          relative each), everything else in FP64.  EF
-                          within 1e-9 relative of the exact value */
+                          relative each), everything else in FP64, ln S
+                          and T/S by a table-based logarithm and a refined
+                          reciprocal (about 1e-14 relative).  EF within
+                          1e-9 relative of the exact value */
     EF_PREC_FP32C = 1  /* d ln d in FP32 (hardware log2) with compensated
                           (Kahan) FP32 sums per thread; the credits a node
                           receives from its neighbours are summed in FP64;

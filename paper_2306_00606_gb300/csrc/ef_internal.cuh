@@ -437,6 +437,7 @@ int launch_big_items(const Scratch &s, int32_t n, cudaStream_t st);
 int launch_batch_check(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const int64_t *goff, int32_t G,
                        const Scratch &s, const Tune &t, cudaStream_t st);
 int prepare_kernels();
+int prepare_final_tables();   // ln table of the finalize (ef_final.cu), once per device
 int64_t device_l2_bytes();   // of the current device (after prepare_kernels ran on it)
 
 // Whether the one-thread row passes may take their rows in work-bin order

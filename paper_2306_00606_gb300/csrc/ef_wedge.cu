@@ -596,7 +596,7 @@ int prepare_kernels() {
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
         return -1;
     DeviceProps &p = g_dev_props[dev];
-    if (class_occupancy<true>(p) || class_occupancy<false>(p)) return -1;
+    if (class_occupancy<true>(p) || class_occupancy<false>(p) || prepare_final_tables()) return -1;
     p.l2_bytes = l2;
     return 0;
 }
