@@ -5,8 +5,8 @@
 // Pass order (one graph or one batch, all on the context stream):
 //   part A   one memset of the per-node accumulators and the counters;
 //            degrees + row_ptr checks + wedge bins; per-row checks,
-//            sigma1/sigma2, out-degrees, the symmetry sum; (batched) the
-//            check that no entry leaves its graph
+//            sigma1/sigma2, out-degrees, the symmetry sum and (batched) the
+//            check that no entry leaves its graph, in the same row pass
 //   host     one small readback: validation word, symmetry sum and max
 //            degree (skipped with trust_input); part B runs on valid input only
 //   part B   f table (f(d) = d ln d and the triangle corrections, d < 3 maxdeg + 1);
@@ -91,15 +91,15 @@ namespace {
 
 thread_local char g_err[512];
 
-// Kernels one call launches: part A 3 (+1 batched), f table 1, orientation
+// Kernels one call launches: part A 3 (the batch check runs in the row pass), f table 1, orientation
 // (degree-bin layout: layout gather, a scan of 3, layout scatter; node
 // layout: a scan of 3; then node records, the row kernel in two forms of
 // which one returns at once, the hub rows, hash tables of the longer rows;
 // the short rows' tables are filled by the row kernel itself), small wedges
 // 4, big wedges (class kernels 2; direct mode: item counts, a scan of 3,
 // direct kernel, reduction), pair tests 1, finalize 1.
-int64_t kernels_per_call(bool batched, bool bins, int wedge_mode) {
-    return 3 + (batched ? 1 : 0) + 1 + (bins ? 5 : 3) + 5 + 4 + (wedge_mode == 1 ? 6 : 2) + 1 + 1;
+int64_t kernels_per_call(bool bins, int wedge_mode) {
+    return 3 + 1 + (bins ? 5 : 3) + 5 + 4 + (wedge_mode == 1 ? 6 : 2) + 1 + 1;
 }
 
 void set_err(ef_ctx *c, const char *fmt, ...) {
@@ -225,8 +225,7 @@ struct Job {
 int part_a(ef_ctx *ctx, const Job &j, const ef::Scratch &s, cudaStream_t st) {
     using namespace ef;
     CU(cudaMemsetAsync(s.Tacc, 0, accumulator_bytes(s), st));
-    LAUNCH(launch_prep_a(j.rp, j.ci, j.n, j.m, s, ctx->tune, st), "prep");
-    if (j.goff_dev) LAUNCH(launch_batch_check(j.rp, j.ci, j.n, j.m, j.goff_dev, j.G, s, ctx->tune, st), "batch check");
+    LAUNCH(launch_prep_a(j.rp, j.ci, j.n, j.m, s, ctx->tune, st, j.goff_dev, j.G), "prep");
     return EF_OK;
 }
 
@@ -374,7 +373,7 @@ int check_args(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_opti
 
 // Events: 0 start, 1 part B start (after the validation readback), 2..6
 // after orientation, small wedges, big wedges, hash tables, pair tests, 7 end.
-void accumulate_stats(ef_ctx *ctx, bool batched, int wedge_mode) {
+void accumulate_stats(ef_ctx *ctx, int wedge_mode) {
     auto el = [&](int a, int b) {
         float t = 0.f;
         return cudaEventElapsedTime(&t, ctx->ev[a], ctx->ev[b]) == cudaSuccess ? (double)t : 0.0;
@@ -388,7 +387,7 @@ void accumulate_stats(ef_ctx *ctx, bool batched, int wedge_mode) {
     st.tri_pairs_ms += el(4, 6);
     st.finalize_ms += el(6, 7);
     st.total_ms += el(0, 7);
-    st.kernels += kernels_per_call(batched, ctx->bins, wedge_mode);
+    st.kernels += kernels_per_call(ctx->bins, wedge_mode);
 }
 
 // Host I/O and synchronisation around compute_device.
@@ -432,7 +431,7 @@ int run_job(ef_ctx *ctx, Job j, const ef_outputs *host_out) {
     if (rc) return rc;
     if (!j.o.async) {
         CU(cudaStreamSynchronize(ctx->stream));
-        if (j.o.profile) accumulate_stats(ctx, j.goff_dev != nullptr, j.o.wedge_mode);
+        if (j.o.profile) accumulate_stats(ctx, j.o.wedge_mode);
     }
     CU(cudaGetLastError());
     return EF_OK;

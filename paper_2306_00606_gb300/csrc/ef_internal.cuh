@@ -425,8 +425,10 @@ struct RankScratch {
 
 // ------------------------------------------------------------ launchers
 namespace ef {
+// goff, G: a batch's G + 1 graph node offsets on the device (the row pass
+// then also checks that no entry leaves its row's graph), else nullptr.
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
-                  cudaStream_t st);
+                  cudaStream_t st, const int64_t *goff = nullptr, int32_t G = 0);
 // The out-lists in degree-bin order (bins) or node order.
 // With tables, also the hash tables of the out-lists longer than SHORT_MAX
 // (cleared here, filled as the lists are written).
@@ -434,8 +436,6 @@ int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
                   cudaStream_t st, int32_t *nmin = nullptr, int32_t *nmax = nullptr, bool bins = true,
                   bool tables = true);
 int launch_big_items(const Scratch &s, int32_t n, cudaStream_t st);
-int launch_batch_check(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const int64_t *goff, int32_t G,
-                       const Scratch &s, const Tune &t, cudaStream_t st);
 int prepare_kernels();
 int prepare_final_tables();   // ln table of the finalize (ef_final.cu), once per device
 int64_t device_l2_bytes();   // of the current device (after prepare_kernels ran on it)

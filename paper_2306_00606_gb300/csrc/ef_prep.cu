@@ -99,51 +99,73 @@ __device__ __forceinline__ int warp_bin_slot(int *s_cnt, int b) {
     return p;
 }
 
-// Thread per node: D, max degree, row_ptr checks, and the wedge bins (they
-// depend on D only): small sub-warp bins, or "big" plus the mid list or a
-// hub bucket.  Block-level counting in shared memory, one global atomic per
-// bin per block.
-__global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, int hub_min,
-                          int32_t *__restrict__ D, int32_t *__restrict__ bins, int32_t *__restrict__ cnt) {
+// D, max degree, row_ptr checks, and the wedge bins (they depend on D
+// only): small sub-warp bins, or "big" plus the mid list or a hub bucket.
+// A thread takes DEG_PER nodes, blockDim apart; block-level counting in
+// shared memory, one global atomic per bin per block.  (A node per thread in
+// blocks of 1024 ran in waves of tiny blocks whose phases -- loads, shared
+// counts, global slot atomics, stores -- did not overlap: 0.37 ms for the
+// WS batch's 41M nodes.)
+constexpr int DEG_THREADS = 256, DEG_PER = 8;
+
+__global__ void __launch_bounds__(DEG_THREADS) k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m,
+                                                         int hub_min, int32_t *__restrict__ D,
+                                                         int32_t *__restrict__ bins, int32_t *__restrict__ cnt) {
     __shared__ int s_cnt[NUM_BINS], s_base[NUM_BINS];
     __shared__ int s_mx[32], s_err[32], s_blo[32], s_bhi[32];
     if (threadIdx.x < NUM_BINS) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    int mx = 0, err = 0, b0 = -1, b1 = -1, p0 = 0, p1 = 0, blo = 0, bhi = 0;
-    if (v < n) {
-        const int a = rp[v], b = rp[v + 1];
-        int d = 0;
-        if (a < 0 || b < a || (int64_t)b > m) err |= ERRB_ROWPTR;
-        else d = b - a;
-        D[v] = d;
-        mx = d;
-        if (d >= 1 && d <= SMALL_MAX) {
-            b0 = d <= 4 ? BIN_S4 : d <= 8 ? BIN_S8 : d <= 16 ? BIN_S16 : BIN_S32;
-        } else if (d > SMALL_MAX) {
-            b0 = BIN_BIG;
-            blo = n - 1 - v;
-            bhi = v;
-            if (d < hub_min) {
-                b1 = BIN_MID;
-            } else {
-                const int lg = 31 - __clz(d);   // floor(log2 d)
-                b1 = BIN_HUB0 + max(0, min(lg - 9, NUM_HUB_BUCKETS - 1));
+    const int64_t v0 = (int64_t)blockIdx.x * DEG_THREADS * DEG_PER + threadIdx.x;
+    int mx = 0, err = 0, blo = 0, bhi = 0;
+    int ra[DEG_PER], rb[DEG_PER];
+#pragma unroll
+    for (int q = 0; q < DEG_PER; ++q) {
+        const int64_t v = v0 + q * DEG_THREADS;
+        ra[q] = v < n ? rp[v] : 0;
+        rb[q] = v < n ? rp[v + 1] : 0;
+    }
+    int b0[DEG_PER], b1[DEG_PER];
+#pragma unroll
+    for (int q = 0; q < DEG_PER; ++q) {
+        const int64_t v = v0 + q * DEG_THREADS;
+        b0[q] = -1;
+        b1[q] = -1;
+        if (v < n) {
+            const int a = ra[q], b = rb[q];
+            int d = 0;
+            if (a < 0 || b < a || (int64_t)b > m) err |= ERRB_ROWPTR;
+            else d = b - a;
+            D[v] = d;
+            mx = max(mx, d);
+            if (d >= 1 && d <= SMALL_MAX) {
+                b0[q] = d <= 4 ? BIN_S4 : d <= 8 ? BIN_S8 : d <= 16 ? BIN_S16 : BIN_S32;
+            } else if (d > SMALL_MAX) {
+                b0[q] = BIN_BIG;
+                blo = max(blo, (int)(n - 1 - v));
+                bhi = max(bhi, (int)v);
+                if (d < hub_min) {
+                    b1[q] = BIN_MID;
+                } else {
+                    const int lg = 31 - __clz(d);   // floor(log2 d)
+                    b1[q] = BIN_HUB0 + max(0, min(lg - 9, NUM_HUB_BUCKETS - 1));
+                }
             }
         }
     }
-    if (v == 0 && (rp[0] != 0 || (int64_t)rp[n] != m)) err |= ERRB_ROWPTR;
+    if (v0 == 0 && (rp[0] != 0 || (int64_t)rp[n] != m)) err |= ERRB_ROWPTR;
     // positions in the block's bins: one shared atomic per bin and warp
-    // (lattices put a whole block in one or two bins)
-    p0 = warp_bin_slot(s_cnt, b0);
-    p1 = warp_bin_slot(s_cnt, b1);
+    // (lattices put a whole block in one or two bins); bin << 16 | position
+    // (< DEG_THREADS * DEG_PER), or -1
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(FULL, mx, o));
-        err |= __shfl_xor_sync(FULL, err, o);
-        blo = max(blo, __shfl_xor_sync(FULL, blo, o));
-        bhi = max(bhi, __shfl_xor_sync(FULL, bhi, o));
+    for (int q = 0; q < DEG_PER; ++q) {
+        const int p0 = warp_bin_slot(s_cnt, b0[q]), p1 = warp_bin_slot(s_cnt, b1[q]);
+        b0[q] = b0[q] >= 0 ? b0[q] << 16 | p0 : -1;
+        b1[q] = b1[q] >= 0 ? b1[q] << 16 | p1 : -1;
     }
+    mx = __reduce_max_sync(FULL, mx);
+    err = __reduce_or_sync(FULL, err);
+    blo = __reduce_max_sync(FULL, blo);
+    bhi = __reduce_max_sync(FULL, bhi);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) {
         s_mx[w] = mx;
@@ -157,15 +179,11 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
     if (w == 0) {
         // one global atomic per statistic and block (the same few addresses
         // for every block: per-warp atomics there cost 0.07 ms at n = 4M)
-        const int nw = blockDim.x >> 5;
-        mx = l < nw ? s_mx[l] : 0;
-        err = l < nw ? s_err[l] : 0;
-        blo = l < nw ? s_blo[l] : 0;
-        bhi = l < nw ? s_bhi[l] : 0;
-        mx = __reduce_max_sync(FULL, mx);
-        err = __reduce_or_sync(FULL, err);
-        blo = __reduce_max_sync(FULL, blo);
-        bhi = __reduce_max_sync(FULL, bhi);
+        constexpr int nw = DEG_THREADS / 32;
+        mx = __reduce_max_sync(FULL, l < nw ? s_mx[l] : 0);
+        err = __reduce_or_sync(FULL, l < nw ? s_err[l] : 0);
+        blo = __reduce_max_sync(FULL, l < nw ? s_blo[l] : 0);
+        bhi = __reduce_max_sync(FULL, l < nw ? s_bhi[l] : 0);
         if (l == 0) {
             if (mx) atomicMax(cnt + CNT_MAXDEG, mx);
             if (err) atomicOr(cnt + CNT_ERR, err);
@@ -174,8 +192,12 @@ __global__ void k_degrees(const int32_t *__restrict__ rp, int32_t n, int64_t m, 
         }
     }
     __syncthreads();
-    if (b0 >= 0) bins[(size_t)b0 * n + s_base[b0] + p0] = v;
-    if (b1 >= 0) bins[(size_t)b1 * n + s_base[b1] + p1] = v;
+#pragma unroll
+    for (int q = 0; q < DEG_PER; ++q) {
+        const int v = (int)(v0 + q * DEG_THREADS);
+        if (b0[q] >= 0) bins[(size_t)(b0[q] >> 16) * n + s_base[b0[q] >> 16] + (b0[q] & 0xffff)] = v;
+        if (b1[q] >= 0) bins[(size_t)(b1[q] >> 16) * n + s_base[b1[q] >> 16] + (b1[q] & 0xffff)] = v;
+    }
 }
 
 // Row order of the one-thread row passes (k_row_stats, k_orient), decided on
@@ -270,7 +292,22 @@ struct RowStats {
 struct RowOut {
     int64_t *sig1, *sig2;
     int32_t *outdeg;
+    const int64_t *goff;   // batched input: G + 1 node offsets of the graphs (else nullptr)
+    int32_t G;
 };
+
+// Batched input: every entry of row v must lie in v's own graph
+// [goff[g], goff[g + 1]).  The row pass checks that rows ascend, so the
+// first and last entries decide (a < b).
+__device__ __forceinline__ int cross_bits(const RowOut &ro, const int32_t *__restrict__ ci, int64_t v, int a, int b) {
+    if (!ro.goff || b <= a) return 0;
+    int lo = 0, hi = ro.G - 1;   // last g with goff[g] <= v
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ro.goff[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return ci[a] < ro.goff[lo] || ci[b - 1] >= ro.goff[lo + 1] ? ERRB_CROSS : 0;
+}
 
 __device__ __forceinline__ void add_sym(int32_t *cnt, uint64_t sym) {
     sym = warp_sum(sym);
@@ -293,7 +330,8 @@ __device__ __forceinline__ void row_stats_warp(const int32_t *__restrict__ ci, c
         ro.sig1[u] = s1;
         ro.sig2[u] = s2;
         ro.outdeg[u] = od;
-        if (err) atomicOr(cnt + CNT_ERR, err);
+        const int e2 = err | cross_bits(ro, ci, u, ua, ub);
+        if (e2) atomicOr(cnt + CNT_ERR, e2);
     }
 }
 
@@ -321,7 +359,10 @@ __global__ void __launch_bounds__(256, 6) k_row_stats(const int32_t *__restrict_
         const int Dv = ok ? b - a : 0;
         if (in && Dv <= tmax) {
             RowStats r;
-            if (ok) r.row(ci, D, n, v, Dv, a, b);
+            if (ok) {
+                r.row(ci, D, n, v, Dv, a, b);
+                r.err |= cross_bits(ro, ci, v, a, b);
+            }
             ro.sig1[v] = r.s1;
             ro.sig2[v] = r.s2;
             ro.outdeg[v] = r.od;
@@ -380,6 +421,7 @@ __global__ void __launch_bounds__(ROW_CTA) k_row_stats_hub(const int32_t *__rest
             ro.sig1[u] = s1;
             ro.sig2[u] = s2;
             ro.outdeg[u] = (int32_t)od;
+            if (const int e2 = cross_bits(ro, ci, u, a, b)) atomicOr(cnt + CNT_ERR, e2);
         }
     }
     add_sym(cnt, sym);
@@ -925,9 +967,10 @@ static inline unsigned grid_for(int64_t work, int per_block, int64_t cap) {
 
 // Degrees + wedge bins, per-row checks and neighbour sums.
 int launch_prep_a(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s, const Tune &t,
-                  cudaStream_t st) {
-    k_degrees<<<grid_for(n, 1024, 1 << 30), 1024, 0, st>>>(rp, n, m, t.hub_min, s.D, s.bins, s.counters);
-    const RowOut ro{s.sig1, s.sig2, s.outdeg};
+                  cudaStream_t st, const int64_t *goff, int32_t G) {
+    k_degrees<<<grid_for(n, DEG_THREADS * DEG_PER, 1 << 30), DEG_THREADS, 0, st>>>(rp, n, m, t.hub_min, s.D, s.bins,
+                                                                                 s.counters);
+    const RowOut ro{s.sig1, s.sig2, s.outdeg, goff, G};
     k_row_stats<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, ci, n, m, t.row_thread_max, t.hub_min, s.D, s.bins,
                                                          rows_in_bins_allowed(m), ro, s.counters);
     k_row_stats_hub<<<t.num_sms * 4, ROW_CTA, 0, st>>>(rp, ci, n, s.D, s.bins, ro, s.counters);
@@ -966,45 +1009,6 @@ int launch_orient(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, co
         k_hash_rows<<<(unsigned)(t.num_sms * 8), 256, 0, st>>>(rp, n, m, t.row_thread_max, s.bins + (size_t)BIN_BIG * n,
                                                                s.counters, s.info, s.out_ptr, s.outdeg, s.out_col,
                                                                s.out_hash);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
-
-// Batched input: every entry of row v must lie in v's own graph
-// [goff[g], goff[g+1]).  Rows are checked to be strictly ascending by the row
-// pass, so the first and last entries decide.
-__global__ void k_batch_check(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int32_t n, int64_t m,
-                              const int64_t *__restrict__ goff, int32_t G, int32_t *__restrict__ cnt) {
-    // a warp takes 32 consecutive rows: one binary search for the graph of the
-    // first (by lane 0), then each lane steps forward to its own graph
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    int err = 0;
-    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
-         base += nwarps * 32) {
-        int g0 = 0;
-        if (lane == 0) {
-            int lo = 0, hi = G - 1;   // last g with goff[g] <= base
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (goff[mid] <= base) lo = mid; else hi = mid - 1;
-            }
-            g0 = lo;
-        }
-        int g = __shfl_sync(FULL, g0, 0);
-        const int64_t v = base + lane;
-        if (v < n) {
-            while (g + 1 < G && goff[g + 1] <= v) ++g;
-            const int a = rp[v], b = rp[v + 1];   // bad row pointers are reported by k_degrees
-            if (a >= 0 && a < b && (int64_t)b <= m && (ci[a] < goff[g] || ci[b - 1] >= goff[g + 1])) err |= ERRB_CROSS;
-        }
-    }
-    err = __reduce_or_sync(FULL, err);
-    if ((threadIdx.x & 31) == 0 && err) atomicOr(cnt + CNT_ERR, err);
-}
-
-int launch_batch_check(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const int64_t *goff, int32_t G,
-                       const Scratch &s, const Tune &t, cudaStream_t st) {
-    k_batch_check<<<t.grid((int64_t)n, 256), 256, 0, st>>>(rp, ci, n, m, goff, G, s.counters);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

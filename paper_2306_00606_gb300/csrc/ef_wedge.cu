@@ -28,6 +28,14 @@ namespace ef {
 // distinct (degree, degree) pairs than ordered neighbour pairs: small wedges
 // 3.50 -> 4.44 ms there, 0.30 -> 0.51 ms on the power-law graph (the match
 // and two indexed shuffles per class cost more than the pairs they save).
+//
+// A warp step takes SMALL_ILP sets of 32 / G rows and issues their chains of
+// dependent loads (work list -> degree and row start -> neighbour -> its
+// degree) together.  FP32C, small wedges (ms) with 1 / 2 / 3 sets: WS batch
+// 3.25 / 2.93 / 2.92, BA 16M 2.83 / 2.82 / 2.73, power-law 4M 0.283 / 0.286 /
+// 0.288; three sets take 37-40 registers instead of 32.
+constexpr int SMALL_ILP = 2;
+
 template <int G, bool F64>
 __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                                      const int32_t *__restrict__ D, const int32_t *__restrict__ list,
@@ -35,51 +43,82 @@ __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__
                                                      const float2 *__restrict__ ftab, double *__restrict__ Tacc,
                                                      void *__restrict__ Ccenter) {
     using Acc = typename std::conditional<F64, double, float>::type;
-    constexpr int PER = 32 / G;
+    constexpr int PER = 32 / G, ILP = SMALL_ILP;
     const int lane = threadIdx.x & 31, grp = lane / G, k = lane % G;
     const int count = cnt[bin];
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * PER; base < count;
-         base += nwarps * PER) {
-        const int64_t idx = base + grp;
-        const bool vc = idx < count;
-        const int u = vc ? list[idx] : 0;
-        const int Du = vc ? D[u] : 0;
-        const int start = vc ? rp[u] : 0;
-        const bool own = k < Du;
-        const int x = own ? ci[start + k] : 0;
-        const int ak = own ? D[x] : 0;
-        const int b0 = Du - 4 + ak;
-        Acc acc = 0;
-        // the warp's largest row bounds the loop (rows of a bin are often
-        // much shorter than G); degrees travel as floats (exact below 2^24),
-        // so no conversion sits in the loop
-        const int jmax = __reduce_max_sync(FULL, Du);
-        if constexpr (F64) {
-            // at most 31 terms: one FP32-pair chunk (F2Sum)
-            F2Sum a2;
-#pragma unroll 4
-            for (int j = 0; j < jmax; ++j) {
-                const int aj = __shfl_sync(FULL, ak, j, G);
-                if (own && j < Du && j != k) a2.add(__ldg(ftab + (b0 + aj)));   // b0 + aj >= 0 for D_u >= 2
-            }
-            acc = a2.value();
-        } else {
-            // d = D_u - 4 + D_x + D_j >= 3 once D_u > 4 (G >= 8): only the
-            // smallest bin needs the guard that keeps d = 0 from 0 * log2(0)
-            const float akf = (float)ak, b0f = (float)b0;
-            const int lim = own ? Du : 0;
-#pragma unroll 4
-            for (int j = 0; j < jmax; ++j) {
-                const float d = b0f + __shfl_sync(FULL, akf, j, G);
-                const float t = dlog2d(G == 4 ? fmaxf(d, 1.0f) : d);
-                if (j < lim && j != k) acc += t;
-            }
+    for (int64_t base0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * PER * ILP; base0 < count;
+         base0 += nwarps * PER * ILP) {
+        int us[ILP], Dus[ILP], xs[ILP], aks[ILP];
+#pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+            const int64_t idx = base0 + r * PER + grp;
+            us[r] = idx < count ? list[idx] : -1;
         }
-        const Acc r = own ? (F64 ? acc : acc * (Acc)LN2) : (Acc)0;
-        if (own) credit_end(Tacc, x, (double)r);
-        const Acc c = group_sum<G>(r);
-        if (k == 0 && vc) reinterpret_cast<Acc *>(Ccenter)[u] = c;
+        int sts[ILP];
+#pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+            Dus[r] = us[r] >= 0 ? D[us[r]] : 0;
+            sts[r] = us[r] >= 0 ? rp[us[r]] : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < ILP; ++r) xs[r] = k < Dus[r] ? ci[sts[r] + k] : 0;
+#pragma unroll
+        for (int r = 0; r < ILP; ++r) aks[r] = k < Dus[r] ? D[xs[r]] : 0;
+#pragma unroll
+        for (int r = 0; r < ILP; ++r) {
+            const bool vc = us[r] >= 0;
+            const int u = vc ? us[r] : 0;
+            const int Du = Dus[r];
+            const bool own = k < Du;
+            const int x = xs[r];
+            const int ak = aks[r];
+            const int b0 = Du - 4 + ak;
+            Acc acc = 0;
+            // the warp's largest row bounds the loop (rows of a bin are often
+            // much shorter than G); degrees travel as floats (exact below 2^24),
+            // so no conversion sits in the loop
+            const int jmax = __reduce_max_sync(FULL, Du);
+            if constexpr (F64) {
+                // at most 31 terms: one FP32-pair chunk (F2Sum)
+                F2Sum a2;
+#pragma unroll 4
+                for (int j = 0; j < jmax; ++j) {
+                    const int aj = __shfl_sync(FULL, ak, j, G);
+                    if (own && j < Du && j != k) a2.add(__ldg(ftab + (b0 + aj)));   // b0 + aj >= 0 for D_u >= 2
+                }
+                acc = a2.value();
+            } else {
+                // One FMA per term.  Up to the warp's shortest row every lane's
+                // terms are real, so that loop adds without a test; the rest of
+                // the rows (jmin..jmax) add under j < D_u.  Both include the
+                // lane's own term j = k once, removed at the end (one of D_u
+                // positive terms).  d = D_u - 4 + D_x + D_j >= 3 once D_u > 4
+                // (G >= 8): only the smallest bin needs the guard that keeps d = 0
+                // from 0 * log2(0)
+                const float akf = (float)ak, b0f = (float)b0;
+                const int jmin = __reduce_min_sync(FULL, vc ? Du : G);
+                const int lim = own ? Du : 0;
+                float sum = 0.0f;
+#pragma unroll 4
+                for (int j = 0; j < jmin; ++j) {
+                    float d = b0f + __shfl_sync(FULL, akf, j, G);
+                    if (G == 4) d = fmaxf(d, 1.0f);
+                    sum = fmaf(d, __log2f(d), sum);
+                }
+                for (int j = jmin; j < jmax; ++j) {
+                    float d = b0f + __shfl_sync(FULL, akf, j, G);
+                    if (G == 4) d = fmaxf(d, 1.0f);
+                    const float t = __log2f(d);
+                    if (j < lim) sum = fmaf(d, t, sum);
+                }
+                acc = sum - dlog2d(G == 4 ? fmaxf(b0f + akf, 1.0f) : b0f + akf);
+            }
+            const Acc rs = own ? (F64 ? acc : acc * (Acc)LN2) : (Acc)0;
+            if (own) credit_end(Tacc, x, (double)rs);
+            const Acc c = group_sum<G>(rs);
+            if (k == 0 && vc) reinterpret_cast<Acc *>(Ccenter)[u] = c;
+        }
     }
 }
 
