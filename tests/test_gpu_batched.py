@@ -150,6 +150,21 @@ def test_batched_rejects_edge_between_graphs(ctx):
     run_batched(ctx, u, np.array([0, 20, 50], dtype=np.int64), "fp64")   # the right cut passes
 
 
+@pytest.mark.parametrize("leaves", [100, 3000])
+def test_batched_rejects_edge_between_graphs_at_big_rows(ctx, leaves):
+    """The cross-graph check where a warp (degree 101) or a block (degree 3001) walks the row: two
+    stars whose centres are joined, cut between the centres, so that the centres' rows hold the
+    only entries outside their graph."""
+    import paper_2306_00606_gb300 as ef
+    c1, c2 = leaves, leaves + 1
+    edges = [(i, c1) for i in range(leaves)] + [(c1, c2)] + [(c2, c2 + 1 + i) for i in range(leaves)]
+    g = synth.from_edges(2 * leaves + 2, edges)
+    with pytest.raises(ef.EfError) as ei:
+        run_batched(ctx, g, np.array([0, c2, 2 * leaves + 2], dtype=np.int64), "fp64")
+    assert ei.value.code == ef.EF_ERR_GRAPH and "between-graphs" in ef.ef_last_error(ctx.handle)
+    run_batched(ctx, g, np.array([0, 2 * leaves + 2], dtype=np.int64), "fp64")
+
+
 def test_batched_rejects_bad_offsets(ctx):
     import paper_2306_00606_gb300 as ef
     u = synth.cycle(10)
