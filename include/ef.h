@@ -86,8 +86,13 @@ typedef struct {
     int32_t trust_input;   /* 1: skip CSR validation (and its host sync) */
     int32_t host_io;       /* 1: graph and outputs are host pointers; the
                               library copies them in and out */
-    int32_t async;         /* 1 (device I/O and trust_input only): return
-                              without waiting; results valid after ef_sync */
+    int32_t async;         /* 1: return once the work is queued on the
+                              context stream (with validation, after its
+                              readback midway); results, in device or host
+                              buffers, are valid after ef_sync, and host
+                              buffers must stay valid and unchanged until
+                              then.  Two contexts on two streams then overlap
+                              one call's copies with another's kernels. */
     int32_t profile;       /* 1: time each pass with CUDA events on the
                               context stream (read with ef_get_stats) */
     int32_t wedge_mode;    /* 0: automatic (degree-class kernels for middle

@@ -360,7 +360,6 @@ int compute_device(ef_ctx *ctx, const Job &j) {
 
 int check_opts(ef_ctx *ctx, const ef_options &o) {
     if (o.precision != EF_PREC_FP64 && o.precision != EF_PREC_FP32C) { set_err(ctx, "bad precision %d", o.precision); return EF_ERR_ARG; }
-    if (o.async && (o.host_io || !o.trust_input)) { set_err(ctx, "async needs device I/O and trust_input"); return EF_ERR_ARG; }
     return EF_OK;
 }
 

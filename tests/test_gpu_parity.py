@@ -321,6 +321,36 @@ def test_host_io_matches_device(ctx):
     np.testing.assert_allclose(host["ef"], dev["ef"], rtol=1e-13, atol=1e-13)
 
 
+def test_async_calls_match_synchronous(ctx):
+    """async = 1: device I/O without validation, and host I/O with validation on two contexts whose
+    calls alternate (one call's copies beside the other's kernels); every result read after
+    ef_sync equals the synchronous call's."""
+    import torch
+    import paper_2306_00606_gb300 as ef
+    g = synth.barabasi_albert(20000, 4, 5)
+    ref = run(ctx, g, "fp64")
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    ci = torch.from_numpy(g.col_idx).cuda()
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    ef.ef_compute_ex(ctx.handle, rp, ci, precision="fp64", trust_input=True, async_=True, ef=out)
+    ef.ef_sync(ctx.handle)
+    np.testing.assert_allclose(out.cpu().numpy(), ref["ef"], rtol=1e-13, atol=1e-13)
+    h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+    h_ci = torch.from_numpy(g.col_idx).pin_memory()
+    outs = [torch.zeros(g.n, dtype=torch.float64).pin_memory() for _ in range(4)]
+    s_out = [torch.zeros(g.n, dtype=torch.int64).pin_memory() for _ in range(4)]
+    with ef.Context(0, torch.cuda.Stream()) as ctx2:
+        ctxs = (ctx, ctx2)
+        for i in range(4):
+            ef.ef_compute_ex(ctxs[i % 2].handle, h_rp, h_ci, precision="fp64", host_io=True, async_=True,
+                             ef=outs[i], s=s_out[i])
+        ef.ef_sync(ctx.handle)
+        ef.ef_sync(ctx2.handle)
+    for i in range(4):
+        assert np.array_equal(s_out[i].numpy(), ref["s"])
+        np.testing.assert_allclose(outs[i].numpy(), ref["ef"], rtol=1e-13, atol=1e-13)
+
+
 def test_plain_ef_compute_entry(ctx):
     import torch
     import paper_2306_00606_gb300 as ef
