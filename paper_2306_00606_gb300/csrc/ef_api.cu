@@ -542,7 +542,8 @@ int rank_buffers(ef_ctx *ctx, int32_t n, ef::RankScratch &r) {
 // ranking needs anyway for its triangles) instead of the lighter omega pass;
 // the orientation always builds the hash tables, since triangles follow.
 int features_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, int mode,
-                    const ef::Scratch &s, ef::RankScratch r, float *x, bool with_orient = false) {
+                    const ef::Scratch &s, ef::RankScratch r, float *x, bool with_orient = false,
+                    const ef::ModelDev *std_model = nullptr) {
     using namespace ef;
     cudaStream_t st = ctx->stream;
     if (with_orient || mode == 1)
@@ -551,7 +552,7 @@ int features_device(ef_ctx *ctx, const int32_t *rp, const int32_t *ci, int32_t n
         LAUNCH(launch_omega_mm(rp, ci, n, m, s, r, ctx->tune, st), "omega");
     if (mode == 1) LAUNCH(launch_tri_pairs(s, n, m, ctx->tune, st), "triangle");
     r.x = x;
-    LAUNCH(launch_features(s, r, n, mode, ctx->tune, st), "features");
+    LAUNCH(launch_features(s, r, n, mode, ctx->tune, st, std_model), "features");
     return EF_OK;
 }
 
@@ -1389,10 +1390,13 @@ int ef_surrogate_rank(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const 
     RankScratch r;
     rc = rank_buffers(ctx, n, r);
     if (rc) return rc;
-    rc = features_device(ctx, g->row_ptr, g->col_idx, n, m, model->feature_mode, s, r, r.x, true);
+    // the features go out standardised and in BF16 (the network's operand),
+    // half the bytes of the FP32 rows that ef_features returns
+    rc = features_device(ctx, g->row_ptr, g->col_idx, n, m, model->feature_mode, s, r, r.x, true, model->d);
     if (rc) return rc;
     CU(cudaEventRecord(ctx->ev[1], st));
-    LAUNCH(launch_mlp_infer(model->d, r.x, n, r.score, ctx->num_sms, st), "network");
+    LAUNCH(launch_mlp_infer_bf16(model->d, reinterpret_cast<const uint32_t *>(r.x), n, r.score, ctx->num_sms, st),
+           "network");
     if (out_score) CU(cudaMemcpyAsync(out_score, r.score, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     CU(cudaEventRecord(ctx->ev[2], st));
     // candidates, audit sample, their union

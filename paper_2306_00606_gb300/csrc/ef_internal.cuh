@@ -24,6 +24,7 @@
 // point) and tcnt the same way.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -367,6 +368,12 @@ __device__ __forceinline__ double f2_value(float2 t) { return (double)t.x + (dou
 // d * log2(d) for integral d >= 1 held in a float (MUFU lg2).
 __device__ __forceinline__ float dlog2d(float d) { return d * __log2f(d); }
 
+// Two floats rounded to BF16 (nearest, ties to even), lo in the low half.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
 // Credit R_u(x) of middle node u to its end x (an L2 reduction, no return).
 __device__ __forceinline__ void credit_end(double *Tacc, int x, double r) { atomicAdd(Tacc + x, r); }
 
@@ -457,6 +464,11 @@ int launch_finalize(const Scratch &s, int precision, int32_t n, const ef_outputs
                     cudaStream_t st);
 // learned path (ef_mlp.cu, ef_rank.cu)
 int launch_mlp_infer(const ModelDev *M, const float *x, int32_t n, float *out, int num_sms, cudaStream_t st);
+// The same network on rows already standardised and rounded to BF16 (8
+// words of two features per row, as launch_features writes them with a
+// model): the same predictions, half the bytes read.
+int launch_mlp_infer_bf16(const ModelDev *M, const uint32_t *xb, int32_t n, float *out, int num_sms,
+                          cudaStream_t st);
 int launch_mlp_step(ModelDev *M, const float *x, const float *y, int32_t n, int32_t batch, uint64_t seed, bool sample,
                     bool count_step, bool adam, float lr, uint16_t *acts, int num_sms, cudaStream_t st);
 size_t mlp_act_bytes(int32_t batch);
@@ -464,7 +476,10 @@ int launch_model_pack(ModelDev *M, cudaStream_t st);
 int launch_feature_stats(const float *x, int32_t n, ModelDev *M, double *tmp, cudaStream_t st);
 int launch_omega_mm(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, const Scratch &s,
                     const RankScratch &r, const Tune &t, cudaStream_t st);
-int launch_features(const Scratch &s, const RankScratch &r, int32_t n, int mode, const Tune &t, cudaStream_t st);
+// std_model: write the rows standardised with that model's statistics and
+// rounded to BF16 into r.x (8 words per row) instead of FP32 features.
+int launch_features(const Scratch &s, const RankScratch &r, int32_t n, int mode, const Tune &t, cudaStream_t st,
+                    const ModelDev *std_model = nullptr);
 int launch_select_top(const RankScratch &r, int32_t n, int64_t k, int bits, const Tune &t, cudaStream_t st);
 int launch_bin_nodes(const int32_t *list, int32_t k, const int32_t *kptr, const int32_t *rp, const int32_t *ci,
                      const Scratch &s, int32_t *mark, int32_t n, const Tune &t, cudaStream_t st);

@@ -26,11 +26,6 @@
 
 namespace ef {
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-
 __device__ __forceinline__ float bf16_to_float(uint16_t u) { return __uint_as_float((uint32_t)u << 16); }
 
 __device__ __forceinline__ uint32_t pair_u16(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
@@ -103,6 +98,7 @@ __device__ __forceinline__ RowPart load_row(const float *x) {
 }
 
 __device__ __forceinline__ void tile_forward(const MlpSmem &s, RowPart rg, RowPart rg8, bool vg, bool vg8, Tile &T);
+__device__ __forceinline__ void tile_layers(const MlpSmem &s, Tile &T);
 
 __device__ __forceinline__ void tile_forward(const MlpSmem &s, const float *xg, const float *xg8, Tile &T) {
     tile_forward(s, load_row(xg), load_row(xg8), xg != nullptr, xg8 != nullptr, T);
@@ -125,6 +121,12 @@ __device__ __forceinline__ void tile_forward(const MlpSmem &s, RowPart rg, RowPa
     T.a1[1] = pack_bf16(z[1][0], z[1][1]);
     T.a1[2] = pack_bf16(z[0][2], z[0][3]);
     T.a1[3] = pack_bf16(z[1][2], z[1][3]);
+    tile_layers(s, T);
+}
+
+// Layers 1-3 of a tile whose first-layer operand T.a1 is set.
+__device__ __forceinline__ void tile_layers(const MlpSmem &s, Tile &T) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int n = 8 * j + g;
@@ -196,6 +198,46 @@ __global__ void __launch_bounds__(MLP_WARPS * 32, 4) k_mlp_infer(const ModelDev 
         }
         Tile T;
         tile_forward(s, ca, cb, r0 < n, r1 < n, T);
+        if (t == 0) {
+            if (r0 < n) out[r0] = T.p0;
+            if (r1 < n) out[r1] = T.p1;
+        }
+    }
+}
+
+// Inference on standardised BF16 rows (8 words per row, word q holding
+// features 2q and 2q + 1): lane (g, t) reads words t and t + 4 of rows g and
+// g + 8, which are the first-layer A fragment as it is, so the predictions
+// equal k_mlp_infer's on the FP32 rows bit for bit.
+__global__ void __launch_bounds__(MLP_WARPS * 32, 4) k_mlp_infer_bf16(const ModelDev *__restrict__ M,
+                                                                   const uint32_t *__restrict__ Xb, int32_t n,
+                                                                   float *__restrict__ out) {
+    __shared__ MlpSmem s;
+    load_model(M, s, false);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
+    const int64_t tiles = ((int64_t)n + 15) / 16;
+    const int64_t step = (int64_t)gridDim.x * MLP_WARPS;
+    auto word = [&](int64_t r, int q) { return r < n ? __ldg(Xb + r * (MLP_F / 2) + q) : 0u; };
+    int64_t tile = (int64_t)blockIdx.x * MLP_WARPS + w;
+    // the next tile's words are loaded before the current tile is computed
+    uint32_t a0 = word(tile * 16 + g, t), a1 = word(tile * 16 + g + 8, t);
+    uint32_t a2 = word(tile * 16 + g, t + 4), a3 = word(tile * 16 + g + 8, t + 4);
+    for (; tile < tiles; tile += step) {
+        const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+        Tile T;
+        T.a1[0] = a0;
+        T.a1[1] = a1;
+        T.a1[2] = a2;
+        T.a1[3] = a3;
+        const int64_t nx = tile + step;
+        if (nx < tiles) {
+            a0 = word(nx * 16 + g, t);
+            a1 = word(nx * 16 + g + 8, t);
+            a2 = word(nx * 16 + g, t + 4);
+            a3 = word(nx * 16 + g + 8, t + 4);
+        }
+        tile_layers(s, T);
         if (t == 0) {
             if (r0 < n) out[r0] = T.p0;
             if (r1 < n) out[r1] = T.p1;
@@ -493,6 +535,16 @@ int launch_mlp_infer(const ModelDev *M, const float *x, int32_t n, float *out, i
     if (g > (int64_t)num_sms * 8) g = (int64_t)num_sms * 8;
     if (g < 1) g = 1;
     k_mlp_infer<<<(unsigned)g, MLP_WARPS * 32, 0, st>>>(M, x, n, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_mlp_infer_bf16(const ModelDev *M, const uint32_t *xb, int32_t n, float *out, int num_sms,
+                          cudaStream_t st) {
+    const int64_t tiles = ((int64_t)n + 15) / 16;
+    int64_t g = (tiles + MLP_WARPS - 1) / MLP_WARPS;
+    if (g > (int64_t)num_sms * 8) g = (int64_t)num_sms * 8;
+    if (g < 1) g = 1;
+    k_mlp_infer_bf16<<<(unsigned)g, MLP_WARPS * 32, 0, st>>>(M, xb, n, out);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

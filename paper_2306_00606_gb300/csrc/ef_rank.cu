@@ -137,11 +137,24 @@ int launch_omega_mm(const int32_t *rp, const int32_t *ci, int32_t n, int64_t m, 
 }
 
 // The 16 features of every node (in the order of the oracle's FEATURE_NAMES).
-// mode 1 uses the triangle counts tcnt, mode 0 takes t = 0.
+// mode 1 uses the triangle counts tcnt, mode 0 takes t = 0.  BF16: each row
+// standardised with the model's mean and standard deviation, z = (x - mean)
+// * (1 / std) in FP32 as the network does it, and rounded to BF16, two
+// features per word: exactly the network's first-layer operand, in 32 bytes
+// per row instead of 64.
+template <bool BF16>
 __global__ void k_features(int32_t n, int mode, const int32_t *__restrict__ D, const int64_t *__restrict__ sig1,
                            const int64_t *__restrict__ sig2, const int64_t *__restrict__ omega,
                            const int32_t *__restrict__ nmin, const int32_t *__restrict__ nmax,
-                           const int64_t *__restrict__ tcnt, float *__restrict__ X) {
+                           const int64_t *__restrict__ tcnt, float *__restrict__ X, const ModelDev *__restrict__ M) {
+    __shared__ float s_mean[MLP_F], s_istd[MLP_F];
+    if (BF16) {
+        if (threadIdx.x < MLP_F) {
+            s_mean[threadIdx.x] = M->mean[threadIdx.x];
+            s_istd[threadIdx.x] = 1.0f / M->stdv[threadIdx.x];
+        }
+        __syncthreads();
+    }
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const int64_t d = D[v], s1 = sig1[v], s2 = sig2[v], om = omega[v];
         const int64_t t = mode ? tcnt[v] : 0;
@@ -171,15 +184,31 @@ __global__ void k_features(int32_t n, int mode, const int32_t *__restrict__ D, c
         f[13] = log1pf((float)S);
         f[14] = f[2] - f[1];
         f[15] = f[3] - f[1];
-        float4 *dst = reinterpret_cast<float4 *>(X + (int64_t)v * MLP_F);
+        if (BF16) {
+            uint32_t wd[MLP_F / 2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+            for (int q = 0; q < MLP_F / 2; ++q)
+                wd[q] = pack_bf16((f[2 * q] - s_mean[2 * q]) * s_istd[2 * q],
+                                  (f[2 * q + 1] - s_mean[2 * q + 1]) * s_istd[2 * q + 1]);
+            uint4 *dst = reinterpret_cast<uint4 *>(X) + (int64_t)v * 2;
+            dst[0] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+            dst[1] = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+        } else {
+            float4 *dst = reinterpret_cast<float4 *>(X + (int64_t)v * MLP_F);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(f[4 * q], f[4 * q + 1], f[4 * q + 2], f[4 * q + 3]);
+        }
     }
 }
 
-int launch_features(const Scratch &s, const RankScratch &r, int32_t n, int mode, const Tune &t, cudaStream_t st) {
-    k_features<<<t.grid((int64_t)n, 256), 256, 0, st>>>(n, mode, s.D, s.sig1, s.sig2, s.omega, r.nbr_min, r.nbr_max,
-                                                         s.tcnt, r.x);
+int launch_features(const Scratch &s, const RankScratch &r, int32_t n, int mode, const Tune &t, cudaStream_t st,
+                    const ModelDev *std_model) {
+    if (std_model)
+        k_features<true><<<t.grid((int64_t)n, 256), 256, 0, st>>>(n, mode, s.D, s.sig1, s.sig2, s.omega, r.nbr_min,
+                                                                 r.nbr_max, s.tcnt, r.x, std_model);
+    else
+        k_features<false><<<t.grid((int64_t)n, 256), 256, 0, st>>>(n, mode, s.D, s.sig1, s.sig2, s.omega, r.nbr_min,
+                                                                  r.nbr_max, s.tcnt, r.x, nullptr);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -305,6 +305,22 @@ def _rank(ctx, model, g, cand_frac):
     return idx.cpu().numpy(), efv.cpu().numpy(), score.cpu().numpy(), st
 
 
+def test_rank_scores_equal_network_on_fp32_features(ctx, trained):
+    """The ranking path writes its features standardised and rounded to BF16 (the network's first
+    operand) and runs the network on those rows; every prediction equals the network's on the FP32
+    rows of ef_features, bit for bit."""
+    import torch
+    import paper_2306_00606_gb300 as ef
+    model = trained[0]
+    g = synth.barabasi_albert(50000, 4, 61)
+    _, _, score, _ = _rank(ctx, model, g, cand_frac=0.02)
+    x = _features(ctx, g, ef.ef_model_feature_mode(model.handle))
+    ref = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    model.forward(x, ref)
+    torch.cuda.synchronize()
+    assert np.array_equal(score, ref.cpu().numpy())
+
+
 def test_ranking_recall_and_what_the_network_gains(ctx, trained):
     import paper_2306_00606_gb300 as ef
     model = trained[0]
