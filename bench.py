@@ -700,6 +700,13 @@ def workloads_leg(args, dev, hbm: float) -> dict:
                            "roofline_path": {"bound": "hbm", "algorithmic_bytes": path_bytes,
                                              "achieved": path_bytes / (ms / 1e3) / 1e9, "peak": hbm,
                                              "unit": "GB/s", "frac": path_bytes / (ms / 1e3) / 1e9 / hbm}}
+        if not batched:
+            # validation on the device (no readback midway), alone and as one replayed CUDA graph
+            entry["device_check_fp32c"] = {}
+            for label, kw in (("ms_per_call", {}), ("ms_per_call_graph", {"graph": True})):
+                def dcall(kw=kw):
+                    ef.ef_compute_ex(ctx.handle, rp, ci, precision="fp32c", ef=out, device_check=True, **kw)
+                entry["device_check_fp32c"][label] = _time_events(dcall, stream, dev, reps=10)
         if name in ("er2000", "ba1m"):
             # the oracle beside it, on all host cores and on one (bounded samples)
             entry["oracle"] = {}
@@ -710,7 +717,7 @@ def workloads_leg(args, dev, hbm: float) -> dict:
         if batched:
             # each graph alone: its rows relabelled to 0.., one synchronous call each
             off = g.graph_off
-            walls, works = [], []
+            walls, walls_dc, works = [], [], []
             for k in range(G):
                 a, b = int(off[k]), int(off[k + 1])
                 e0, e1 = int(g.row_ptr[a]), int(g.row_ptr[b])
@@ -724,6 +731,9 @@ def workloads_leg(args, dev, hbm: float) -> dict:
                 t0 = time.perf_counter()
                 ef.ef_compute_ex(ctx.handle, srp, sci, precision="fp32c", ef=sout)
                 walls.append((time.perf_counter() - t0) * 1e3)
+                t0 = time.perf_counter()
+                ef.ef_compute_ex(ctx.handle, srp, sci, precision="fp32c", ef=sout, device_check=True)
+                walls_dc.append((time.perf_counter() - t0) * 1e3)
                 d = np.diff(g.row_ptr[a:b + 1]).astype(np.int64)
                 works.append(int((d * (d - 1) // 2).sum()))
             w = np.array(walls)
@@ -734,6 +744,12 @@ def workloads_leg(args, dev, hbm: float) -> dict:
                 "clusters_per_graph_p10_p50_p90": [float(np.percentile(works, q)) for q in (10, 50, 90)],
                 "note": "each graph as a separate synchronous ef_compute_ex call (host wall clock, validation "
                         "readback included); the batched call above runs all of them in one pass"}
+            w = np.array(walls_dc)
+            entry["per_graph_alone_fp32c_device_check"] = {
+                "ms_p10": float(np.percentile(w, 10)), "ms_p50": float(np.percentile(w, 50)),
+                "ms_p90": float(np.percentile(w, 90)), "ms_p99": float(np.percentile(w, 99)),
+                "ms_max": float(w.max()), "ms_sum": float(w.sum()),
+                "note": "the same calls with device_check (validation on the device, one readback at the end)"}
         res[name] = entry
         del rp, ci, out
         torch.cuda.empty_cache()

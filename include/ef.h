@@ -104,7 +104,23 @@ typedef struct {
                               one CUDA graph, captured on the first call and
                               replayed while pointers, sizes, options and
                               tuning stay the same (ignored with profile) */
-    int32_t reserved;
+    int32_t device_check;  /* 1: validate on the device with no readback in
+                              the middle of the call (ignored with
+                              trust_input).  The kernels after the
+                              validation do nothing when it failed, so the
+                              whole call -- validation included -- is one
+                              CUDA graph with graph = 1.  A synchronous call
+                              reads the validation result once at its end and
+                              returns EF_ERR_GRAPH or EF_ERR_UNSUPPORTED as
+                              without device_check; with async the next
+                              ef_sync returns that error (any failed call
+                              since the previous ef_sync).  On an error the
+                              outputs are not written.  The layout of the
+                              oriented lists is then chosen without the
+                              readback (ef_tuning.layout), and the f table
+                              is sized for min(n - 1, m, EF_MAX_DEGREE).
+                              Read by ef_compute_ex and ef_compute_batched;
+                              the other calls ignore it. */
 } ef_options;
 
 /* Optional per-node outputs (any may be NULL); length n each. */
@@ -171,7 +187,10 @@ int ef_ctx_destroy(ef_ctx *ctx);
 /* Message of the last failure on this context ("" if none); ctx may be
  * NULL for failures of ef_compute and ef_ctx_create. */
 const char *ef_last_error(const ef_ctx *ctx);
-/* Wait for all work issued on the context's stream. */
+/* Wait for all work issued on the context's stream.  Returns EF_ERR_GRAPH
+ * or EF_ERR_UNSUPPORTED when an asynchronous call with device_check since
+ * the previous ef_sync failed its validation (the message names the bits of
+ * all of them), else EF_OK or EF_ERR_CUDA. */
 int ef_sync(ef_ctx *ctx);
 /* Read (and with reset != 0, clear) the accumulated pass timings. */
 int ef_get_stats(ef_ctx *ctx, ef_stats *out, int reset);

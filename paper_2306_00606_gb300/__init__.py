@@ -48,7 +48,7 @@ class ef_csr(ctypes.Structure):
 class ef_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("trust_input", ctypes.c_int32), ("host_io", ctypes.c_int32),
                 ("async_", ctypes.c_int32), ("profile", ctypes.c_int32), ("wedge_mode", ctypes.c_int32),
-                ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("graph", ctypes.c_int32), ("device_check", ctypes.c_int32)]
 
 
 class ef_outputs(ctypes.Structure):
@@ -231,18 +231,19 @@ def ef_compute(row_ptr, col_idx, out_ef) -> None:
     _check(load_library().ef_compute(ctypes.byref(g), n, int(col_idx.shape[0]), _ptr(out_ef)))
 
 
-def _options(precision, trust_input, host_io, async_, profile, wedge_mode, graph) -> ef_options:
+def _options(precision, trust_input, host_io, async_, profile, wedge_mode, graph, device_check=False) -> ef_options:
     return ef_options(PRECISIONS[precision], int(trust_input), int(host_io), int(async_), int(profile),
-                      int(wedge_mode), int(graph))
+                      int(wedge_mode), int(graph), int(device_check))
 
 
 def ef_compute_ex(ctx: int, row_ptr, col_idx, *, precision: str = "fp64", ef=None, n_clusters=None, s=None,
                   t=None, triangles=None, flag=None, trust_input: bool = False, host_io: bool = False,
-                  async_: bool = False, profile: bool = False, wedge_mode: int = 0, graph: bool = False) -> None:
+                  async_: bool = False, profile: bool = False, wedge_mode: int = 0, graph: bool = False,
+                  device_check: bool = False) -> None:
     """Full-control EF: writes whichever output buffers are given (device, or host with host_io)."""
     n = int(row_ptr.shape[0]) - 1
     g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
-    o = _options(precision, trust_input, host_io, async_, profile, wedge_mode, graph)
+    o = _options(precision, trust_input, host_io, async_, profile, wedge_mode, graph, device_check)
     out = ef_outputs(_ptr(ef), _ptr(n_clusters), _ptr(s), _ptr(t), _ptr(triangles), _ptr(flag))
     _check(load_library().ef_compute_ex(ctx, ctypes.byref(g), n, int(col_idx.shape[0]), ctypes.byref(o),
                                         ctypes.byref(out)), ctx)
@@ -251,12 +252,12 @@ def ef_compute_ex(ctx: int, row_ptr, col_idx, *, precision: str = "fp64", ef=Non
 def ef_compute_batched(ctx: int, row_ptr, col_idx, graph_off, *, precision: str = "fp64", ef=None,
                        n_clusters=None, s=None, t=None, triangles=None, flag=None, trust_input: bool = False,
                        host_io: bool = False, async_: bool = False, profile: bool = False, wedge_mode: int = 0,
-                       graph: bool = True) -> None:
+                       graph: bool = True, device_check: bool = False) -> None:
     """EF of every node of a batch of graphs given as one disjoint-union CSR; graph_off is a host int64
     array of num_graphs + 1 node offsets."""
     off = np.ascontiguousarray(np.asarray(graph_off, dtype=np.int64))
     g = ef_csr(_ptr(row_ptr), _ptr(col_idx))
-    o = _options(precision, trust_input, host_io, async_, profile, wedge_mode, graph)
+    o = _options(precision, trust_input, host_io, async_, profile, wedge_mode, graph, device_check)
     out = ef_outputs(_ptr(ef), _ptr(n_clusters), _ptr(s), _ptr(t), _ptr(triangles), _ptr(flag))
     _check(load_library().ef_compute_batched(ctx, ctypes.byref(g), int(col_idx.shape[0]),
                                              off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1,

@@ -9,6 +9,10 @@
 //            check that no entry leaves its graph, in the same row pass
 //   host     one small readback: validation word, symmetry sum and max
 //            degree (skipped with trust_input); part B runs on valid input only
+//            (device_check: no readback here; a one-thread kernel stores the
+//            validation bits where every kernel of part B reads them, so part B
+//            does nothing on invalid input, and the host reads the bits once
+//            the call's work is done)
 //   part B   f table (f(d) = d ln d and the triangle corrections, d < 3 maxdeg + 1);
 //            orientation (oriented CSR + omega); wedge pass (small, then mid +
 //            hub middle nodes); hash tables and pair tests; finalize (per node)
@@ -18,7 +22,8 @@
 // than doubles under contention), so they run in sequence.
 //
 // CUDA graphs (ef_options.graph): the part that needs no host decision --
-// part B, or parts A and B together under trust_input -- is captured once on
+// part B, or parts A and B together under trust_input or device_check -- is
+// captured once on
 // a private stream and replayed into the context stream while the pointers,
 // sizes, options and tuning stay the same (one cached graph per context).
 #include "ef_internal.cuh"
@@ -59,7 +64,10 @@ struct ef_ctx {
     size_t scratch_bytes = 0;
     double *ftab = nullptr;
     int64_t ftab_cap = 0;
-    int32_t *h_counters = nullptr;   // pinned, NUM_COUNTERS ints
+    int32_t *h_counters = nullptr;   // pinned, NUM_COUNTERS ints, then the host copy of *d_sticky
+    int32_t *d_sticky = nullptr;     // validation bits of asynchronous device-checked calls since ef_sync
+    bool sticky_pending = false;     // such a call was issued since the last ef_sync
+    int32_t *scratch_counters = nullptr;   // counters of the last call's scratch (device)
     void *io = nullptr;              // device copies for host_io
     size_t io_bytes = 0;
     int64_t *goff = nullptr;         // device copy of the batch offsets
@@ -289,13 +297,23 @@ int compute_device(ef_ctx *ctx, const Job &j) {
     int rc = ensure_buffer(ctx, &ctx->scratch, &ctx->scratch_bytes, need, need / 8);
     if (rc) return rc;
     carve_scratch((char *)ctx->scratch, j.n, j.m, s);
+    ctx->scratch_counters = s.counters;
     const bool prof = o.profile != 0;
     const bool use_graph = o.graph != 0 && !prof;
+    const bool dev_check = o.device_check != 0 && !o.trust_input;
+    // part A in the same stream as part B, with no host decision between them
+    const bool a_inline = o.trust_input || dev_check;
+    auto part_a_inline = [&](cudaStream_t cs) -> int {
+        int r = part_a(ctx, j, s, cs);
+        if (!r && dev_check) LAUNCH(launch_gate(s.counters, o.async ? ctx->d_sticky : nullptr, cs), "validation gate");
+        return r;
+    };
 
     // f table size: from the validated max degree, else the largest possible
     int64_t fcap;
-    if (o.trust_input) {
-        const int64_t bound = (int64_t)j.n - 1 < j.m ? (int64_t)j.n - 1 : j.m;
+    if (a_inline) {
+        int64_t bound = (int64_t)j.n - 1 < j.m ? (int64_t)j.n - 1 : j.m;
+        if (bound > EF_MAX_DEGREE) bound = EF_MAX_DEGREE;
         fcap = 3 * (bound > 0 ? bound : 0) + 1;
         ctx->bins = bin_layout(ctx->tune, nullptr, j.n, j.goff_dev != nullptr);
     } else {
@@ -333,21 +351,21 @@ int compute_device(ef_ctx *ctx, const Job &j) {
         key.G = j.G;
         key.precision = o.precision;
         key.wedge_mode = o.wedge_mode;
-        key.trust = o.trust_input;
+        key.trust = o.trust_input | (dev_check ? 2 : 0) | (dev_check && o.async ? 4 : 0);
         key.bins = ctx->bins;
         key.tune = ctx->tune;
         rc = run_graph(ctx, key, [&](cudaStream_t cs) {
-            if (o.trust_input) {
-                const int r = part_a(ctx, j, s, cs);
+            if (a_inline) {
+                const int r = part_a_inline(cs);
                 if (r) return r;
             }
             return part_b(ctx, j, s, fcap, false, cs);
         });
         if (rc) return rc;
     } else {
-        if (o.trust_input) {
+        if (a_inline) {
             if (prof) CU(cudaEventRecord(ctx->ev[0], st));
-            rc = part_a(ctx, j, s, st);
+            rc = part_a_inline(st);
             if (rc) return rc;
         }
         if (prof) CU(cudaEventRecord(ctx->ev[1], st));
@@ -428,9 +446,19 @@ int run_job(ef_ctx *ctx, Job j, const ef_outputs *host_out) {
         if (ho.flag) CU(cudaMemcpyAsync(ho.flag, dout.flag, N, cudaMemcpyDeviceToHost, ctx->stream));
     }
     if (rc) return rc;
+    const bool dev_check = j.o.device_check != 0 && !j.o.trust_input;
     if (!j.o.async) {
+        if (dev_check)
+            CU(cudaMemcpyAsync(ctx->h_counters, ctx->scratch_counters, ef::NUM_COUNTERS * sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
+        if (dev_check) {
+            if (const int bits = ef::prep_error_bits(ctx->h_counters)) return graph_error(ctx, bits);
+            if (const int lim = degree_limit(ctx, ctx->h_counters)) return lim;
+        }
         if (j.o.profile) accumulate_stats(ctx, j.o.wedge_mode);
+    } else if (dev_check) {
+        ctx->sticky_pending = true;
     }
     CU(cudaGetLastError());
     return EF_OK;
@@ -714,7 +742,9 @@ int ef_ctx_create(int device, void *stream, ef_ctx **out) {
     ctx->stream = (cudaStream_t)stream;
     cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     ctx->tune.num_sms = ctx->num_sms;
-    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counters, ef::NUM_COUNTERS * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counters, (ef::NUM_COUNTERS + 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_sticky, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_sticky, 0, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking);
     for (int i = 0; i < 10 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
     if (e == cudaSuccess && ef::prepare_kernels()) e = cudaGetLastError();
@@ -746,6 +776,7 @@ int ef_ctx_destroy(ef_ctx *ctx) {
     cudaFree(ctx->acts);
     cudaFree(ctx->dtmp);
     cudaFree(ctx->sir);
+    cudaFree(ctx->d_sticky);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     for (int i = 0; i < 10; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
@@ -759,7 +790,24 @@ const char *ef_last_error(const ef_ctx *ctx) { return ctx ? ctx->err : g_err; }
 int ef_sync(ef_ctx *ctx) {
     if (!ctx) return EF_ERR_ARG;
     DeviceGuard dg(ctx->device);
+    if (!ctx->sticky_pending) {
+        CU(cudaStreamSynchronize(ctx->stream));
+        return EF_OK;
+    }
+    // asynchronous device-checked calls since the last ef_sync: their
+    // validation bits, OR-ed together on the device
+    int32_t *h = ctx->h_counters + ef::NUM_COUNTERS;
+    CU(cudaMemcpyAsync(h, ctx->d_sticky, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_sticky, 0, sizeof(int32_t), ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    ctx->sticky_pending = false;
+    const int bits = *h;
+    if (bits & ~ef::ERRB_DEGREE) return graph_error(ctx, bits & ~ef::ERRB_DEGREE);
+    if (bits) {
+        set_err(ctx, "maximum degree above EF_MAX_DEGREE (%d): the exact cluster-degree sums would overflow 64 bits",
+                EF_MAX_DEGREE);
+        return EF_ERR_UNSUPPORTED;
+    }
     return EF_OK;
 }
 

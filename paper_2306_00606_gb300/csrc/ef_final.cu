@@ -99,6 +99,7 @@ struct FinalArgs {
 
 template <bool F64>
 __global__ void __launch_bounds__(256) k_finalize(int32_t n, FinalArgs f) {
+    if (gate_closed(f.cnt)) return;
     const int F = f.cnt[CNT_TRIFRAC];
     const double qscale = ldexp(1.0, -F);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {

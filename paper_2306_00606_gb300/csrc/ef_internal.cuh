@@ -47,6 +47,7 @@ enum : int {
     ERRB_CROSS = 32,    // batched input: an entry outside its row's graph
     ERRB_NODE = 64,     // a requested node id outside [0, n)
     ERRB_SIR_ARG = 128, // SIR: an index case outside [0, n) or immune, or an immune-set index out of range
+    ERRB_DEGREE = 256,  // device-side check: the maximum degree is above EF_MAX_DEGREE
 };
 
 // Work bins (each a list of node ids of capacity n), filled from the degrees.
@@ -146,6 +147,7 @@ enum : int {
     CNT_SYM = 44,     // 44, 45: the symmetry sum (uint64, 8-byte aligned)
     CNT_BIGLO = 46,   // n - 1 - (smallest id of a node of degree > SMALL_MAX), if any
     CNT_BIGHI = 47,   // largest id of a node of degree > SMALL_MAX, if any
+    CNT_GATE = 48,    // device-side check: the call's validation bits (0: part B runs), see gate_closed
     NUM_COUNTERS = 64
 };
 
@@ -180,6 +182,14 @@ size_t carve_scratch(char *base, int32_t n, int64_t m, Scratch &s);
 size_t accumulator_bytes(const Scratch &s);
 
 // ----------------------------------------------------------------- helpers
+// Device-side validation (ef_options.device_check): k_gate stores the call's
+// validation bits in cnt[CNT_GATE] once the row passes are done, and every
+// kernel after them returns at once when they are set, so nothing indexes by
+// the column ids (or by anything derived from them) of a graph that failed.
+// The word is 0 in every other mode: the counters start at zero each call,
+// and the host refuses an invalid graph before part B.
+__device__ __forceinline__ bool gate_closed(const int32_t *cnt) { return cnt[CNT_GATE] != 0; }
+
 __device__ __forceinline__ bool rank_less(int32_t Dx, int32_t x, int32_t Dy, int32_t y) {
     // degree order used to orient edges for triangle listing: (degree, id)
     return Dx < Dy || (Dx == Dy && x < y);
@@ -454,6 +464,10 @@ int64_t device_l2_bytes();   // of the current device (after prepare_kernels ran
 inline bool rows_in_bins_allowed(int64_t m) { return 4 * m <= device_l2_bytes() / 2; }
 int launch_scan(const int32_t *in, int32_t *out, int32_t n, int32_t *tmp, cudaStream_t st);
 int launch_ftab(float2 *ftab, int64_t *tq, int32_t *cnt, int64_t cap, cudaStream_t st);
+// Device-side check after the row passes: the validation bits (error word,
+// symmetry sum, maximum degree above EF_MAX_DEGREE) into cnt[CNT_GATE], and
+// OR-ed into *sticky when it is not null.
+int launch_gate(int32_t *cnt, int32_t *sticky, cudaStream_t st);
 int launch_wedge_small(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int32_t n,
                        const Tune &t, cudaStream_t st);
 int launch_wedge_big(const int32_t *rp, const int32_t *ci, const Scratch &s, int precision, int wedge_mode,

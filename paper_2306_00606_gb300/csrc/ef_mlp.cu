@@ -105,7 +105,7 @@ __device__ __forceinline__ void tile_forward(const MlpSmem &s, const float *xg, 
 }
 
 __device__ __forceinline__ void tile_forward(const MlpSmem &s, RowPart rg, RowPart rg8, bool vg, bool vg8, Tile &T) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int t = threadIdx.x & 3;
     const int f0 = 2 * t, f1 = 2 * t + 8;
     float z[2][4];
 #pragma unroll

@@ -591,6 +591,7 @@ __device__ __forceinline__ int layout_node(const int32_t *bins, int32_t n, const
 __global__ void k_layout_gather(const int32_t *__restrict__ bins, const int32_t *__restrict__ cnt, int32_t n,
                                 const int32_t *__restrict__ outdeg, int32_t *__restrict__ lay_node,
                                 int32_t *__restrict__ lay_deg) {
+    if (gate_closed(cnt)) return;
     __shared__ int s_base[LAYOUT_BINS + 1];
     if (threadIdx.x == 0) layout_bases(cnt, s_base);
     __syncthreads();
@@ -608,6 +609,7 @@ __global__ void k_layout_gather(const int32_t *__restrict__ bins, const int32_t 
 
 __global__ void k_layout_scatter(const int32_t *__restrict__ cnt, int32_t n, const int32_t *__restrict__ lay_node,
                                  const int32_t *__restrict__ lay_ptr, int32_t *__restrict__ out_ptr) {
+    if (gate_closed(cnt)) return;
     __shared__ int s_base[LAYOUT_BINS + 1];
     if (threadIdx.x == 0) layout_bases(cnt, s_base);
     __syncthreads();
@@ -671,6 +673,7 @@ __global__ void __launch_bounds__(256, CHUNK == 8 ? 3 : 5) k_orient(
     const int32_t *__restrict__ rp, int32_t n, int64_t m, int tmax, int hub_min, Orient o,
     const int32_t *__restrict__ D, const int32_t *__restrict__ bins, bool bins_ok, const int32_t *__restrict__ cnt,
     const int32_t *__restrict__ out_ptr, const int32_t *__restrict__ outdeg, int64_t *__restrict__ omega) {
+    if (gate_closed(cnt)) return;
     if ((cnt[BIN_BIG] == 0) != (CHUNK == 8)) return;
     constexpr int CAP = OrientCap<CHUNK>::value;
     constexpr int SCAP = CAP > 0 ? CAP : 1, TCAP = CAP > 0 ? 2 * CAP + 8 : 1;
@@ -757,6 +760,7 @@ __global__ void __launch_bounds__(ROW_CTA) k_orient_hub(const int32_t *__restric
                                                         const int32_t *__restrict__ out_ptr,
                                                         const int32_t *__restrict__ cnt,
                                                         int64_t *__restrict__ omega) {
+    if (gate_closed(cnt)) return;
     __shared__ int64_t s_buf[32];
     const int total = hub_total(cnt);
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
@@ -805,6 +809,7 @@ __global__ void k_hash_rows(const int32_t *__restrict__ rp, int32_t n, int64_t m
                             const int4 *__restrict__ info, const int32_t *__restrict__ out_ptr,
                             const int32_t *__restrict__ outdeg, const int32_t *__restrict__ out_col,
                             int32_t *__restrict__ out_hash) {
+    if (gate_closed(cnt)) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -832,6 +837,7 @@ __global__ void k_hash_tail(const int32_t *__restrict__ cnt, const int32_t *__re
                             const int32_t *__restrict__ out_ptr, int32_t n, const int4 *__restrict__ info,
                             const int32_t *__restrict__ out_col, const int32_t *__restrict__ out_src,
                             int32_t *__restrict__ out_hash) {
+    if (gate_closed(cnt)) return;
     __shared__ int s_base[LAYOUT_BINS + 1];
     if (threadIdx.x == 0) layout_bases(cnt, s_base);
     __syncthreads();
@@ -850,6 +856,7 @@ __global__ void k_hash_tail(const int32_t *__restrict__ cnt, const int32_t *__re
 // each; entries past the bin count are 0 so a scan over n gives the offsets.
 __global__ void k_big_chunks(const int32_t *__restrict__ D, const int32_t *__restrict__ big_list,
                              const int32_t *__restrict__ cnt, int32_t n, int32_t *__restrict__ chunks) {
+    if (gate_closed(cnt)) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int nb = cnt[BIN_BIG];
@@ -865,14 +872,23 @@ __global__ void k_big_chunks(const int32_t *__restrict__ D, const int32_t *__res
 // (|g| <= 8 (ln(3 maxdeg) + 1) + 8); every thread derives the same F and
 // thread 0 publishes it for the finalize pass.
 __global__ void k_ftab(float2 *__restrict__ ftab, int64_t *__restrict__ tq, int32_t *__restrict__ cnt, int64_t cap) {
+    if (gate_closed(cnt)) return;
     const int64_t maxdeg = cnt[CNT_MAXDEG];
     int64_t L = 3 * maxdeg + 1;
     if (L > cap) L = cap;
-    const double tmax = 0.5 * (double)maxdeg * (double)(maxdeg > 0 ? maxdeg - 1 : 0) + 1.0;
-    const double gmax = 8.0 * (log(3.0 * (double)maxdeg + 8.0) + 1.0) + 8.0;
-    int F = (int)floor(62.0 - log2(tmax * gmax));
-    F = F > TRI_FRAC_MAX ? TRI_FRAC_MAX : (F < 0 ? 0 : F);
-    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[CNT_TRIFRAC] = F;
+    // blocks past the table (the grid is sized for the capacity, which may
+    // be far above 3 maxdeg + 1 when it was not read back) leave at once
+    if ((int64_t)blockIdx.x * blockDim.x >= L && blockIdx.x != 0) return;
+    __shared__ int s_F;
+    if (threadIdx.x == 0) {
+        const double tmax = 0.5 * (double)maxdeg * (double)(maxdeg > 0 ? maxdeg - 1 : 0) + 1.0;
+        const double gmax = 8.0 * (log(3.0 * (double)maxdeg + 8.0) + 1.0) + 8.0;
+        const int F0 = (int)floor(62.0 - log2(tmax * gmax));
+        s_F = F0 > TRI_FRAC_MAX ? TRI_FRAC_MAX : (F0 < 0 ? 0 : F0);
+        if (blockIdx.x == 0) cnt[CNT_TRIFRAC] = s_F;
+    }
+    __syncthreads();
+    const int F = s_F;
     for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < L; d += (int64_t)gridDim.x * blockDim.x) {
         const double f = d > 1 ? (double)d * log((double)d) : 0.0;
         const float hi = (float)f;
@@ -950,9 +966,22 @@ int launch_scan(const int32_t *in, int32_t *out, int32_t n, int32_t *tmp, cudaSt
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+__global__ void k_gate(int32_t *__restrict__ cnt, int32_t *__restrict__ sticky) {
+    unsigned long long sym;
+    memcpy(&sym, cnt + CNT_SYM, sizeof sym);
+    const int bits = cnt[CNT_ERR] | (sym ? ERRB_ASYM : 0) | (cnt[CNT_MAXDEG] > EF_MAX_DEGREE ? ERRB_DEGREE : 0);
+    cnt[CNT_GATE] = bits;
+    if (bits && sticky) atomicOr(sticky, bits);
+}
+
+int launch_gate(int32_t *cnt, int32_t *sticky, cudaStream_t st) {
+    k_gate<<<1, 1, 0, st>>>(cnt, sticky);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_ftab(float2 *ftab, int64_t *tq, int32_t *cnt, int64_t cap, cudaStream_t st) {
     int64_t blocks = (cap + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
+    if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
     k_ftab<<<(unsigned)blocks, 256, 0, st>>>(ftab, tq, cnt, cap);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

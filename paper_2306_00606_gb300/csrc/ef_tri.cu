@@ -142,14 +142,14 @@ __global__ void __launch_bounds__(TRI_WARPS * 32, TRI_BLOCKS) k_tri_pairs(
     const int2 *__restrict__ out_pd, const int32_t *__restrict__ out_src, const int32_t *__restrict__ out_hash,
     const int32_t *__restrict__ outdeg, const int32_t *__restrict__ D, int32_t n,
     const int32_t *__restrict__ owner_range, const int64_t *__restrict__ tq,
-    int64_t *__restrict__ qacc, int64_t *__restrict__ tcnt) {
+    int64_t *__restrict__ qacc, int64_t *__restrict__ tcnt, const int32_t *__restrict__ cnt) {
     static_assert(EW == 32 || EW == 64, "a warp step takes 32 or 64 edges");
     __shared__ int s_ex[TRI_WARPS][EW];   // exclusive prefix of unit counts
     __shared__ int s_kend[TRI_WARPS][EW], s_b[TRI_WARPS][EW], s_Db[TRI_WARPS][EW], s_Dab[TRI_WARPS][EW];
     __shared__ int s_a[TRI_WARPS][EW];
     __shared__ int2 s_bpd[TRI_WARPS][EW];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t total = out_ptr[n];
+    const int64_t total = gate_closed(cnt) ? 0 : out_ptr[n];   // no pairs when the device check failed
     const int64_t stride = (int64_t)gridDim.x * TRI_WARPS * EW;
     // owners a in [a_lo, a_hi) open their pairs (all nodes, or one shard's range)
     const int a_lo = owner_range ? owner_range[0] : 0, a_hi = owner_range ? owner_range[1] : n;
@@ -273,11 +273,11 @@ int launch_tri_pairs(const Scratch &s, int32_t n, int64_t m, const Tune &t, cuda
     if (t.tri_variant == 1)
         k_tri_pairs<4, 3, 32><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pd, s.out_src,
                                                             s.out_hash, s.outdeg, s.D, n, owner_range, s.tq, s.qacc,
-                                                            s.tcnt);
+                                                            s.tcnt, s.counters);
     else
         k_tri_pairs<2, 4, 64><<<grid, TRI_WARPS * 32, 0, st>>>(s.out_ptr, s.out_col, s.out_D, s.out_pd, s.out_src,
                                                             s.out_hash, s.outdeg, s.D, n, owner_range, s.tq, s.qacc,
-                                                            s.tcnt);
+                                                            s.tcnt, s.counters);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(256) k_wedge_small(const int32_t *__restrict__
                                                      const int32_t *__restrict__ cnt, int bin,
                                                      const float2 *__restrict__ ftab, double *__restrict__ Tacc,
                                                      void *__restrict__ Ccenter) {
+    if (gate_closed(cnt)) return;
     using Acc = typename std::conditional<F64, double, float>::type;
     constexpr int PER = 32 / G, ILP = SMALL_ILP;
     const int lane = threadIdx.x & 31, grp = lane / G, k = lane % G;
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(BIG_ROWS) k_wedge_big_direct(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
     const int32_t *__restrict__ list, int32_t *__restrict__ cnt, const int32_t *__restrict__ item_ptr,
     const float2 *__restrict__ ftab, double *__restrict__ Tacc, double *__restrict__ partial) {
+    if (gate_closed(cnt)) return;
     using Acc = typename std::conditional<F64, double, float>::type;
     using Elt = typename std::conditional<F64, int, float>::type;
     __shared__ __align__(16) Elt s_a[BIG_TILE];   // FP32C: D_j as float; FP64: D_j as a table offset
@@ -213,6 +215,7 @@ template <bool F64>
 __global__ void k_big_reduce(const int32_t *__restrict__ list, const int32_t *__restrict__ cnt,
                              const int32_t *__restrict__ item_ptr, const double *__restrict__ partial,
                              void *__restrict__ Ccenter_) {
+    if (gate_closed(cnt)) return;
     AccT<F64> *Ccenter = reinterpret_cast<AccT<F64> *>(Ccenter_);
     const int nb = cnt[BIN_BIG];
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
@@ -328,6 +331,7 @@ __global__ void __launch_bounds__(MID_WARPS * 32) k_wedge_mid(
     const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const int32_t *__restrict__ D,
     const int32_t *__restrict__ list, int32_t *__restrict__ cnt, const float2 *__restrict__ ftab,
     double *__restrict__ Tacc, void *__restrict__ Ccenter) {
+    if (gate_closed(cnt)) return;
     using E = ClassEval<F64>;
     using Cls = typename E::Cls;
     using R = typename E::R;
@@ -453,6 +457,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
     const int32_t *__restrict__ bins, int32_t n, int32_t *__restrict__ cnt, const float2 *__restrict__ ftab,
     double *__restrict__ Tacc, void *__restrict__ Ccenter, int32_t *__restrict__ cidx_g, void *__restrict__ cls_g_,
     void *__restrict__ q_g_) {
+    if (gate_closed(cnt)) return;
     using E = ClassEval<F64>;
     using Cls = typename E::Cls;
     using R = typename E::R;
