@@ -253,6 +253,24 @@ def test_rmat_graph(ctx, precision):
     assert_parity(run(ctx, g, precision), alg1_ref(g), precision)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_column_array_not_16_byte_aligned(ctx, precision):
+    """col_idx and row_ptr as views that start 4 bytes into their buffers (only 4-byte
+    alignment): every read of the caller's arrays is a 4-byte load, so the results are the
+    oracle's as for aligned input."""
+    import torch
+    g = synth.disjoint_union([synth.powerlaw_cm(20000, 2.1, 2, 3000, 71), synth.complete(40), synth.path(3)])
+    rbuf = torch.empty(g.n + 2, dtype=torch.int32, device="cuda")
+    cbuf = torch.empty(g.nnz + 1, dtype=torch.int32, device="cuda")
+    rbuf[1:] = torch.from_numpy(g.row_ptr).cuda()
+    cbuf[1:] = torch.from_numpy(g.col_idx).cuda()
+    rp, ci = rbuf[1:], cbuf[1:]
+    assert rp.data_ptr() % 16 and ci.data_ptr() % 16
+    out = ctx.compute(rp, ci, precision=precision, outputs=("ef", "n_clusters", "s", "t", "triangles", "flag"))
+    torch.cuda.synchronize()
+    assert_parity({k: v.cpu().numpy() for k, v in out.items()}, alg1_ref(g), precision)
+
+
 def test_empty_graph(ctx):
     import torch
     out = ctx.compute(torch.zeros(1, dtype=torch.int32, device="cuda"),
