@@ -659,10 +659,12 @@ def _time_events(fn, stream, dev, reps: int, warm: int = 3) -> float:
 
 def workloads_leg(args, dev, hbm: float) -> dict:
     """Every workload besides the headline one, one ef_compute_ex (or
-    ef_compute_batched) per step, inputs in HBM, 3 warm-up and 10 timed
+    ef_compute_batched) per step as in the headline (validation on the
+    device, one replayed CUDA graph), inputs in HBM, 3 warm-up and 10 timed
     calls (CUDA events): ms per graph, clusters/s, the per-pass breakdown
     (a profiled call) and the path's algorithmic bytes (CSR read once, EF
-    written once) against HBM.  The batch adds each graph's own time as a
+    written once) against HBM; single graphs add the default options' time
+    (validation word read back midway).  The batch adds each graph's own time as a
     call of its own (host wall clock around the synchronous call)."""
     import torch
     import paper_2306_00606_gb300 as ef
@@ -684,13 +686,15 @@ def workloads_leg(args, dev, hbm: float) -> dict:
         entry = {"workload": desc, "nodes": g.n, "nnz": g.nnz, "edges": g.nnz // 2, "clusters": gs["W"],
                  "graphs": G, "max_degree": gs["maxdeg"]}
         for prec in precs:
+            # as the headline step: validation on the device, one replayed CUDA graph per call
             if batched:
                 def call(profile=False):
                     ef.ef_compute_batched(ctx.handle, rp, ci, g.graph_off, precision=prec, ef=out,
-                                          graph=not profile, profile=profile)
+                                          graph=not profile, profile=profile, device_check=True)
             else:
                 def call(profile=False):
-                    ef.ef_compute_ex(ctx.handle, rp, ci, precision=prec, ef=out, profile=profile)
+                    ef.ef_compute_ex(ctx.handle, rp, ci, precision=prec, ef=out, profile=profile,
+                                     graph=not profile, device_check=True)
             ms = _time_events(call, stream, dev, reps=10)
             ctx.stats(reset=True)
             call(profile=True)
@@ -701,12 +705,13 @@ def workloads_leg(args, dev, hbm: float) -> dict:
                                              "achieved": path_bytes / (ms / 1e3) / 1e9, "peak": hbm,
                                              "unit": "GB/s", "frac": path_bytes / (ms / 1e3) / 1e9 / hbm}}
         if not batched:
-            # validation on the device (no readback midway), alone and as one replayed CUDA graph
-            entry["device_check_fp32c"] = {}
+            # the default options instead: the validation word read back midway, the passes
+            # launched one by one or part B as a replayed graph
+            entry["readback_fp32c"] = {}
             for label, kw in (("ms_per_call", {}), ("ms_per_call_graph", {"graph": True})):
                 def dcall(kw=kw):
-                    ef.ef_compute_ex(ctx.handle, rp, ci, precision="fp32c", ef=out, device_check=True, **kw)
-                entry["device_check_fp32c"][label] = _time_events(dcall, stream, dev, reps=10)
+                    ef.ef_compute_ex(ctx.handle, rp, ci, precision="fp32c", ef=out, **kw)
+                entry["readback_fp32c"][label] = _time_events(dcall, stream, dev, reps=10)
         if name in ("er2000", "ba1m"):
             # the oracle beside it, on all host cores and on one (bounded samples)
             entry["oracle"] = {}
@@ -784,8 +789,11 @@ def run_ours(args):
     if args.autotune:
         tuned = ef.ef_autotune(ctx.handle, rp, ci, precision=args.precision, reps=2)
 
+    # Every step validates its graph (on the device, no readback midway) and
+    # runs as one replayed CUDA graph; profiled steps run the passes one by
+    # one with events between them.
     def step(profile=False, io=None, c=None, async_=False):
-        kw = dict(precision=args.precision, profile=profile)
+        kw = dict(precision=args.precision, profile=profile, device_check=True, graph=not profile)
         if io is None:
             kw.update(ef=out)
             a, b = rp, ci
@@ -794,7 +802,7 @@ def run_ours(args):
             a, b = io[0], io[1]
         h = (c or ctx).handle
         if batched:
-            ef.ef_compute_batched(h, a, b, g.graph_off, graph=not profile, **kw)
+            ef.ef_compute_batched(h, a, b, g.graph_off, **kw)
         else:
             ef.ef_compute_ex(h, a, b, **kw)
 

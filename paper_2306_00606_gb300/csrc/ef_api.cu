@@ -105,9 +105,10 @@ thread_local char g_err[512];
 // which one returns at once, the hub rows, hash tables of the longer rows;
 // the short rows' tables are filled by the row kernel itself), small wedges
 // 4, big wedges (class kernels 2; direct mode: item counts, a scan of 3,
-// direct kernel, reduction), pair tests 1, finalize 1.
-int64_t kernels_per_call(bool bins, int wedge_mode) {
-    return 3 + 1 + (bins ? 5 : 3) + 5 + 4 + (wedge_mode == 1 ? 6 : 2) + 1 + 1;
+// direct kernel, reduction), pair tests 1, finalize 1; with device_check
+// the validation gate 1.
+int64_t kernels_per_call(bool bins, int wedge_mode, bool dev_check) {
+    return 3 + 1 + (bins ? 5 : 3) + 5 + 4 + (wedge_mode == 1 ? 6 : 2) + 1 + 1 + (dev_check ? 1 : 0);
 }
 
 void set_err(ef_ctx *c, const char *fmt, ...) {
@@ -390,7 +391,7 @@ int check_args(ef_ctx *ctx, const ef_csr *g, int32_t n, int64_t m, const ef_opti
 
 // Events: 0 start, 1 part B start (after the validation readback), 2..6
 // after orientation, small wedges, big wedges, hash tables, pair tests, 7 end.
-void accumulate_stats(ef_ctx *ctx, int wedge_mode) {
+void accumulate_stats(ef_ctx *ctx, int wedge_mode, bool dev_check) {
     auto el = [&](int a, int b) {
         float t = 0.f;
         return cudaEventElapsedTime(&t, ctx->ev[a], ctx->ev[b]) == cudaSuccess ? (double)t : 0.0;
@@ -404,7 +405,7 @@ void accumulate_stats(ef_ctx *ctx, int wedge_mode) {
     st.tri_pairs_ms += el(4, 6);
     st.finalize_ms += el(6, 7);
     st.total_ms += el(0, 7);
-    st.kernels += kernels_per_call(ctx->bins, wedge_mode);
+    st.kernels += kernels_per_call(ctx->bins, wedge_mode, dev_check);
 }
 
 // Host I/O and synchronisation around compute_device.
@@ -456,7 +457,7 @@ int run_job(ef_ctx *ctx, Job j, const ef_outputs *host_out) {
             if (const int bits = ef::prep_error_bits(ctx->h_counters)) return graph_error(ctx, bits);
             if (const int lim = degree_limit(ctx, ctx->h_counters)) return lim;
         }
-        if (j.o.profile) accumulate_stats(ctx, j.o.wedge_mode);
+        if (j.o.profile) accumulate_stats(ctx, j.o.wedge_mode, dev_check);
     } else if (dev_check) {
         ctx->sticky_pending = true;
     }
