@@ -84,7 +84,7 @@ def algorithmic_bytes(g, st):
     }
 
 
-PASS_PREFIX = {"prep_ms": ("k_degrees", "k_row_stats"),
+PASS_PREFIX = {"prep_ms": ("k_degrees", "k_row_stats", "k_gate"),
                "orient_ms": ("k_ftab", "k_layout", "k_scan", "k_node_info", "k_orient", "k_hash"),
                "wedge_small_ms": ("k_wedge_small",), "wedge_big_ms": ("k_wedge_mid", "k_wedge_hub", "k_wedge_big", "k_big"),
                "tri_pairs_ms": ("k_tri_pairs",), "finalize_ms": ("k_finalize",)}
