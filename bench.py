@@ -349,13 +349,14 @@ def rmat_sweep(ctx, args, dev) -> list:
         rp = torch.from_numpy(g.row_ptr).to(dev)
         ci = torch.from_numpy(g.col_idx).to(dev)
         out = torch.empty(g.n, dtype=torch.float64, device=dev)
+        # as the headline step: validation on the device, one replayed CUDA graph per call
         for _ in range(3):
-            ef.ef_compute_ex(ctx.handle, rp, ci, precision=args.precision, ef=out)
+            ef.ef_compute_ex(ctx.handle, rp, ci, precision=args.precision, ef=out, device_check=True, graph=True)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(10):
-            ef.ef_compute_ex(ctx.handle, rp, ci, precision=args.precision, ef=out)
+            ef.ef_compute_ex(ctx.handle, rp, ci, precision=args.precision, ef=out, device_check=True, graph=True)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / 10
