@@ -114,9 +114,11 @@ def committed_kernels(workload):
 
 def passes_ncu(workload):
     """Per pass, from committed_kernels: the kernels, their summed share of the
-    launch time and DRAM bytes per launch (the full-size launch list), and the
-    time-weighted L2 hit rate (a smaller case of the same kernels, inputs still
-    larger than L2; None for a pass with no fresh record)."""
+    launch time and DRAM bytes per launch (the full-size launch list), and,
+    time-weighted over the pass's kernels, the L2 hit rate, the share of
+    cycles in which a warp scheduler issued (the pass's issue or ALU
+    fraction) and the warp slots in use (a smaller case of the same kernels,
+    inputs still larger than L2; None for a pass with no fresh record)."""
     recs = committed_kernels(workload)
     res = {}
     for p, pre in PASS_PREFIX.items():
@@ -125,12 +127,16 @@ def passes_ncu(workload):
             res[p] = None
             continue
         t = sum(r["ms_per_launch"] * r["launches"] for r in ks.values())
-        hk = {k: r for k, r in ks.items() if r.get("l2_hit_pct") is not None}
-        th = sum(r["ms_per_launch"] * r["launches"] for r in hk.values())
+        def weighted(field):
+            # time-weighted over the pass's kernels that have the figure
+            hk = {k: r for k, r in ks.items() if r.get(field) is not None}
+            th = sum(r["ms_per_launch"] * r["launches"] for r in hk.values())
+            return sum(r[field] * r["ms_per_launch"] * r["launches"] for r in hk.values()) / th if th > 0 else None
         res[p] = {"kernels": sorted(ks), "ncu_share": sum(r["share"] for r in ks.values()),
                   "dram_bytes_per_launch": sum(r["dram_bytes_per_launch"] for r in ks.values()),
-                  "l2_hit_pct": sum(r["l2_hit_pct"] * r["ms_per_launch"] * r["launches"] for r in hk.values()) / th
-                  if th > 0 else None}
+                  "l2_hit_pct": weighted("l2_hit_pct"),
+                  "issue_active_pct": weighted("issue_active_pct"),
+                  "warps_active_pct": weighted("warps_active_pct")}
     return res
 
 
