@@ -55,3 +55,42 @@ def test_no_cuda_means_error_not_fallback():
         pytest.skip("a GPU is present")
     with pytest.raises(ef.EfError):
         ef.Context(0)
+
+
+C_NAMES = {"async_": "async"}   # binding field names that are Python keywords in C
+STRUCTS = ("ef_csr", "ef_options", "ef_outputs", "ef_stats", "ef_tuning", "ef_partials", "ef_sir_params",
+           "ef_sir_outputs", "ef_train_options", "ef_train_stats", "ef_rank_stats")
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding passes by pointer has the size and the field
+    names and offsets of its declaration in ef.h: a C program compiled
+    against the header prints them (gcc, no CUDA needed)."""
+    import shutil
+    import subprocess
+    import paper_2306_00606_gb300 as ef
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ef.h"', "int main(void) {"]
+    for name in STRUCTS:
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in getattr(ef, name)._fields_:
+            cfield = C_NAMES.get(field, field)
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {cfield}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    include = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([cc, "-std=c11", "-I", include, str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for name in STRUCTS:
+        cls = getattr(ef, name)
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, f"{name}.{field}"
