@@ -3,8 +3,8 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU legs may
 import this module.  It shares no code with the CUDA library.
 
-The model is Section 3.1's SIR process in discrete time, with this build's
-readings of what the paper leaves open:
+The model is Section 3.1's SIR process in discrete time, with these readings
+of what the paper leaves open:
 
 * Steps t = 0, 1, 2, ... act synchronously on the states at the start of
   the step.  The index case is infected at t = 0; immune nodes never change.
