@@ -181,3 +181,27 @@ def test_device_check_batched(ctx, precision):
                               precision=precision, graph=True, device_check=True, **res)
     assert ei.value.code == ef.EF_ERR_GRAPH and "between-graphs" in ef.ef_last_error(ctx.handle)
     assert np.all(_host(res)["ef"] == -7.0)
+
+
+def test_device_check_host_buffers_two_contexts_in_flight(ctx):
+    """The end-to-end form of the benchmark: host buffers, validation on the device, one replayed
+    graph per call, asynchronous calls alternating between two contexts on two streams (one call's
+    copies beside the other's kernels); every result read after ef_sync is Algorithm 1's."""
+    import torch
+    import paper_2306_00606_gb300 as ef
+    g = synth.barabasi_albert(20000, 4, 5)
+    ref = alg1_ref(g)
+    h_rp = torch.from_numpy(g.row_ptr).pin_memory()
+    h_ci = torch.from_numpy(g.col_idx).pin_memory()
+    outs = [torch.zeros(g.n, dtype=torch.float64).pin_memory() for _ in range(6)]
+    s_out = [torch.zeros(g.n, dtype=torch.int64).pin_memory() for _ in range(6)]
+    with ef.Context(0, torch.cuda.Stream()) as ctx2:
+        ctxs = (ctx, ctx2)
+        for i in range(6):
+            ef.ef_compute_ex(ctxs[i % 2].handle, h_rp, h_ci, precision="fp64", host_io=True, async_=True,
+                             device_check=True, graph=True, ef=outs[i], s=s_out[i])
+        ef.ef_sync(ctx.handle)
+        ef.ef_sync(ctx2.handle)
+    for i in range(6):
+        np.testing.assert_array_equal(s_out[i].numpy(), ref["S"])
+        np.testing.assert_allclose(outs[i].numpy(), ref["EF"], rtol=EF_RTOL64, atol=1e-12)
