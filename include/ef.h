@@ -115,10 +115,12 @@ typedef struct {
                               without device_check; with async the next
                               ef_sync returns that error (any failed call
                               since the previous ef_sync).  On an error the
-                              outputs are not written.  The layout of the
-                              oriented lists is then chosen without the
-                              readback (ef_tuning.layout), and the f table
-                              is sized for min(n - 1, m, EF_MAX_DEGREE).
+                              device outputs are not written (with host_io
+                              the host buffers' contents are undefined).  The
+                              layout of the oriented lists is then chosen
+                              without the readback (ef_tuning.layout), and
+                              the f table is sized for min(n - 1, m,
+                              EF_MAX_DEGREE).
                               Read by ef_compute_ex and ef_compute_batched;
                               the other calls ignore it. */
 } ef_options;
