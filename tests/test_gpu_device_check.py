@@ -205,3 +205,28 @@ def test_device_check_host_buffers_two_contexts_in_flight(ctx):
     for i in range(6):
         np.testing.assert_array_equal(s_out[i].numpy(), ref["S"])
         np.testing.assert_allclose(outs[i].numpy(), ref["EF"], rtol=EF_RTOL64, atol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32c"])
+def test_device_check_direct_kernel_and_profile(ctx, precision):
+    """The direct pairwise wedge kernel (wedge_mode 1, its item counts and reduction gated too) and a
+    profiled call (per-pass events, the gate kernel counted) with validation on the device: results
+    are Algorithm 1's, and a malformed graph is still refused with the outputs left as they were."""
+    import paper_2306_00606_gb300 as ef
+    g = synth.powerlaw_cm(20000, 2.1, 2, 3000, 22)
+    ref = alg1_ref(g)
+    for kw in (dict(wedge_mode=1), dict(profile=True)):
+        ctx.stats(reset=True)
+        res = _alloc(g.n)
+        ef.ef_compute_ex(ctx.handle, _dev(g.row_ptr), _dev(g.col_idx), precision=precision, device_check=True,
+                         **kw, **res)
+        assert_parity(_host(res), ref, precision)
+        if kw.get("profile"):
+            st = ctx.stats(reset=True)
+            assert st["calls"] == 1 and st["prep_ms"] > 0 and st["tri_pairs_ms"] > 0
+        rp, ci = bad_graph("range")
+        out = _alloc(len(rp) - 1, fill=-7)
+        with pytest.raises(ef.EfError) as ei:
+            ef.ef_compute_ex(ctx.handle, _dev(rp), _dev(ci), precision=precision, device_check=True, **kw, **out)
+        assert ei.value.code == ef.EF_ERR_GRAPH
+        assert np.all(_host(out)["ef"] == -7.0)
