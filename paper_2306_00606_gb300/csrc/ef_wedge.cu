@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
     Cls *cls_s = reinterpret_cast<Cls *>(hub_smem + HUB_HIST * sizeof(int32_t));
     R *q_s = reinterpret_cast<R *>(hub_smem + HUB_HIST * sizeof(int32_t) + HUB_SMEM_K * sizeof(Cls));
     __shared__ int s_w[33];
-    __shared__ int s_item, s_nsp;
+    __shared__ int s_item, s_nsp, s_kb;
     __shared__ double s_red[HUB_THREADS / 32];
     const int tid = threadIdx.x;
     int total = 0;
@@ -523,23 +523,27 @@ __global__ void __launch_bounds__(HUB_THREADS) k_wedge_hub(
                 hist[bin] = off++;
             }
         }
+        if (tid == 0) s_kb = Kd;
         __syncthreads();
-        // sparse classes, in neighbour order
-        int kbase = Kd;
+        // sparse classes: positions from a shared counter, one atomic per warp
+        // and pass (no block barrier inside the loop; their order varies)
+        const unsigned lt = (1u << (tid & 31)) - 1u;
         for (int k0 = 0; k0 < Du; k0 += HUB_THREADS) {
             const int k = k0 + tid;
             const bool act = k < Du;
             const int a = act ? cidx[k] : 0;
             const bool sp = act && a >= HUB_HIST;
-            int tot;
-            const int pos = hub_scan(sp ? 1 : 0, s_w, tot);
+            const unsigned bal = __ballot_sync(FULL, sp);
+            int wbase = 0;
+            if ((tid & 31) == 0 && bal) wbase = atomicAdd(&s_kb, __popc(bal));
+            wbase = __shfl_sync(FULL, wbase, 0);
             if (sp) {
-                cls[kbase + pos] = E::make(a, 1, pair_ok);
-                cidx[k] = kbase + pos;
+                const int pos = wbase + __popc(bal & lt);
+                cls[pos] = E::make(a, 1, pair_ok);
+                cidx[k] = pos;
             } else if (act) {
                 cidx[k] = hist[a];
             }
-            kbase += tot;
         }
         __syncthreads();
         double center = 0.0;
