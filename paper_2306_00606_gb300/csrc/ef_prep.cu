@@ -762,11 +762,17 @@ __global__ void __launch_bounds__(ROW_CTA) k_orient_hub(const int32_t *__restric
                                                         int64_t *__restrict__ omega) {
     if (gate_closed(cnt)) return;
     __shared__ int64_t s_buf[32];
+    __shared__ int s_k;
     const int total = hub_total(cnt);
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         const int u = hub_row(bins, n, cnt, it);
         const int a = rp[u], b = rp[u + 1];
-        int k0 = out_ptr[u];
+        // the out-list's entries take their positions from a shared counter,
+        // one atomic per warp and pass (no block barrier per pass; the
+        // list's order varies, which nothing downstream depends on)
+        if (threadIdx.x == 0) s_k = out_ptr[u];
+        __syncthreads();
         int64_t om = 0;
         int64_t mn = 0x7fffffff, mx = 0;
         for (int e0 = a; e0 < b; e0 += ROW_CTA) {
@@ -778,10 +784,11 @@ __global__ void __launch_bounds__(ROW_CTA) k_orient_hub(const int32_t *__restric
                 mn = min(mn, (int64_t)nf.x);
                 mx = max(mx, (int64_t)nf.x);
             }
-            int tot;
-            const int off = block_exclusive_scan(isout ? 1 : 0, &tot);
-            if (isout) o.put(k0 + off, u, x, nf);
-            k0 += tot;
+            const unsigned bal = __ballot_sync(FULL, isout);
+            int wk = 0;
+            if ((threadIdx.x & 31) == 0 && bal) wk = atomicAdd(&s_k, __popc(bal));
+            wk = __shfl_sync(FULL, wk, 0);
+            if (isout) o.put(wk + __popc(bal & lt), u, x, nf);
         }
         om = block_sum<int64_t>(om, s_buf);
         if (o.nmin) {
